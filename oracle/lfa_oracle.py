@@ -1,0 +1,263 @@
+"""FP64 CPU oracle for the SVD of stride-1 periodic multi-channel 2-D convolutions.
+
+TEST INFRASTRUCTURE ONLY. Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` may import this module. The product path (the CUDA
+library and its Python binding) never calls it, and it imports nothing from the
+product package.
+
+What it computes, and where the paper defines it (arXiv 2506.05617, Sec. III):
+
+* ``dense_operator`` -- the convolution as a multiplication operator on the
+  periodic crystal torus, (A f)(x) = sum_{y in N} M_y f(x + y) ("Convolutional
+  Mappings"), unrolled into the dense (c_out*n*m) x (c_in*n*m) matrix that the
+  paper's brute-force baseline decomposes (Sec. I, Sec. IV "Runtime Analysis").
+  ``dense_svd`` is its full LAPACK SVD. This is the plain definition.
+* ``symbols`` -- the symbol A_k = sum_{y in N} M_y exp(2 pi i <k, y>) at every
+  frequency k of the frequency torus T*_{n,m} ("Convolution Theorem"; line 4 of
+  Algorithm 1).
+* ``lfa_svd`` -- Algorithm 1: a LAPACK SVD A_k = U_k S_k V_k^* of every symbol.
+* ``lift`` -- the global singular vectors U^_k = F_k^out U_k and V^_k = F_k^in V_k,
+  whose columns are (channel vector) (x) (Fourier mode / sqrt(nm)).
+* ``fft_symbols`` -- the FFT route of the paper's comparison system (Sec. II,
+  Sec. IV): a 2-D FFT of the zero-padded, origin-shifted kernel. It yields the
+  complex conjugate of the symbol, so the same singular values.
+* ``lfa_backward`` -- dL/dw for a loss L(sigma): with d(sigma_s) = Re(u_s^* dA_k v_s)
+  and dA_k/dw[o,i,a,b] = exp(2 pi i <k, y_ab>) e_o e_i^T (symbol definition above),
+  dL/dw[o,i,a,b] = sum_k sum_s g_{k,s} Re(conj(U_k[o,s]) V_k[i,s] exp(2 pi i <k,y_ab>)).
+
+Conventions (readings of the paper where it is ambiguous):
+* Rows of the torus are n (index j of the frequency, a of the tap, x1 of the
+  pixel); columns are m (l, b, x2). Frequencies are enumerated row-major,
+  f = j*m + l. The paper's Algorithm 1 loops X over n and Y over m.
+* Tap (a, b) sits at offset y = (a - p_h, b - p_w); p defaults to floor(k/2),
+  the stencil centred at x. The exponent sign is +, as in the symbol definition
+  (cross-correlation, f(x + y)).
+* The symbol is c_out x c_in. For c_in != c_out only r = min(c_in, c_out)
+  singular values per frequency are returned; the dense operator has
+  |c_out - c_in|*n*m further singular values that are exactly zero.
+* Singular values are sorted in descending order within each frequency.
+* Phases are reduced exactly on integers: (j*(a - p_h)) mod n, then exp in fp64.
+
+Every function works in float64 / complex128. Inputs may be float32 arrays; they
+are upcast exactly.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "origin", "dense_operator", "dense_svd", "symbols", "fft_symbols", "lfa_svd",
+    "lift", "apply_operator", "apply_adjoint", "half_grid", "lfa_backward",
+    "regulariser_loss", "regulariser_grad_sigma", "folded_kernel",
+]
+
+
+def origin(kh: int, kw: int, pad_h: int = -1, pad_w: int = -1):
+    """Tap origin p = (p_h, p_w); -1 selects floor(k/2), the centred stencil (Sec. III, 3x3 stencil figure)."""
+    return (kh // 2 if pad_h < 0 else pad_h, kw // 2 if pad_w < 0 else pad_w)
+
+
+# --------------------------------------------------------------------------- O1: the definition
+def dense_operator(w, n: int, m: int, pad_h: int = -1, pad_w: int = -1) -> np.ndarray:
+    """Dense periodic operator, Sec. III "Convolutional Mappings": (A f)(x) = sum_y M_y f(x + y).
+
+    Row index (o, x1, x2) -> o*n*m + x1*m + x2; column index (i, z1, z2) likewise.
+    Entry [(o, x), (i, x + y_ab mod (n, m))] accumulates w[o, i, a, b]; taps that
+    alias (k > n) add up, as the periodic torus requires.
+    """
+    w = np.asarray(w, dtype=np.float64)
+    c_out, c_in, kh, kw = w.shape
+    ph, pw = origin(kh, kw, pad_h, pad_w)
+    F = n * m
+    A = np.zeros((c_out * F, c_in * F), dtype=np.float64)
+    x1, x2 = np.meshgrid(np.arange(n), np.arange(m), indexing="ij")
+    pix = (x1 * m + x2).ravel()
+    for a in range(kh):
+        for b in range(kw):
+            src = (((x1 + a - ph) % n) * m + ((x2 + b - pw) % m)).ravel()
+            for o in range(c_out):
+                for i in range(c_in):
+                    np.add.at(A, (o * F + pix, i * F + src), w[o, i, a, b])
+    return A
+
+
+def dense_svd(w, n: int, m: int, pad_h: int = -1, pad_w: int = -1, compute_uv: bool = False):
+    """Full LAPACK SVD of the dense operator (the paper's explicit baseline)."""
+    A = dense_operator(w, n, m, pad_h, pad_w)
+    return np.linalg.svd(A, compute_uv=compute_uv)
+
+
+def apply_operator(w, f, pad_h: int = -1, pad_w: int = -1) -> np.ndarray:
+    """(A f)(o, x) = sum_{i,a,b} w[o,i,a,b] f(i, x + y_ab) on the torus, without forming A.
+
+    ``f`` is [c_in, n, m] (real or complex); returns [c_out, n, m]. Used for residuals
+    at sizes where the dense matrix does not fit.
+    """
+    w = np.asarray(w, dtype=np.float64)
+    c_out, c_in, kh, kw = w.shape
+    ph, pw = origin(kh, kw, pad_h, pad_w)
+    f = np.asarray(f)
+    out = np.zeros((c_out,) + f.shape[1:], dtype=np.result_type(f.dtype, np.float64))
+    for a in range(kh):
+        for b in range(kw):
+            # g(i, x) = f(i, x + y): shifting by -y brings x + y to x
+            g = np.roll(f, shift=(-(a - ph), -(b - pw)), axis=(1, 2))
+            out += np.tensordot(w[:, :, a, b], g, axes=([1], [0]))
+    return out
+
+
+def apply_adjoint(w, g, pad_h: int = -1, pad_w: int = -1) -> np.ndarray:
+    """(A^T g)(i, z) = sum_{o,a,b} w[o,i,a,b] g(o, z - y_ab); ``g`` is [c_out, n, m]."""
+    w = np.asarray(w, dtype=np.float64)
+    c_out, c_in, kh, kw = w.shape
+    ph, pw = origin(kh, kw, pad_h, pad_w)
+    g = np.asarray(g)
+    out = np.zeros((c_in,) + g.shape[1:], dtype=np.result_type(g.dtype, np.float64))
+    for a in range(kh):
+        for b in range(kw):
+            h = np.roll(g, shift=(a - ph, b - pw), axis=(1, 2))
+            out += np.tensordot(w[:, :, a, b].T, h, axes=([1], [0]))
+    return out
+
+
+# --------------------------------------------------------------------------- O2: Algorithm 1
+def _phase(n: int, m: int, dy1: int, dy2: int) -> np.ndarray:
+    """exp(2 pi i <k, y>) for all k = (j/n, l/m) of T*_{n,m}, y = (dy1, dy2); shape [n, m].
+
+    The integer products j*dy1 and l*dy2 are reduced mod n and mod m before the
+    exponential, so the phase is exact up to one fp64 rounding of exp.
+    """
+    j = np.arange(n)[:, None]
+    l = np.arange(m)[None, :]
+    t = ((j * dy1) % n) / n + ((l * dy2) % m) / m
+    return np.exp(2j * np.pi * t)
+
+
+def symbols(w, n: int, m: int, pad_h: int = -1, pad_w: int = -1) -> np.ndarray:
+    """Symbols A_k = sum_{y in N} M_y exp(2 pi i <k, y>) for all n*m frequencies (Sec. III, Alg. 1 line 4).
+
+    Returns complex128 [n*m, c_out, c_in]; frequency f = j*m + l is k = (j/n, l/m).
+    """
+    w = np.asarray(w, dtype=np.float64)
+    c_out, c_in, kh, kw = w.shape
+    ph, pw = origin(kh, kw, pad_h, pad_w)
+    S = np.zeros((n, m, c_out, c_in), dtype=np.complex128)
+    for a in range(kh):
+        for b in range(kw):
+            S += _phase(n, m, a - ph, b - pw)[:, :, None, None] * w[None, None, :, :, a, b]
+    return S.reshape(n * m, c_out, c_in)
+
+
+def fft_symbols(w, n: int, m: int, pad_h: int = -1, pad_w: int = -1) -> np.ndarray:
+    """FFT route (the paper's comparison system, Sec. II and IV): fft2 of the zero-padded kernel.
+
+    The kernel is placed on the n x m grid at its offsets y_ab mod (n, m) (rolled by -p,
+    aliasing taps added), then transformed with numpy's FFT over the spatial axes.
+    numpy's forward FFT uses exp(-2 pi i ...), so the result is conj(A_k). Returns
+    complex128 [n*m, c_out, c_in].
+    """
+    w = np.asarray(w, dtype=np.float64)
+    c_out, c_in, kh, kw = w.shape
+    ph, pw = origin(kh, kw, pad_h, pad_w)
+    K = np.zeros((c_out, c_in, n, m), dtype=np.float64)
+    for a in range(kh):
+        for b in range(kw):
+            K[:, :, (a - ph) % n, (b - pw) % m] += w[:, :, a, b]
+    Fk = np.fft.fft2(K, axes=(2, 3))                      # [c_out, c_in, n, m]
+    return np.ascontiguousarray(Fk.transpose(2, 3, 0, 1)).reshape(n * m, c_out, c_in)
+
+
+def lfa_svd(w, n: int, m: int, pad_h: int = -1, pad_w: int = -1, compute_uv: bool = True):
+    """Algorithm 1 in FP64: a LAPACK SVD of the symbol at every frequency of T*_{n,m}.
+
+    Returns ``sigma`` [n*m, r] (descending per frequency) and, when ``compute_uv``,
+    ``U`` [n*m, c_out, r] and ``V`` [n*m, c_in, r] with A_k = U_k diag(sigma_k) V_k^*.
+    """
+    S = symbols(w, n, m, pad_h, pad_w)
+    if not compute_uv:
+        return np.linalg.svd(S, compute_uv=False)
+    U, s, Vh = np.linalg.svd(S, full_matrices=False)
+    V = np.conj(np.swapaxes(Vh, 1, 2))
+    return s, U, V
+
+
+def lift(U_k, V_k, j: int, l: int, n: int, m: int):
+    """Global singular vectors of one frequency, U^_k = F_k^out U_k and V^_k = F_k^in V_k (Sec. III).
+
+    ``U_k`` [c_out, q] and ``V_k`` [c_in, q] hold q symbol singular vectors. The
+    Fourier mode is f_k(x) = exp(2 pi i (j x1 / n + l x2 / m)) / sqrt(n m) on the
+    row-major grid. Returns u_hat [q, c_out, n, m] and v_hat [q, c_in, n, m].
+    """
+    t = ((j * np.arange(n))[:, None] % n) / n + ((l * np.arange(m))[None, :] % m) / m
+    mode = np.exp(2j * np.pi * t) / np.sqrt(n * m)
+    u_hat = np.einsum("cq,xy->qcxy", np.asarray(U_k), mode)
+    v_hat = np.einsum("cq,xy->qcxy", np.asarray(V_k), mode)
+    return u_hat, v_hat
+
+
+def half_grid(n: int, m: int) -> np.ndarray:
+    """Frequencies f = j*m + l that represent their conjugate pair {k, -k}.
+
+    For a real kernel A_{-k} = conj(A_k) (symbol definition), so one member of each
+    pair carries all the information. The representative is the member with the
+    smaller row-major index; self-conjugate frequencies represent themselves.
+    Returned in increasing order; its length is (n*m + s)/2 with s the number of
+    self-conjugate frequencies.
+    """
+    j, l = np.meshgrid(np.arange(n), np.arange(m), indexing="ij")
+    f = (j * m + l).ravel()
+    fc = (((-j) % n) * m + ((-l) % m)).ravel()
+    return f[f <= fc]
+
+
+def folded_kernel(w, n: int, m: int, pad_h: int = -1, pad_w: int = -1) -> np.ndarray:
+    """Kernel folded onto the torus: taps with equal offsets mod (n, m) added; [c_out, c_in, n, m]."""
+    w = np.asarray(w, dtype=np.float64)
+    c_out, c_in, kh, kw = w.shape
+    ph, pw = origin(kh, kw, pad_h, pad_w)
+    K = np.zeros((c_out, c_in, n, m))
+    for a in range(kh):
+        for b in range(kw):
+            K[:, :, (a - ph) % n, (b - pw) % m] += w[:, :, a, b]
+    return K
+
+
+# --------------------------------------------------------------------------- backward
+def lfa_backward(w, n: int, m: int, g, U, V, pad_h: int = -1, pad_w: int = -1) -> np.ndarray:
+    """dL/dw from the upstream gradient ``g`` = dL/dsigma [n*m, r] and the per-frequency U, V.
+
+    Uses d(sigma_s) = Re(u_s^* dA_k v_s) for a simple singular value and the symbol
+    definition dA_k/dw[o,i,a,b] = exp(2 pi i <k, y_ab>) e_o e_i^T, summed over the
+    full frequency grid:
+        dW[o,i,a,b] = sum_k Re( sum_s g[k,s] conj(U_k[o,s]) V_k[i,s] exp(2 pi i <k, y_ab>) ).
+    """
+    w = np.asarray(w, dtype=np.float64)
+    c_out, c_in, kh, kw = w.shape
+    ph, pw = origin(kh, kw, pad_h, pad_w)
+    g = np.asarray(g, dtype=np.float64)
+    H = np.einsum("fs,fos,fis->foi", g, np.conj(U), V)   # [F, c_out, c_in]
+    dW = np.zeros_like(w)
+    for a in range(kh):
+        for b in range(kw):
+            ph_k = _phase(n, m, a - ph, b - pw).reshape(n * m)
+            dW[:, :, a, b] = np.real(np.einsum("f,foi->oi", ph_k, H))
+    return dW
+
+
+def regulariser_loss(sigmas, lam: float) -> float:
+    """Spectral regulariser over layers: sum_layers max(sigma) + lam * sum (sigma - 1)^2."""
+    return float(sum(np.max(s) + lam * np.sum((np.asarray(s, np.float64) - 1.0) ** 2) for s in sigmas))
+
+
+def regulariser_grad_sigma(sigma, lam: float) -> np.ndarray:
+    """d/dsigma of max(sigma) + lam * sum (sigma - 1)^2 for one layer's [F, r] array.
+
+    The max term contributes 1 at the first maximiser in row-major order. The largest
+    singular value is attained at both k and -k, but sigma_k and sigma_{-k} are the same
+    function of w, so either member gives the same gradient through ``lfa_backward``.
+    """
+    s = np.asarray(sigma, np.float64)
+    g = 2.0 * lam * (s - 1.0)
+    idx = np.unravel_index(int(np.argmax(s)), s.shape)
+    g[idx] += 1.0
+    return g
