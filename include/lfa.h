@@ -1,0 +1,204 @@
+/*
+ * lfa.h -- C ABI of the GB300 (sm_103a) library for the singular value
+ * decomposition of stride-1 periodic multi-channel 2-D convolutions by local
+ * Fourier analysis (LFA), arXiv 2506.05617.
+ *
+ * The method (Sec. III of the paper): a stride-1 convolution on the periodic
+ * n x m torus, (A f)(x) = sum_{y in N} M_y f(x + y) with M_y in R^{c_out x c_in}
+ * ("Convolutional Mappings"), leaves every Fourier mode invariant. Its SVD is
+ * therefore the union, over the n*m frequencies k = (j/n, l/m) of the
+ * frequency torus, of the SVDs of the c_out x c_in symbols
+ *     A_k = sum_{y in N} M_y exp(2 pi i <k, y>)            ("Convolution Theorem"),
+ * and the global singular vectors are the symbol's singular vectors times the
+ * Fourier mode (U^_k = F_k^out U_k, V^_k = F_k^in V_k). Algorithm 1 of the
+ * paper loops over all frequencies, forms the symbol and takes its SVD; this
+ * library does the same on the GPU for all layers of a network at once.
+ *
+ * Conventions used by every call:
+ *  - Weights are float32 in PyTorch's conv layout [c_out][c_in][kh][kw],
+ *    row-major, on the device. Tap (a, b) acts at offset
+ *    y = (a - pad_h, b - pad_w); pad = -1 selects floor(k/2) (centred stencil,
+ *    the paper's 3x3 stencil centred at x). The exponent sign is + as in the
+ *    symbol definition above (cross-correlation f(x + y)).
+ *  - Rows of the torus are n (frequency index j, tap a, pixel x1); columns are
+ *    m (l, b, x2). Frequency f = j*m + l, k = (j/n, l/m).
+ *  - r = min(c_out, c_in) singular values per frequency (the thin SVD of the
+ *    symbol). The dense operator's remaining |c_out - c_in|*n*m singular
+ *    values are exactly zero and are not emitted.
+ *  - For real weights A_{-k} = conj(A_k), so only the "half grid" is decomposed:
+ *    the frequency f represents the pair {f, fc} with fc = ((n-j)%n)*m + (m-l)%m
+ *    when f <= fc. The half grid lists those f in increasing order; its length
+ *    is F_h = (n*m + s)/2, s = number of self-conjugate frequencies.
+ *  - Complex arrays are interleaved float32 pairs (re, im) ("complex64").
+ *  - Singular values are non-negative and sorted in descending order within a
+ *    frequency; U and V columns follow the same order.
+ *  - Every pointer argument that names GPU data is a device pointer. Arrays of
+ *    per-layer pointers ("const float* const* w") are HOST arrays of nlayers
+ *    device pointers. The caller owns all input and output buffers; the plan
+ *    owns only its own tables and counters.
+ *  - Calls that take a stream are asynchronous on that stream (a
+ *    cudaStream_t passed as void*; NULL = legacy default stream). Argument
+ *    errors are reported synchronously by the return value. Numerical
+ *    conditions found on the device (a symbol that did not converge, a
+ *    non-finite entry) are counted on the device and read by lfa_get_info().
+ *  - No call aborts the process or raises; every failure is a status code.
+ *  - A plan is not thread-safe: use one plan per host thread or serialise.
+ */
+#ifndef LFA_H_
+#define LFA_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lfa_status {
+  LFA_OK = 0,
+  LFA_ERR_INVALID_ARG = 1,   /* a size, flag or pointer argument is invalid */
+  LFA_ERR_UNSUPPORTED = 2,   /* valid but not supported (e.g. no sm_103 device) */
+  LFA_ERR_OOM = 3,           /* a device or pinned-host allocation in lfa_plan failed */
+  LFA_ERR_CUDA = 4,          /* a CUDA runtime call failed; see lfa_last_cuda_error() */
+  LFA_ERR_NOT_CONVERGED = 5, /* returned by lfa_get_info() when a symbol hit max_sweeps */
+  LFA_ERR_NONFINITE = 6,     /* returned by lfa_get_info() when a symbol had NaN/Inf */
+  LFA_ERR_TIMEOUT = 7        /* reserved: a bounded device wait ran out */
+} lfa_status_t;
+
+/* One stride-1 periodic convolution layer (Sec. III "Convolutional Mappings"):
+ * weights [c_out][c_in][kh][kw] on an n x m torus, tap origin (pad_h, pad_w),
+ * -1 = floor(k/2). Limits: 1 <= c_out, c_in <= 512; 1 <= kh, kw <= 15;
+ * 1 <= n, m <= 65536; n*m <= 2^31 - 1; 0 <= pad < k or -1. */
+typedef struct lfa_layer_desc {
+  int32_t c_out, c_in, kh, kw, n, m, pad_h, pad_w;
+} lfa_layer_desc_t;
+
+/* Plan flags. */
+#define LFA_VALUES       0x1u  /* singular values (always computed) */
+#define LFA_VECTORS      0x2u  /* also the symbol singular vectors U_k, V_k */
+#define LFA_HALF_OUTPUT  0x4u  /* sigma only on the half grid, [F_h][r] (else full grid [n*m][r]) */
+#define LFA_PLAIN        0x8u  /* plain per-layer path: materialised symbols, one launch per layer
+                                  and stage, no graph (the baseline the batched path is measured
+                                  against) */
+
+/* Options (nullable pointer: defaults). */
+typedef struct lfa_options {
+  float tol;            /* one-sided Jacobi threshold: a pair (p, q) is rotated while
+                           |x_p^H x_q| > tol * ||x_p|| ||x_q||. <= 0: default 2^-22 */
+  int32_t max_sweeps;   /* sweep cap per symbol; <= 0: default 30 */
+  int32_t variant;      /* -1: built-in / autotuned choice; >= 0 forces a kernel variant
+                           (see lfa_variant_name) for every layer it can run */
+  int32_t use_graph;    /* 1 (default if <0): lfa_svd replays a captured CUDA graph */
+  const char* tune_cache; /* nullable path of the autotuner's cache (text); read at plan time */
+} lfa_options_t;
+
+typedef struct lfa_plan_s* lfa_plan_t;
+
+/* Device-side counters of the last lfa_svd on a plan (read by lfa_get_info). */
+typedef struct lfa_info {
+  int64_t symbols;          /* half-grid symbols decomposed per lfa_svd (all layers) */
+  int64_t singular_values;  /* sum over layers of n*m*r (full-grid count) */
+  int64_t unconverged;      /* symbols that reached max_sweeps in the last lfa_svd */
+  int64_t nonfinite;        /* symbols with a non-finite input or result in the last lfa_svd */
+  int64_t sweeps;           /* total sweeps over all symbols in the last lfa_svd */
+  int64_t rotations;        /* total applied 2x2 rotations in the last lfa_svd */
+  int64_t plan_device_bytes;/* device memory owned by the plan */
+  int32_t nlayers;
+  int32_t max_sweeps;
+  float tol;
+} lfa_info_t;
+
+/* Creates a plan for nlayers layers (Algorithm 1's "SVD with LFA(A, m, n)",
+ * applied to a whole network). Builds the twiddle tables T_n[t] = exp(2 pi i t/n)
+ * in fp64 on the host (rounded to fp32), the half-grid work list and the Jacobi
+ * schedules; chooses a kernel variant per layer; allocates the plan's device
+ * memory (the only allocation of the library). flags: LFA_VALUES is implied;
+ * LFA_VECTORS adds U, V; LFA_HALF_OUTPUT; LFA_PLAIN. opt may be NULL.
+ * On success *plan is set; on failure *plan is NULL and nothing leaks.
+ * Errors: LFA_ERR_INVALID_ARG (sizes, flags, NULL plan/layers, nlayers not in
+ * [1, 64]), LFA_ERR_UNSUPPORTED (no CUDA device of compute capability 10.3),
+ * LFA_ERR_OOM, LFA_ERR_CUDA. */
+lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t nlayers,
+                      uint32_t flags, const lfa_options_t* opt);
+
+/* Forward: the SVD of every layer's operator (Sec. III, Algorithm 1).
+ *  w[l]      device float32 [c_out][c_in][kh][kw]                 (input)
+ *  sigma[l]  device float32 [n*m][r], or [F_h][r] with LFA_HALF_OUTPUT (output)
+ *  U[l]      device complex64 [F_h][c_out][r]: U_k for the half-grid frequency k (output,
+ *            required iff the plan has LFA_VECTORS, else ignored and may be NULL)
+ *  V[l]      device complex64 [F_h][c_in][r]: V_k likewise.
+ *            A_k = U_k diag(sigma_k) V_k^*. For the conjugate frequency -k the
+ *            factors are conj(U_k), sigma_k, conj(V_k).
+ * Allocates nothing; asynchronous on `stream`. Errors: LFA_ERR_INVALID_ARG
+ * (NULL plan or pointer), LFA_ERR_CUDA (launch failure). */
+lfa_status_t lfa_svd(lfa_plan_t plan, const float* const* w, float* const* sigma,
+                     float* const* U, float* const* V, void* stream);
+
+/* The symbols themselves (Sec. III, the c_out x c_in matrix A_k) of one layer,
+ * for all half-grid frequencies: out = device complex64 [F_h][c_out][c_in].
+ * Asynchronous. Errors: LFA_ERR_INVALID_ARG. */
+lfa_status_t lfa_symbols(lfa_plan_t plan, int32_t layer, const float* w, float* out, void* stream);
+
+/* Global singular vectors (Sec. III, U^_k = F_k^out U_k, V^_k = F_k^in V_k) of one
+ * layer for the flat indices q in [first, first + count), q = f*r + s over the
+ * FULL grid (f = j*m + l, s = position in descending order):
+ *   u_hat[q - first][o][x1][x2] = U_f[o][s] * exp(2 pi i (j x1/n + l x2/m)) / sqrt(n m)
+ *   v_hat[q - first][i][x1][x2] = V_f[i][s] * exp(2 pi i (j x1/n + l x2/m)) / sqrt(n m)
+ * where U_f = U[h] for a half-grid frequency f (h its position in the half grid) and
+ * U_f = conj(U[h(fc)]) otherwise. U, V: the layer's lfa_svd outputs. u_hat is complex64
+ * [count][c_out][n][m], v_hat complex64 [count][c_in][n][m]; either may be NULL.
+ * Errors: LFA_ERR_INVALID_ARG (range outside [0, n*m*r), plan without LFA_VECTORS). */
+lfa_status_t lfa_expand(lfa_plan_t plan, int32_t layer, const float* U, const float* V,
+                        int64_t first, int64_t count, float* u_hat, float* v_hat, void* stream);
+
+/* Backward: dL/dw from dL/dsigma. For a simple singular value
+ * d(sigma_s) = Re(u_s^* dA_k v_s) and, from the symbol definition,
+ * dA_k/dw[o,i,a,b] = exp(2 pi i <k, y_ab>) e_o e_i^T. Summed over frequencies:
+ *   dw[o,i,a,b] = sum_k Re( G_k[o,i] exp(-2 pi i <k, y_ab>) ),  G_k = U_k diag(g~_k) V_k^*,
+ * over the half grid, with g~_k = g_k + g_{-k} for a conjugate pair and g~_k = g_k for a
+ * self-conjugate k (full-grid dsigma), or g~_k = dsigma_half[k] with LFA_HALF_OUTPUT.
+ * Symbols are not needed (only U, V, dsigma).
+ *  dsigma[l] device float32 in sigma's layout (input)
+ *  U[l], V[l] the lfa_svd outputs of the same w (input)
+ *  dw[l]     device float32 [c_out][c_in][kh][kw], overwritten (output)
+ * Deterministic (fixed reduction order; no float atomics). Requires a plan with
+ * LFA_VECTORS (else LFA_ERR_INVALID_ARG). Asynchronous. */
+lfa_status_t lfa_svd_backward(lfa_plan_t plan, const float* const* dsigma, const float* const* U,
+                              const float* const* V, float* const* dw, void* stream);
+
+/* dL/dsigma of the spectral regulariser L = sum_layers max(sigma) + lam * sum (sigma - 1)^2
+ * (a spectral-norm term plus an orthogonality term) for each layer's sigma in the plan's
+ * sigma layout: dsigma = 2 lam (sigma - 1), plus 1 at the first maximiser (row-major).
+ * The max is attained at both k and -k; they are the same function of w, so one
+ * representative carries the gradient. Also writes the loss value per layer to
+ * loss[l] (device float32 scalar; nullable). Asynchronous. */
+lfa_status_t lfa_regulariser_grad(lfa_plan_t plan, const float* const* sigma, float lam,
+                                  float* const* dsigma, float* const* loss, void* stream);
+
+/* Frees the plan's device memory and the plan. NULL is accepted. Synchronises
+ * the device work the plan issued. */
+lfa_status_t lfa_destroy(lfa_plan_t plan);
+
+/* Copies the counters of the last lfa_svd into *info (synchronises the plan's
+ * last stream). Returns LFA_ERR_NONFINITE if a symbol had NaN/Inf, else
+ * LFA_ERR_NOT_CONVERGED if a symbol hit max_sweeps, else LFA_OK. */
+lfa_status_t lfa_get_info(lfa_plan_t plan, lfa_info_t* info);
+
+/* Per-layer queries: half-grid size F_h, r, the kernel variant chosen, and the
+ * half-grid frequency list (host int32 array of F_h entries, may be NULL). */
+lfa_status_t lfa_layer_query(lfa_plan_t plan, int32_t layer, int64_t* F_h, int32_t* r,
+                             int32_t* variant, int32_t* half_grid);
+
+/* Static strings; never NULL. */
+const char* lfa_status_string(lfa_status_t status);
+const char* lfa_variant_name(int32_t variant);
+/* The last CUDA runtime error seen by the library in this thread (cudaError_t as int). */
+int32_t lfa_last_cuda_error(void);
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int32_t lfa_version(void);
+
+#ifdef __cplusplus
+}  /* extern "C" */
+#endif
+
+#endif  /* LFA_H_ */

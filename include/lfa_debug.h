@@ -1,0 +1,38 @@
+/*
+ * lfa_debug.h -- host-only hooks of the LFA SVD library that expose its plan-time
+ * logic (no device work), so that it can be tested on a machine without a GPU.
+ * The paper has no counterpart of these; they exist for testing the library.
+ */
+#ifndef LFA_DEBUG_H_
+#define LFA_DEBUG_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* The Jacobi pair schedule for ncols (even, 2..1024) columns: one sweep of ncols-1 rounds
+ * of ncols/2 pairs, as (a, b) column ids, written to out[(round*ncols/2 + team)*2 + {0,1}]
+ * when out is not NULL (cap = capacity in uint16 elements). Consecutive rounds share exactly
+ * one column per team, kept in the same slot; every pair occurs once per sweep.
+ * Returns the number of rounds, or a negative value on invalid input (-1), a failed
+ * construction (-2) or a too small buffer (-3). */
+int32_t lfa_debug_schedule(int32_t ncols, uint16_t* out, int64_t cap);
+
+/* The half-grid frequency list of an n x m torus (see lfa.h): writes it to out (cap entries)
+ * when out is not NULL and returns its length F_h, or a negative value on invalid input. */
+int64_t lfa_debug_half_grid(int32_t n, int32_t m, int32_t* out, int64_t cap);
+
+/* The built-in kernel-variant choice for an M x N Jacobi problem (M = max(c_out, c_in),
+ * N = min(c_out, c_in)); -1 if no register-resident variant holds it. */
+int32_t lfa_debug_choose_variant(int32_t M, int32_t N, int32_t vectors);
+
+/* Number of kernel variants (ids 0 .. count-1, named by lfa_variant_name). */
+int32_t lfa_debug_variant_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LFA_DEBUG_H_ */

@@ -1,0 +1,285 @@
+// Auxiliary kernels of the LFA SVD library (arXiv 2506.05617, Sec. III):
+//  * symbol assembly into memory (the plain path and lfa_symbols),
+//  * lifting of symbol singular vectors to global singular vectors,
+//  * the backward pass dL/dw,
+//  * the spectral regulariser's dL/dsigma.
+#include "lfa_internal.cuh"
+
+namespace lfa {
+
+__device__ __forceinline__ int mod_pos(int a, int n) {
+  int r = a % n;
+  return r < 0 ? r + n : r;
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// ----------------------------------------------------------------------------- symbols
+// A_k[o][i] = sum_{a,b} w[o,i,a,b] T_n[j(a-p_h) mod n] T_m[l(b-p_w) mod m] for the
+// half-grid frequencies (symbol definition, Sec. III). One CTA per frequency; the
+// kh x kw phase grid is built once in shared memory; threads stride over (o, i),
+// reading the contiguous kh*kw taps of one (o, i).
+__global__ void __launch_bounds__(256) symbols_kernel(LayerArgs La, float2* out) {
+  __shared__ float2 phs[kMaxTaps];
+  const int h = blockIdx.x;
+  const int f = La.half[h];
+  const int j = f / La.m, l = f - j * La.m;
+  const int kk = La.kh * La.kw;
+  for (int t = threadIdx.x; t < kk; t += blockDim.x) {
+    const int a = t / La.kw, b = t - a * La.kw;
+    phs[t] = cmul(La.tw_n[mod_pos(j * (a - La.ph), La.n)], La.tw_m[mod_pos(l * (b - La.pw), La.m)]);
+  }
+  __syncthreads();
+  const int CC = La.c_out * La.c_in;
+  float2* o = out + (size_t)h * CC;
+  for (int e = threadIdx.x; e < CC; e += blockDim.x) {
+    const float* wp = La.w + (size_t)e * kk;
+    float re = 0.f, im = 0.f;
+    for (int t = 0; t < kk; ++t) {
+      const float wv = __ldg(wp + t);
+      re = fmaf(wv, phs[t].x, re);
+      im = fmaf(wv, phs[t].y, im);
+    }
+    o[e] = make_float2(re, im);
+  }
+}
+
+cudaError_t launch_symbols(const LayerArgs& La, float2* out, cudaStream_t s) {
+  if (La.F_h <= 0) return cudaSuccess;
+  symbols_kernel<<<La.F_h, 256, 0, s>>>(La, out);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------- expansion
+// u_hat[q][c][x1][x2] = U_f[c][s] exp(2 pi i (j x1/n + l x2/m)) / sqrt(nm), q = f*r + s
+// (U^_k = F_k U_k, Sec. III). U_f = U[h] on the half grid, conj(U[h(fc)]) otherwise.
+// One CTA per vector q; threads stride over the c*n*m outputs (x2 fastest: coalesced).
+__device__ int half_index(const int32_t* half, int F_h, int f) {
+  int lo = 0, hi = F_h - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (half[mid] < f) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(256) expand_kernel(LayerArgs La, const float2* U, const float2* V,
+                                                     int64_t first, float2* u_hat, float2* v_hat) {
+  const int64_t q = first + blockIdx.x;
+  const int r = La.r;
+  const int f = (int)(q / r), s = (int)(q - (int64_t)f * r);
+  const int j = f / La.m, l = f - j * La.m;
+  const int fc = ((La.n - j) % La.n) * La.m + (La.m - l) % La.m;
+  const bool conj = fc < f;
+  const int h = half_index(La.half, La.F_h, conj ? fc : f);
+  const int nm = La.n * La.m;
+  const float scale = rsqrtf((float)nm);
+  for (int pass = 0; pass < 2; ++pass) {
+    const float2* Src = pass == 0 ? U : V;
+    float2* dst = pass == 0 ? u_hat : v_hat;
+    const int C = pass == 0 ? La.c_out : La.c_in;
+    if (dst == nullptr || Src == nullptr) continue;
+    const float2* col = Src + (size_t)h * C * r + s;
+    float2* d = dst + (size_t)blockIdx.x * C * nm;
+    for (int e = threadIdx.x; e < C * nm; e += blockDim.x) {
+      const int c = e / nm, x = e - c * nm;
+      const int x1 = x / La.m, x2 = x - x1 * La.m;
+      float2 u = __ldg(col + (size_t)c * r);
+      if (conj) u.y = -u.y;
+      const float2 ph = cmul(La.tw_n[(int)(((int64_t)j * x1) % La.n)],
+                             La.tw_m[(int)(((int64_t)l * x2) % La.m)]);
+      const float2 v = cmul(u, ph);
+      d[e] = make_float2(v.x * scale, v.y * scale);
+    }
+  }
+}
+
+cudaError_t launch_expand(const LayerArgs& La, const float2* U, const float2* V, int64_t first,
+                          int64_t count, float2* u_hat, float2* v_hat, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  if (count > 0x7fffffff) return cudaErrorInvalidValue;
+  expand_kernel<<<(unsigned)count, 256, 0, s>>>(La, U, V, first, u_hat, v_hat);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------- backward
+// Stage 1: G_h = U_h diag(g~_h) V_h^* (c_out x c_in complex) for every half-grid h, with
+// g~ = g_f + g_fc for a conjugate pair, g_f for a self-conjugate f (full-grid dsigma), or the
+// half-grid dsigma as is. Tiled batched complex GEMM over s: 32x32 output tile per CTA,
+// 256 threads x 4 outputs, U/V chunks of 32 singular indices staged in shared memory.
+__global__ void __launch_bounds__(256) backward_g_kernel(LayerArgs La, const float* dsigma,
+                                                         int half_output, const float2* U,
+                                                         const float2* V, int h_begin, float2* G) {
+  __shared__ float2 Us[32][33];
+  __shared__ float2 Vs[32][33];
+  __shared__ float gs[32];
+  const int h = h_begin + blockIdx.z;
+  const int o0 = blockIdx.y * 32, i0 = blockIdx.x * 32;
+  const int r = La.r, co = La.c_out, ci = La.c_in;
+  const int f = La.half[h];
+  const int j = f / La.m, l = f - j * La.m;
+  const int fc = ((La.n - j) % La.n) * La.m + (La.m - l) % La.m;
+  const float* g_f = dsigma + (size_t)(half_output ? h : f) * r;
+  const float* g_c = (!half_output && fc != f) ? dsigma + (size_t)fc * r : nullptr;
+  const float2* Uh = U + (size_t)h * co * r;
+  const float2* Vh = V + (size_t)h * ci * r;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  float2 acc[4] = {};
+  for (int s0 = 0; s0 < r; s0 += 32) {
+    for (int e = threadIdx.x; e < 32 * 32; e += 256) {
+      const int rr = e >> 5, ss = e & 31;
+      const int s = s0 + ss;
+      Us[rr][ss] = (o0 + rr < co && s < r) ? Uh[(size_t)(o0 + rr) * r + s] : make_float2(0.f, 0.f);
+      Vs[rr][ss] = (i0 + rr < ci && s < r) ? Vh[(size_t)(i0 + rr) * r + s] : make_float2(0.f, 0.f);
+    }
+    if (threadIdx.x < 32) {
+      const int s = s0 + threadIdx.x;
+      float g = 0.f;
+      if (s < r) g = g_f[s] + (g_c ? g_c[s] : 0.f);
+      gs[threadIdx.x] = g;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int ss = 0; ss < 32; ++ss) {
+      const float2 v = Vs[tx][ss];
+      const float g = gs[ss];
+      const float2 vg = make_float2(v.x * g, -v.y * g);  // g conj(v)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float2 u = Us[ty + 8 * k][ss];
+        acc[k].x = fmaf(u.x, vg.x, fmaf(-u.y, vg.y, acc[k].x));
+        acc[k].y = fmaf(u.x, vg.y, fmaf(u.y, vg.x, acc[k].y));
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int o = o0 + ty + 8 * k, i = i0 + tx;
+    if (o < co && i < ci) G[((size_t)blockIdx.z * co + o) * ci + i] = acc[k];
+  }
+}
+
+// Stage 2: partial[c][o][i][a][b] = sum_{h in chunk c} Re(G_h[o,i] exp(-2 pi i <k_h, y_ab>)),
+// the phase split into its row and column factors. Thread per (o, i); the chunk's
+// frequencies in a fixed order (deterministic).
+__global__ void __launch_bounds__(128) backward_dw_kernel(LayerArgs La, const float2* G, int g_begin,
+                                                          int chunk, int c_begin, float* partial) {
+  const int CC = La.c_out * La.c_in;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = c_begin + blockIdx.y;
+  if (e >= CC) return;
+  const int kh = La.kh, kw = La.kw;
+  float acc[kMaxTaps];
+#pragma unroll 1
+  for (int t = 0; t < kh * kw; ++t) acc[t] = 0.f;
+  const int h0 = c * chunk, h1 = min(La.F_h, h0 + chunk);
+  for (int h = h0; h < h1; ++h) {
+    const int f = La.half[h];
+    const int j = f / La.m, l = f - j * La.m;
+    const float2 g = G[(size_t)(h - g_begin) * CC + e];
+    for (int a = 0; a < kh; ++a) {
+      const float2 pa = La.tw_n[mod_pos(j * (a - La.ph), La.n)];
+      // G * conj(pa)
+      const float2 ga = make_float2(g.x * pa.x + g.y * pa.y, g.y * pa.x - g.x * pa.y);
+      for (int b = 0; b < kw; ++b) {
+        const float2 pb = La.tw_m[mod_pos(l * (b - La.pw), La.m)];
+        // Re(ga * conj(pb))
+        acc[a * kw + b] += ga.x * pb.x + ga.y * pb.y;
+      }
+    }
+  }
+  float* p = partial + ((size_t)c * CC + e) * (kh * kw);
+  for (int t = 0; t < kh * kw; ++t) p[t] = acc[t];
+}
+
+// Stage 3: dw = sum over chunks in order.
+__global__ void __launch_bounds__(256) backward_reduce_kernel(const float* partial, int chunks,
+                                                              int64_t total, float* dw) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  float s = 0.f;
+  for (int c = 0; c < chunks; ++c) s += partial[(size_t)c * total + e];
+  dw[e] = s;
+}
+
+// G holds g_cap symbols' G_h; the half grid is processed in blocks of whole chunks that fit.
+cudaError_t launch_backward(const LayerArgs& La, const float* dsigma, int half_output,
+                            const float2* U, const float2* V, float2* G, int64_t g_cap, float* partial,
+                            int chunks, float* dw, cudaStream_t s) {
+  if (La.F_h <= 0) return cudaSuccess;
+  const int CC = La.c_out * La.c_in;
+  const int chunk = (La.F_h + chunks - 1) / chunks;
+  chunks = (La.F_h + chunk - 1) / chunk;
+  int per_block = (int)(g_cap / chunk) < 1 ? 1 : (int)(g_cap / chunk);
+  per_block = per_block * chunk > 65535 ? 65535 / chunk : per_block;   // gridDim.z limit
+  if (per_block < 1) return cudaErrorInvalidValue;
+  if ((int64_t)chunk > g_cap) return cudaErrorInvalidValue;
+  cudaError_t e = cudaSuccess;
+  for (int c0 = 0; c0 < chunks; c0 += per_block) {
+    const int c1 = c0 + per_block < chunks ? c0 + per_block : chunks;
+    const int h0 = c0 * chunk;
+    const int h1 = c1 * chunk < La.F_h ? c1 * chunk : La.F_h;
+    dim3 gg((La.c_in + 31) / 32, (La.c_out + 31) / 32, h1 - h0);
+    backward_g_kernel<<<gg, 256, 0, s>>>(La, dsigma, half_output, U, V, h0, G);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dim3 gd((CC + 127) / 128, c1 - c0);
+    backward_dw_kernel<<<gd, 128, 0, s>>>(La, G, h0, chunk, c0, partial);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  const int64_t total = (int64_t)CC * La.kh * La.kw;
+  backward_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(partial, chunks, total, dw);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------- regulariser
+// loss = max(sigma) + lam * sum (sigma - 1)^2; dsigma = 2 lam (sigma - 1) + [first argmax].
+// One CTA of 1024 threads per layer; fixed-order tree reductions (deterministic).
+__global__ void __launch_bounds__(1024) regulariser_kernel(const float* sigma, int64_t count, float lam,
+                                                           float* dsigma, float* loss) {
+  __shared__ float smax[32];
+  __shared__ long long sidx[32];
+  __shared__ float ssum[32];
+  float best = -1.f;
+  long long bi = 0x7fffffffffffffffll;
+  float sum = 0.f;
+  for (int64_t e = threadIdx.x; e < count; e += blockDim.x) {
+    const float v = sigma[e];
+    if (v > best) { best = v; bi = e; }
+    const float d = v - 1.f;
+    sum = fmaf(d, d, sum);
+    dsigma[e] = 2.f * lam * d;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const float ob = __shfl_xor_sync(0xffffffffu, best, off);
+    const long long oi = __shfl_xor_sync(0xffffffffu, bi, off);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    sum += __shfl_xor_sync(0xffffffffu, sum, off);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { smax[w] = best; sidx[w] = bi; ssum[w] = sum; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float b = -1.f, s = 0.f;
+    long long ix = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      if (smax[i] > b || (smax[i] == b && sidx[i] < ix)) { b = smax[i]; ix = sidx[i]; }
+      s += ssum[i];
+    }
+    if (count > 0) dsigma[ix] += 1.f;
+    if (loss) *loss = b + lam * s;
+  }
+}
+
+cudaError_t launch_regulariser(const LayerArgs& La, int half_output, const float* sigma, float lam,
+                               float* dsigma, float* loss, cudaStream_t s) {
+  const int64_t count = (int64_t)(half_output ? La.F_h : La.n * La.m) * La.r;
+  regulariser_kernel<<<1, 1024, 0, s>>>(sigma, count, lam, dsigma, loss);
+  return cudaGetLastError();
+}
+
+}  // namespace lfa

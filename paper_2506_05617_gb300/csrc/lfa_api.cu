@@ -1,0 +1,675 @@
+// Host implementation of the C ABI declared in include/lfa.h (LFA SVD of periodic
+// convolutions, arXiv 2506.05617). Plans own tables, counters and workspace; all
+// per-call buffers belong to the caller.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <functional>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lfa.h"
+#include "../../include/lfa_debug.h"
+#include "jacobi_variants.cuh"
+#include "lfa_internal.cuh"
+
+using namespace lfa;
+
+namespace {
+
+thread_local int32_t g_last_cuda_error = 0;
+
+lfa_status_t from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return LFA_OK;
+  g_last_cuda_error = (int32_t)e;
+  if (e == cudaErrorMemoryAllocation) return LFA_ERR_OOM;
+  return LFA_ERR_CUDA;
+}
+
+#define LFA_CUDA_TRY(expr)                          \
+  do {                                              \
+    cudaError_t _e = (expr);                        \
+    if (_e != cudaSuccess) return from_cuda(_e);    \
+  } while (0)
+
+// Host fault injection for failure-detection tests: LFA_FAULT_INJECT=alloc|launch|nonconverge.
+bool fault(const char* what) {
+  const char* v = std::getenv("LFA_FAULT_INJECT");
+  return v != nullptr && std::strstr(v, what) != nullptr;
+}
+
+// --------------------------------------------------------------------------- half grid
+// Frequencies f = j*m + l with f <= fc, fc the index of -k; increasing order.
+void build_half_grid(int n, int m, std::vector<int32_t>& out) {
+  out.clear();
+  for (int j = 0; j < n; ++j)
+    for (int l = 0; l < m; ++l) {
+      const int f = j * m + l;
+      const int fc = ((n - j) % n) * m + (m - l) % m;
+      if (f <= fc) out.push_back(f);
+    }
+}
+
+// --------------------------------------------------------------------------- schedule
+// Circle-method round robin over NC columns (NC even): round t pairs the fixed column
+// NC-1 with t, and (t+i) with (t-i) mod NC-1 for i = 1 .. NC/2-1. Teams are relabelled
+// between consecutive rounds of a sweep by a bipartite matching so that every team keeps
+// one column (in its slot) and receives one. Returns false if a matching fails.
+bool build_schedule(int NC, std::vector<ushort2>& out) {
+  const int NP = NC / 2, Cn = NC - 1;
+  auto round_pairs = [&](int t, std::vector<std::pair<int, int>>& pr) {
+    pr.clear();
+    pr.push_back({NC - 1, t % Cn});
+    for (int i = 1; i < NP; ++i) pr.push_back({(t + i) % Cn, ((t - i) % Cn + Cn) % Cn});
+  };
+  std::vector<std::pair<int, int>> teams, pr;
+  round_pairs(0, teams);
+  out.assign((size_t)Cn * NP, ushort2{0, 0});
+  for (int k = 0; k < NP; ++k) out[k] = ushort2{(unsigned short)teams[k].first, (unsigned short)teams[k].second};
+  for (int t = 1; t < Cn; ++t) {
+    round_pairs(t, pr);
+    auto shares = [&](int k, int i) {
+      const int a = teams[k].first, b = teams[k].second;
+      const int c = (pr[i].first == a || pr[i].first == b) + (pr[i].second == a || pr[i].second == b);
+      return c == 1;
+    };
+    std::vector<int> match_p(NP, -1);
+    std::vector<char> seen;
+    std::function<bool(int)> aug = [&](int k) -> bool {
+      for (int i = 0; i < NP; ++i) {
+        if (seen[i] || !shares(k, i)) continue;
+        seen[i] = 1;
+        if (match_p[i] < 0 || aug(match_p[i])) { match_p[i] = k; return true; }
+      }
+      return false;
+    };
+    for (int k = 0; k < NP; ++k) {
+      seen.assign(NP, 0);
+      if (!aug(k)) return false;
+    }
+    std::vector<std::pair<int, int>> nt(NP);
+    for (int i = 0; i < NP; ++i) {
+      const int k = match_p[i];
+      int a = teams[k].first, b = teams[k].second;
+      const int p = pr[i].first, q = pr[i].second;
+      if (a == p || a == q) b = (a == p) ? q : p;   // keep a in slot 0
+      else a = (b == p) ? q : p;                     // keep b in slot 1
+      nt[k] = {a, b};
+    }
+    teams = nt;
+    for (int k = 0; k < NP; ++k)
+      out[(size_t)t * NP + k] = ushort2{(unsigned short)teams[k].first, (unsigned short)teams[k].second};
+  }
+  // every pair exactly once per sweep
+  std::vector<char> hit((size_t)NC * NC, 0);
+  for (int t = 0; t < Cn; ++t)
+    for (int k = 0; k < NP; ++k) {
+      const int a = out[(size_t)t * NP + k].x, b = out[(size_t)t * NP + k].y;
+      if (a == b || a >= NC || b >= NC) return false;
+      const size_t idx = (size_t)std::min(a, b) * NC + std::max(a, b);
+      if (hit[idx]) return false;
+      hit[idx] = 1;
+    }
+  return true;
+}
+
+// --------------------------------------------------------------------------- variants
+struct VDesc { int NP, L, MR, WR; };
+const VDesc kVariants[] = {
+#define LFA_VD(id, NP, L, MR, WR) {NP, L, MR, WR},
+    LFA_JACOBI_VARIANTS(LFA_VD)
+#undef LFA_VD
+};
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+const char* kVariantNames[] = {
+#define LFA_VN(id, NP, L, MR, WR) "reg_np" #NP "_l" #L "_mr" #MR "_wr" #WR,
+    LFA_JACOBI_VARIANTS(LFA_VN)
+#undef LFA_VN
+};
+
+int variant_rows(int v) { return kVariants[v].MR * kVariants[v].L; }
+int variant_cols(int v, bool vec) {
+  const int c = 2 * kVariants[v].NP;
+  return vec ? std::min(c, kVariants[v].WR * kVariants[v].L) : c;
+}
+bool variant_fits(int v, int M, int N, bool vec) {
+  return v >= 0 && v < kNumVariants && M <= variant_rows(v) && N <= variant_cols(v, vec);
+}
+// Default choice: the smallest padded problem (2*NP columns x MR*L rows) that holds M x N;
+// ties go to the larger team (more lanes per pair, fewer registers per lane).
+int choose_variant(int M, int N, bool vec) {
+  int best = -1;
+  long best_area = 0;
+  for (int v = 0; v < kNumVariants; ++v) {
+    if (!variant_fits(v, M, N, vec)) continue;
+    const long area = (long)(2 * kVariants[v].NP) * variant_rows(v);
+    if (best < 0 || area < best_area || (area == best_area && kVariants[v].L > kVariants[best].L)) {
+      best = v;
+      best_area = area;
+    }
+  }
+  return best;
+}
+
+cudaError_t vprepare(int id, bool vec, bool fused) {
+  if (vec && fused) return jacobi_vec_fused_prepare(id);
+  if (!vec && fused) return jacobi_val_fused_prepare(id);
+  if (!vec && !fused) return jacobi_val_plain_prepare(id);
+  return cudaErrorInvalidValue;
+}
+cudaError_t voccupancy(int id, bool vec, bool fused, int* b) {
+  if (vec && fused) return jacobi_vec_fused_occupancy(id, b);
+  if (!vec && fused) return jacobi_val_fused_occupancy(id, b);
+  if (!vec && !fused) return jacobi_val_plain_occupancy(id, b);
+  return cudaErrorInvalidValue;
+}
+cudaError_t vlaunch(int id, bool vec, bool fused, const JacobiLaunch& P, int grid, cudaStream_t s) {
+  if (vec && fused) return jacobi_vec_fused_launch(id, P, grid, s);
+  if (!vec && fused) return jacobi_val_fused_launch(id, P, grid, s);
+  if (!vec && !fused) return jacobi_val_plain_launch(id, P, grid, s);
+  return cudaErrorInvalidValue;
+}
+int variant_spu(int id) {
+  const int T = kVariants[id].NP * kVariants[id].L;
+  return T <= 32 ? 32 / T : 1;
+}
+
+// Optional autotuner cache: text lines "M N vec variant" (first match wins).
+int tuned_variant(const char* path, int M, int N, bool vec) {
+  if (path == nullptr || path[0] == 0) return -1;
+  FILE* fh = std::fopen(path, "r");
+  if (!fh) return -1;
+  int m, n, v, id, found = -1;
+  char line[256];
+  while (std::fgets(line, sizeof line, fh)) {
+    if (line[0] == '#') continue;
+    if (std::sscanf(line, "%d %d %d %d", &m, &n, &v, &id) == 4 && m == M && n == N && (v != 0) == vec) {
+      found = id;
+      break;
+    }
+  }
+  std::fclose(fh);
+  return variant_fits(found, M, N, vec) ? found : -1;
+}
+
+}  // namespace
+
+// ============================================================================= plan
+struct lfa_plan_s {
+  int nlayers = 0;
+  uint32_t flags = 0;
+  bool vec = false, half_output = false, plain = false, use_graph = true;
+  int max_sweeps = 30;
+  float tol_opt = 0.f;
+  int device = 0, sms = 0;
+  std::vector<lfa_layer_desc_t> desc;
+  std::vector<LayerArgs> args;        // device table pointers filled, per-call pointers not
+  std::vector<int> variant;           // per layer
+  std::vector<std::vector<int32_t>> half_host;
+  // variant groups: one persistent launch each
+  struct Group { int variant; std::vector<int> layers; int items; int grid; };
+  std::vector<Group> groups;
+  std::vector<const ushort2*> sched_dev;  // per variant id (NC) or null
+  // device memory
+  void* dmem = nullptr;
+  size_t dbytes = 0;
+  Counters* counters = nullptr;
+  float2* sym_ws = nullptr;  // plain path symbols [F_h][c_out][c_in] (largest layer)
+  float2* g_ws = nullptr;    // backward G workspace
+  int64_t g_cap_bytes = 0;
+  float* partial_ws = nullptr;
+  std::vector<int> bw_chunks;      // per layer
+  // graph cache
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<const void*> graph_key;
+  cudaStream_t last_stream = nullptr;
+};
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+lfa_status_t validate_layer(const lfa_layer_desc_t& d) {
+  if (d.c_out < 1 || d.c_in < 1 || d.c_out > 512 || d.c_in > 512) return LFA_ERR_INVALID_ARG;
+  if (d.kh < 1 || d.kw < 1 || d.kh > 15 || d.kw > 15) return LFA_ERR_INVALID_ARG;
+  if (d.n < 1 || d.m < 1 || d.n > 65536 || d.m > 65536) return LFA_ERR_INVALID_ARG;
+  if ((int64_t)d.n * d.m > 0x7fffffffLL) return LFA_ERR_INVALID_ARG;
+  if (d.pad_h < -1 || d.pad_h >= d.kh || d.pad_w < -1 || d.pad_w >= d.kw) return LFA_ERR_INVALID_ARG;
+  return LFA_OK;
+}
+
+float default_tol(int M) {
+  const float t = 4.f * std::sqrt((float)M) * std::ldexp(1.f, -24);
+  return std::max(t, std::ldexp(1.f, -22));
+}
+
+void free_plan(lfa_plan_s* p) {
+  if (!p) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  if (p->dmem) cudaFree(p->dmem);
+  delete p;
+}
+
+// Enqueue the forward work of one call on stream s (used directly or under capture).
+lfa_status_t enqueue_forward(lfa_plan_s* p, const float* const* w, float* const* sigma,
+                             float* const* U, float* const* V, cudaStream_t s) {
+  LFA_CUDA_TRY(cudaMemsetAsync(p->counters, 0, sizeof(Counters), s));
+  if (fault("launch")) return from_cuda(cudaErrorLaunchFailure);
+  if (p->plain) {
+    // plain per-layer path: materialise the symbols, then one Jacobi launch per layer
+    for (int l = 0; l < p->nlayers; ++l) {
+      LayerArgs La = p->args[l];
+      La.w = w[l];
+      La.sigma = sigma[l];
+      La.symbols = p->sym_ws;
+      La.item_begin = 0;
+      LFA_CUDA_TRY(launch_symbols(La, p->sym_ws, s));
+      JacobiLaunch P{};
+      P.L[0] = La;
+      P.nlayers = 1;
+      const int spu = variant_spu(p->variant[l]);
+      P.total_items = (La.F_h + spu - 1) / spu;
+      P.sched = p->sched_dev[p->variant[l]];
+      P.max_sweeps = p->max_sweeps;
+      P.half_output = p->half_output;
+      P.queue_slot = l % 16;
+      P.counters = p->counters;
+      int occ = 1;
+      LFA_CUDA_TRY(voccupancy(p->variant[l], false, false, &occ));
+      const int grid = std::max(1, std::min(P.total_items, occ * p->sms));
+      if (l >= 16) LFA_CUDA_TRY(cudaMemsetAsync(&p->counters->queue[l % 16], 0, sizeof(unsigned), s));
+      LFA_CUDA_TRY(vlaunch(p->variant[l], false, false, P, grid, s));
+    }
+    return LFA_OK;
+  }
+  int slot = 0;
+  for (const auto& g : p->groups) {
+    JacobiLaunch P{};
+    int items = 0;
+    for (size_t k = 0; k < g.layers.size(); ++k) {
+      const int l = g.layers[k];
+      LayerArgs La = p->args[l];
+      La.w = w[l];
+      La.sigma = sigma[l];
+      La.U = p->vec ? reinterpret_cast<float2*>(U[l]) : nullptr;
+      La.V = p->vec ? reinterpret_cast<float2*>(V[l]) : nullptr;
+      La.item_begin = items;
+      P.L[k] = La;
+      items += (La.F_h + variant_spu(g.variant) - 1) / variant_spu(g.variant);
+    }
+    P.nlayers = (int)g.layers.size();
+    P.total_items = items;
+    P.sched = p->sched_dev[g.variant];
+    P.max_sweeps = p->max_sweeps;
+    P.half_output = p->half_output;
+    P.queue_slot = slot++;
+    P.counters = p->counters;
+    LFA_CUDA_TRY(vlaunch(g.variant, p->vec, true, P, g.grid, s));
+  }
+  return LFA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t nlayers,
+                      uint32_t flags, const lfa_options_t* opt) {
+  if (plan == nullptr) return LFA_ERR_INVALID_ARG;
+  *plan = nullptr;
+  if (layers == nullptr || nlayers < 1 || nlayers > kMaxLayers) return LFA_ERR_INVALID_ARG;
+  if (flags & ~(uint32_t)(LFA_VALUES | LFA_VECTORS | LFA_HALF_OUTPUT | LFA_PLAIN)) return LFA_ERR_INVALID_ARG;
+  if ((flags & LFA_PLAIN) && (flags & LFA_VECTORS)) return LFA_ERR_INVALID_ARG;  // plain = values only
+  for (int l = 0; l < nlayers; ++l) {
+    lfa_status_t st = validate_layer(layers[l]);
+    if (st != LFA_OK) return st;
+  }
+  if (opt && (opt->max_sweeps > 1000 || !(opt->tol < 1.f))) return LFA_ERR_INVALID_ARG;
+  if (fault("alloc")) return LFA_ERR_OOM;
+
+  int dev = 0;
+  LFA_CUDA_TRY(cudaGetDevice(&dev));
+  cudaDeviceProp prop;
+  LFA_CUDA_TRY(cudaGetDeviceProperties(&prop, dev));
+  if (prop.major != 10 || prop.minor != 3) return LFA_ERR_UNSUPPORTED;
+
+  lfa_plan_s* p = new (std::nothrow) lfa_plan_s();
+  if (!p) return LFA_ERR_OOM;
+  p->nlayers = nlayers;
+  p->flags = flags;
+  p->vec = (flags & LFA_VECTORS) != 0;
+  p->half_output = (flags & LFA_HALF_OUTPUT) != 0;
+  p->plain = (flags & LFA_PLAIN) != 0;
+  p->max_sweeps = (opt && opt->max_sweeps > 0) ? opt->max_sweeps : 30;
+  if (fault("nonconverge")) p->max_sweeps = 1;
+  p->tol_opt = opt ? opt->tol : 0.f;
+  p->use_graph = !(opt && opt->use_graph == 0) && !p->plain;
+  p->device = dev;
+  p->sms = prop.multiProcessorCount;
+  p->desc.assign(layers, layers + nlayers);
+  p->args.resize(nlayers);
+  p->variant.resize(nlayers);
+  p->half_host.resize(nlayers);
+  p->bw_chunks.resize(nlayers);
+
+  // ---- per-layer host tables and variant choice
+  size_t bytes = align256(sizeof(Counters));
+  std::vector<size_t> off_half(nlayers), off_twn(nlayers), off_twm(nlayers);
+  size_t sym_bytes = 0, g_need = 0, part_bytes = 0;
+  std::vector<char> need_sched(kNumVariants, 0);
+  for (int l = 0; l < nlayers; ++l) {
+    const lfa_layer_desc_t& d = layers[l];
+    LayerArgs& La = p->args[l];
+    std::memset(&La, 0, sizeof La);
+    La.c_out = d.c_out; La.c_in = d.c_in; La.kh = d.kh; La.kw = d.kw; La.n = d.n; La.m = d.m;
+    La.ph = d.pad_h < 0 ? d.kh / 2 : d.pad_h;
+    La.pw = d.pad_w < 0 ? d.kw / 2 : d.pad_w;
+    La.r = std::min(d.c_out, d.c_in);
+    La.wide = d.c_in > d.c_out ? 1 : 0;
+    La.M = std::max(d.c_out, d.c_in);
+    La.N = La.r;
+    build_half_grid(d.n, d.m, p->half_host[l]);
+    La.F_h = (int)p->half_host[l].size();
+    const float tol = p->tol_opt > 0.f ? p->tol_opt : default_tol(La.M);
+    La.tol2 = tol * tol;
+    int v = -1;
+    if (opt && opt->variant >= 0 && variant_fits(opt->variant, La.M, La.N, p->vec)) v = opt->variant;
+    if (v < 0) v = tuned_variant(opt ? opt->tune_cache : nullptr, La.M, La.N, p->vec);
+    if (v < 0) v = choose_variant(La.M, La.N, p->vec);
+    if (v < 0) { free_plan(p); return LFA_ERR_UNSUPPORTED; }
+    p->variant[l] = v;
+    need_sched[v] = 1;
+    off_half[l] = bytes; bytes += align256((size_t)La.F_h * 4);
+    off_twn[l] = bytes; bytes += align256((size_t)d.n * 8);
+    off_twm[l] = bytes; bytes += align256((size_t)d.m * 8);
+    const size_t CC = (size_t)d.c_out * d.c_in;
+    if (p->plain) sym_bytes = std::max(sym_bytes, (size_t)La.F_h * CC * 8);
+    if (p->vec) g_need = std::max(g_need, (size_t)La.F_h * CC * 8);
+  }
+  // backward workspace: G for at most 256 MB worth of symbols (at least one chunk)
+  const size_t g_budget = (size_t)256 << 20;
+  size_t g_bytes = 0;
+  if (p->vec) {
+    g_bytes = std::min(g_need, g_budget);
+    for (int l = 0; l < nlayers; ++l) {
+      const LayerArgs& La = p->args[l];
+      const int64_t CC = (int64_t)La.c_out * La.c_in;
+      const int64_t cap = std::max<int64_t>(1, (int64_t)(g_bytes / (CC * 8)));
+      int64_t chunks = std::max<int64_t>((155648 + CC - 1) / CC, (La.F_h + cap - 1) / cap);
+      chunks = std::min<int64_t>(std::min<int64_t>(chunks, La.F_h), 4096);
+      int64_t chunk = std::min<int64_t>((La.F_h + chunks - 1) / chunks, 65535);
+      chunks = (La.F_h + chunk - 1) / chunk;
+      g_bytes = std::max(g_bytes, (size_t)(chunk * CC * 8));
+      p->bw_chunks[l] = (int)chunks;
+      part_bytes = std::max(part_bytes, (size_t)(chunks * CC * La.kh * La.kw * 4));
+    }
+  }
+  std::vector<std::vector<ushort2>> sched(kNumVariants);
+  std::vector<size_t> off_sched(kNumVariants, 0);
+  for (int v = 0; v < kNumVariants; ++v) {
+    if (!need_sched[v]) continue;
+    if (!build_schedule(2 * kVariants[v].NP, sched[v])) { free_plan(p); return LFA_ERR_UNSUPPORTED; }
+    off_sched[v] = bytes;
+    bytes += align256(sched[v].size() * sizeof(ushort2));
+  }
+  const size_t off_sym = bytes; bytes += align256(sym_bytes);
+  const size_t off_g = bytes; bytes += align256(g_bytes);
+  const size_t off_part = bytes; bytes += align256(part_bytes);
+
+  cudaError_t e = cudaMalloc(&p->dmem, bytes);
+  if (e != cudaSuccess) { free_plan(p); return from_cuda(e); }
+  p->dbytes = bytes;
+  char* base = static_cast<char*>(p->dmem);
+  p->counters = reinterpret_cast<Counters*>(base);
+  p->sym_ws = sym_bytes ? reinterpret_cast<float2*>(base + off_sym) : nullptr;
+  p->g_ws = g_bytes ? reinterpret_cast<float2*>(base + off_g) : nullptr;
+  p->g_cap_bytes = (int64_t)g_bytes;
+  p->partial_ws = part_bytes ? reinterpret_cast<float*>(base + off_part) : nullptr;
+
+  // ---- upload tables (synchronous, plan time only)
+  std::vector<float2> tw;
+  auto twiddles = [&](int n) {
+    tw.resize(n);
+    for (int t = 0; t < n; ++t) {
+      // exp(2 pi i t / n) in fp64 with exact integer reduction, rounded to fp32 once
+      const double ang = 6.283185307179586476925286766559 * (double)t / (double)n;
+      tw[t] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+  };
+  for (int l = 0; l < nlayers && e == cudaSuccess; ++l) {
+    LayerArgs& La = p->args[l];
+    La.half = reinterpret_cast<const int32_t*>(base + off_half[l]);
+    La.tw_n = reinterpret_cast<const float2*>(base + off_twn[l]);
+    La.tw_m = reinterpret_cast<const float2*>(base + off_twm[l]);
+    e = cudaMemcpy(base + off_half[l], p->half_host[l].data(), (size_t)La.F_h * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) break;
+    twiddles(La.n);
+    e = cudaMemcpy(base + off_twn[l], tw.data(), (size_t)La.n * 8, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) break;
+    twiddles(La.m);
+    e = cudaMemcpy(base + off_twm[l], tw.data(), (size_t)La.m * 8, cudaMemcpyHostToDevice);
+  }
+  p->sched_dev.assign(kNumVariants, nullptr);
+  for (int v = 0; v < kNumVariants && e == cudaSuccess; ++v) {
+    if (!need_sched[v]) continue;
+    e = cudaMemcpy(base + off_sched[v], sched[v].data(), sched[v].size() * sizeof(ushort2),
+                   cudaMemcpyHostToDevice);
+    p->sched_dev[v] = reinterpret_cast<const ushort2*>(base + off_sched[v]);
+  }
+  if (e == cudaSuccess) e = cudaMemset(p->counters, 0, sizeof(Counters));
+  // ---- variant groups (one persistent launch per variant) and kernel attributes
+  for (int v = 0; v < kNumVariants && e == cudaSuccess; ++v) {
+    lfa_plan_s::Group g;
+    g.variant = v;
+    g.items = 0;
+    for (int l = 0; l < nlayers; ++l)
+      if (p->variant[l] == v) {
+        g.layers.push_back(l);
+        g.items += (p->args[l].F_h + variant_spu(v) - 1) / variant_spu(v);
+      }
+    if (g.layers.empty()) continue;
+    const bool fused = !p->plain;
+    e = vprepare(v, p->vec, fused);
+    if (e != cudaSuccess) break;
+    int occ = 0;
+    e = voccupancy(v, p->vec, fused, &occ);
+    if (e != cudaSuccess) break;
+    if (occ < 1) { e = cudaErrorInvalidConfiguration; break; }
+    g.grid = std::max(1, std::min(g.items, occ * p->sms));
+    p->groups.push_back(g);
+  }
+  if (e == cudaSuccess && p->groups.size() > 16) e = cudaErrorInvalidValue;
+  if (e == cudaSuccess && p->use_graph) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) { free_plan(p); return from_cuda(e); }
+  *plan = p;
+  return LFA_OK;
+}
+
+lfa_status_t lfa_svd(lfa_plan_t p, const float* const* w, float* const* sigma, float* const* U,
+                     float* const* V, void* stream) {
+  if (p == nullptr || w == nullptr || sigma == nullptr) return LFA_ERR_INVALID_ARG;
+  if (p->vec && (U == nullptr || V == nullptr)) return LFA_ERR_INVALID_ARG;
+  for (int l = 0; l < p->nlayers; ++l) {
+    if (w[l] == nullptr || sigma[l] == nullptr) return LFA_ERR_INVALID_ARG;
+    if (p->vec && (U[l] == nullptr || V[l] == nullptr)) return LFA_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  p->last_stream = s;
+  if (!p->use_graph) return enqueue_forward(p, w, sigma, U, V, s);
+  // graph path: capture once per distinct set of buffers, then replay
+  std::vector<const void*> key;
+  key.reserve(4 * p->nlayers);
+  for (int l = 0; l < p->nlayers; ++l) {
+    key.push_back(w[l]);
+    key.push_back(sigma[l]);
+    key.push_back(p->vec ? U[l] : nullptr);
+    key.push_back(p->vec ? V[l] : nullptr);
+  }
+  if (p->exec == nullptr || key != p->graph_key) {
+    if (p->exec) { cudaGraphExecDestroy(p->exec); p->exec = nullptr; }
+    if (p->graph) { cudaGraphDestroy(p->graph); p->graph = nullptr; }
+    LFA_CUDA_TRY(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+    lfa_status_t st = enqueue_forward(p, w, sigma, U, V, p->cap_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(p->cap_stream, &g);
+    if (st != LFA_OK) { if (g) cudaGraphDestroy(g); return st; }
+    if (e != cudaSuccess) return from_cuda(e);
+    p->graph = g;
+    e = cudaGraphInstantiate(&p->exec, g, 0);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); p->graph = nullptr; p->exec = nullptr; return from_cuda(e); }
+    p->graph_key = key;
+  }
+  return from_cuda(cudaGraphLaunch(p->exec, s));
+}
+
+lfa_status_t lfa_symbols(lfa_plan_t p, int32_t layer, const float* w, float* out, void* stream) {
+  if (p == nullptr || w == nullptr || out == nullptr || layer < 0 || layer >= p->nlayers)
+    return LFA_ERR_INVALID_ARG;
+  LayerArgs La = p->args[layer];
+  La.w = w;
+  return from_cuda(launch_symbols(La, reinterpret_cast<float2*>(out), static_cast<cudaStream_t>(stream)));
+}
+
+lfa_status_t lfa_expand(lfa_plan_t p, int32_t layer, const float* U, const float* V, int64_t first,
+                        int64_t count, float* u_hat, float* v_hat, void* stream) {
+  if (p == nullptr || layer < 0 || layer >= p->nlayers || !p->vec) return LFA_ERR_INVALID_ARG;
+  const LayerArgs& La = p->args[layer];
+  const int64_t total = (int64_t)La.n * La.m * La.r;
+  if (first < 0 || count < 0 || first + count > total || count > 0x7fffffff) return LFA_ERR_INVALID_ARG;
+  if ((u_hat && !U) || (v_hat && !V)) return LFA_ERR_INVALID_ARG;
+  return from_cuda(launch_expand(La, reinterpret_cast<const float2*>(U), reinterpret_cast<const float2*>(V),
+                                 first, count, reinterpret_cast<float2*>(u_hat),
+                                 reinterpret_cast<float2*>(v_hat), static_cast<cudaStream_t>(stream)));
+}
+
+lfa_status_t lfa_svd_backward(lfa_plan_t p, const float* const* dsigma, const float* const* U,
+                              const float* const* V, float* const* dw, void* stream) {
+  if (p == nullptr || !p->vec || dsigma == nullptr || U == nullptr || V == nullptr || dw == nullptr)
+    return LFA_ERR_INVALID_ARG;
+  for (int l = 0; l < p->nlayers; ++l)
+    if (!dsigma[l] || !U[l] || !V[l] || !dw[l]) return LFA_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int l = 0; l < p->nlayers; ++l) {
+    const LayerArgs& La = p->args[l];
+    const int64_t CC = (int64_t)La.c_out * La.c_in;
+    const int64_t g_cap = p->g_cap_bytes / (CC * 8);
+    LFA_CUDA_TRY(launch_backward(La, dsigma[l], p->half_output, reinterpret_cast<const float2*>(U[l]),
+                                 reinterpret_cast<const float2*>(V[l]), p->g_ws, g_cap, p->partial_ws,
+                                 p->bw_chunks[l], dw[l], s));
+  }
+  return LFA_OK;
+}
+
+lfa_status_t lfa_regulariser_grad(lfa_plan_t p, const float* const* sigma, float lam,
+                                  float* const* dsigma, float* const* loss, void* stream) {
+  if (p == nullptr || sigma == nullptr || dsigma == nullptr || !std::isfinite(lam)) return LFA_ERR_INVALID_ARG;
+  for (int l = 0; l < p->nlayers; ++l)
+    if (!sigma[l] || !dsigma[l]) return LFA_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int l = 0; l < p->nlayers; ++l)
+    LFA_CUDA_TRY(launch_regulariser(p->args[l], p->half_output, sigma[l], lam, dsigma[l],
+                                    loss ? loss[l] : nullptr, s));
+  return LFA_OK;
+}
+
+lfa_status_t lfa_destroy(lfa_plan_t p) {
+  if (p == nullptr) return LFA_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  free_plan(p);
+  return from_cuda(e);
+}
+
+lfa_status_t lfa_get_info(lfa_plan_t p, lfa_info_t* info) {
+  if (p == nullptr || info == nullptr) return LFA_ERR_INVALID_ARG;
+  LFA_CUDA_TRY(cudaStreamSynchronize(p->last_stream));
+  Counters c;
+  LFA_CUDA_TRY(cudaMemcpy(&c, p->counters, sizeof c, cudaMemcpyDeviceToHost));
+  std::memset(info, 0, sizeof *info);
+  for (int l = 0; l < p->nlayers; ++l) {
+    info->symbols += p->args[l].F_h;
+    info->singular_values += (int64_t)p->args[l].n * p->args[l].m * p->args[l].r;
+  }
+  info->unconverged = (int64_t)c.unconverged;
+  info->nonfinite = (int64_t)c.nonfinite;
+  info->sweeps = (int64_t)c.sweeps;
+  info->rotations = (int64_t)c.rotations;
+  info->plan_device_bytes = (int64_t)p->dbytes;
+  info->nlayers = p->nlayers;
+  info->max_sweeps = p->max_sweeps;
+  info->tol = p->tol_opt > 0.f ? p->tol_opt : default_tol(p->args[0].M);
+  if (c.nonfinite) return LFA_ERR_NONFINITE;
+  if (c.unconverged) return LFA_ERR_NOT_CONVERGED;
+  return LFA_OK;
+}
+
+lfa_status_t lfa_layer_query(lfa_plan_t p, int32_t layer, int64_t* F_h, int32_t* r, int32_t* variant,
+                             int32_t* half_grid) {
+  if (p == nullptr || layer < 0 || layer >= p->nlayers) return LFA_ERR_INVALID_ARG;
+  if (F_h) *F_h = p->args[layer].F_h;
+  if (r) *r = p->args[layer].r;
+  if (variant) *variant = p->variant[layer];
+  if (half_grid) std::memcpy(half_grid, p->half_host[layer].data(), p->half_host[layer].size() * 4);
+  return LFA_OK;
+}
+
+const char* lfa_status_string(lfa_status_t s) {
+  switch (s) {
+    case LFA_OK: return "ok";
+    case LFA_ERR_INVALID_ARG: return "invalid argument";
+    case LFA_ERR_UNSUPPORTED: return "unsupported";
+    case LFA_ERR_OOM: return "out of memory";
+    case LFA_ERR_CUDA: return "CUDA error";
+    case LFA_ERR_NOT_CONVERGED: return "a symbol did not converge";
+    case LFA_ERR_NONFINITE: return "non-finite input or result";
+    case LFA_ERR_TIMEOUT: return "timeout";
+  }
+  return "unknown status";
+}
+
+const char* lfa_variant_name(int32_t v) {
+  if (v < 0 || v >= kNumVariants) return "none";
+  return kVariantNames[v];
+}
+
+int32_t lfa_last_cuda_error(void) { return g_last_cuda_error; }
+int32_t lfa_version(void) { return 100; }
+
+// ----------------------------------------------------------------------------- host-logic hooks
+int32_t lfa_debug_schedule(int32_t ncols, uint16_t* out, int64_t cap) {
+  if (ncols < 2 || (ncols & 1) || ncols > 1024) return -1;
+  std::vector<ushort2> s;
+  if (!build_schedule(ncols, s)) return -2;
+  if (out) {
+    if ((int64_t)s.size() * 2 > cap) return -3;
+    for (size_t i = 0; i < s.size(); ++i) { out[2 * i] = s[i].x; out[2 * i + 1] = s[i].y; }
+  }
+  return ncols - 1;
+}
+
+int64_t lfa_debug_half_grid(int32_t n, int32_t m, int32_t* out, int64_t cap) {
+  if (n < 1 || m < 1 || (int64_t)n * m > 0x7fffffffLL) return -1;
+  std::vector<int32_t> h;
+  build_half_grid(n, m, h);
+  if (out) {
+    if ((int64_t)h.size() > cap) return -3;
+    std::memcpy(out, h.data(), h.size() * 4);
+  }
+  return (int64_t)h.size();
+}
+
+int32_t lfa_debug_choose_variant(int32_t M, int32_t N, int32_t vectors) {
+  return choose_variant(M, N, vectors != 0);
+}
+
+int32_t lfa_debug_variant_count(void) { return kNumVariants; }
+
+}  // extern "C"

@@ -1,0 +1,80 @@
+// Internal structures shared by the host API and the kernels of the LFA SVD
+// library (arXiv 2506.05617). Not part of the public ABI (include/lfa.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lfa {
+
+constexpr int kMaxLayers = 64;   // layers per plan
+constexpr int kMaxTaps = 256;    // kh * kw <= 225 (k <= 15)
+
+// Device counters of one lfa_svd call; reset at the start of each call.
+struct Counters {
+  unsigned long long unconverged;
+  unsigned long long nonfinite;
+  unsigned long long sweeps;
+  unsigned long long rotations;
+  unsigned int queue[16];        // work-queue tickets, one per launch of a call
+};
+
+// One layer as a kernel sees it. The Jacobi problem of a symbol is X (M x N), with
+// X = A_k (M = c_out, N = c_in) when c_out >= c_in ("tall"), else X = A_k^* (M = c_in,
+// N = c_out, "wide"). N = r = min(c_out, c_in) columns are orthogonalised.
+struct LayerArgs {
+  const float* w;           // [c_out][c_in][kh][kw]
+  float* sigma;             // full grid [n*m][r] or half grid [F_h][r]
+  float2* U;                // [F_h][c_out][r]
+  float2* V;                // [F_h][c_in][r]
+  const int32_t* half;      // half-grid frequencies f = j*m + l, increasing, [F_h]
+  const float2* tw_n;       // T_n[t] = exp(2 pi i t / n), [n]
+  const float2* tw_m;       // T_m[t] = exp(2 pi i t / m), [m]
+  const float2* symbols;    // materialised symbols [F_h][c_out][c_in] (plain path) or null
+  int32_t c_out, c_in, kh, kw, n, m, ph, pw;
+  int32_t F_h, r, M, N, wide;
+  int32_t item_begin;       // first work item of this layer in its launch
+  float tol2;               // squared Jacobi threshold
+};
+
+// One launch of a Jacobi variant over some layers (a persistent grid pulling items).
+struct JacobiLaunch {
+  LayerArgs L[kMaxLayers];
+  int32_t nlayers;
+  int32_t total_items;
+  const ushort2* sched;     // [NC - 1 rounds][NC / 2 teams] column ids (a, b)
+  int32_t max_sweeps;
+  int32_t half_output;
+  int32_t queue_slot;
+  Counters* counters;
+};
+
+// Host-side launchers implemented in the kernel translation units.
+struct VariantInfo {
+  int id;
+  int NP, L, MR, WR;        // pairs, lanes per pair, X rows per lane, W rows per lane
+  int block;                // threads per CTA
+  int spu;                  // symbols per work item
+  size_t smem;              // dynamic shared memory per CTA (bytes)
+  int max_rows;             // M capacity
+  int max_cols;             // N capacity
+};
+
+int jacobi_variant_count();
+const VariantInfo* jacobi_variant(int id);
+cudaError_t jacobi_prepare(int id, bool vec, bool fused);             // set smem attributes
+cudaError_t jacobi_occupancy(int id, bool vec, bool fused, int* blocks_per_sm);
+cudaError_t jacobi_launch(int id, bool vec, bool fused, const JacobiLaunch& P, int grid,
+                          cudaStream_t s);
+
+// Auxiliary kernels (aux_kernels.cu).
+cudaError_t launch_symbols(const LayerArgs& La, float2* out, cudaStream_t s);
+cudaError_t launch_expand(const LayerArgs& La, const float2* U, const float2* V, int64_t first,
+                          int64_t count, float2* u_hat, float2* v_hat, cudaStream_t s);
+cudaError_t launch_backward(const LayerArgs& La, const float* dsigma, int half_output,
+                            const float2* U, const float2* V, float2* G, int64_t g_cap,
+                            float* partial, int chunks, float* dw, cudaStream_t s);
+cudaError_t launch_regulariser(const LayerArgs& La, int half_output, const float* sigma, float lam,
+                               float* dsigma, float* loss, cudaStream_t s);
+
+}  // namespace lfa

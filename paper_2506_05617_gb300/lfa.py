@@ -1,0 +1,258 @@
+"""Thin Python binding of the C ABI in ``include/lfa.h`` (argument marshalling only).
+
+Each function has the name of the C entry point it calls and takes plain Python
+values: device pointers as ints, per-layer pointer lists as Python lists of ints,
+streams as ints (``torch.cuda.Stream.cuda_stream``) or None. Every step of the
+computation runs in the CUDA library; if ``liblfa.so`` is missing this module
+raises instead of computing anything another way.
+
+A non-OK status raises :class:`LfaError` except where a function documents that it
+returns the status (``lfa_get_info``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_float, c_int32, c_int64, c_uint16, c_uint32, c_void_p
+from typing import Iterable, List, Optional, Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "liblfa.so")
+
+# flags (include/lfa.h)
+LFA_VALUES = 0x1
+LFA_VECTORS = 0x2
+LFA_HALF_OUTPUT = 0x4
+LFA_PLAIN = 0x8
+
+# status codes
+LFA_OK = 0
+LFA_ERR_INVALID_ARG = 1
+LFA_ERR_UNSUPPORTED = 2
+LFA_ERR_OOM = 3
+LFA_ERR_CUDA = 4
+LFA_ERR_NOT_CONVERGED = 5
+LFA_ERR_NONFINITE = 6
+LFA_ERR_TIMEOUT = 7
+
+# every symbol include/lfa.h and include/lfa_debug.h declare
+EXPORTS = [
+    "lfa_plan", "lfa_svd", "lfa_symbols", "lfa_expand", "lfa_svd_backward", "lfa_regulariser_grad",
+    "lfa_destroy", "lfa_get_info", "lfa_layer_query", "lfa_status_string", "lfa_variant_name",
+    "lfa_last_cuda_error", "lfa_version",
+    "lfa_debug_schedule", "lfa_debug_half_grid", "lfa_debug_choose_variant", "lfa_debug_variant_count",
+]
+
+
+class LayerDesc(ctypes.Structure):
+    _fields_ = [("c_out", c_int32), ("c_in", c_int32), ("kh", c_int32), ("kw", c_int32),
+                ("n", c_int32), ("m", c_int32), ("pad_h", c_int32), ("pad_w", c_int32)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("tol", c_float), ("max_sweeps", c_int32), ("variant", c_int32),
+                ("use_graph", c_int32), ("tune_cache", c_char_p)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("symbols", c_int64), ("singular_values", c_int64), ("unconverged", c_int64),
+                ("nonfinite", c_int64), ("sweeps", c_int64), ("rotations", c_int64),
+                ("plan_device_bytes", c_int64), ("nlayers", c_int32), ("max_sweeps", c_int32),
+                ("tol", c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class LfaError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = lib().lfa_status_string(status).decode()
+        if status == LFA_ERR_CUDA:
+            msg += f" (cudaError {lib().lfa_last_cuda_error()})"
+        super().__init__(f"{where}: {msg} [status {status}]")
+
+
+_LIB = None
+
+
+def lib():
+    """The loaded ``liblfa.so`` (raises if it has not been built: there is no fallback)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"the LFA CUDA library is not built ({LIB_PATH} missing); "
+                           "run `python -m paper_2506_05617_gb300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    P = c_void_p
+    PP = POINTER(c_void_p)
+    sig = {
+        "lfa_plan": (c_int32, [POINTER(c_void_p), POINTER(LayerDesc), c_int32, c_uint32, POINTER(Options)]),
+        "lfa_svd": (c_int32, [P, PP, PP, PP, PP, P]),
+        "lfa_symbols": (c_int32, [P, c_int32, P, P, P]),
+        "lfa_expand": (c_int32, [P, c_int32, P, P, c_int64, c_int64, P, P, P]),
+        "lfa_svd_backward": (c_int32, [P, PP, PP, PP, PP, P]),
+        "lfa_regulariser_grad": (c_int32, [P, PP, c_float, PP, PP, P]),
+        "lfa_destroy": (c_int32, [P]),
+        "lfa_get_info": (c_int32, [P, POINTER(Info)]),
+        "lfa_layer_query": (c_int32, [P, c_int32, POINTER(c_int64), POINTER(c_int32), POINTER(c_int32),
+                                      POINTER(c_int32)]),
+        "lfa_status_string": (c_char_p, [c_int32]),
+        "lfa_variant_name": (c_char_p, [c_int32]),
+        "lfa_last_cuda_error": (c_int32, []),
+        "lfa_version": (c_int32, []),
+        "lfa_debug_schedule": (c_int32, [c_int32, POINTER(c_uint16), c_int64]),
+        "lfa_debug_half_grid": (c_int64, [c_int32, c_int32, POINTER(c_int32), c_int64]),
+        "lfa_debug_choose_variant": (c_int32, [c_int32, c_int32, c_int32]),
+        "lfa_debug_variant_count": (c_int32, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = L
+    return L
+
+
+def _check(status: int, where: str):
+    if status != LFA_OK:
+        raise LfaError(status, where)
+
+
+def _ptrs(values: Optional[Sequence[int]], n: int):
+    if values is None:
+        return None
+    arr = (c_void_p * n)()
+    for i, v in enumerate(values):
+        arr[i] = c_void_p(int(v)) if v else None
+    return ctypes.cast(arr, POINTER(c_void_p))
+
+
+def _stream(s) -> Optional[int]:
+    if s is None:
+        return None
+    return int(getattr(s, "cuda_stream", s)) or None
+
+
+# ----------------------------------------------------------------------------- entry points
+def lfa_plan(layers: Iterable, flags: int = LFA_VALUES, tol: float = 0.0, max_sweeps: int = 0,
+             variant: int = -1, use_graph: int = -1, tune_cache: Optional[str] = None) -> int:
+    """Creates a plan; ``layers`` holds LayerDesc or (c_out, c_in, kh, kw, n, m[, pad_h, pad_w])."""
+    descs = []
+    for d in layers:
+        if isinstance(d, LayerDesc):
+            descs.append(d)
+        else:
+            d = tuple(d)
+            if len(d) == 6:
+                d = d + (-1, -1)
+            descs.append(LayerDesc(*[int(x) for x in d]))
+    arr = (LayerDesc * max(1, len(descs)))(*descs)
+    opt = Options(float(tol), int(max_sweeps), int(variant), int(use_graph),
+                  tune_cache.encode() if tune_cache else None)
+    h = c_void_p()
+    _check(lib().lfa_plan(ctypes.byref(h), arr, len(descs), int(flags), ctypes.byref(opt)), "lfa_plan")
+    return int(h.value)
+
+
+def lfa_svd(plan: int, w: Sequence[int], sigma: Sequence[int], U: Optional[Sequence[int]] = None,
+            V: Optional[Sequence[int]] = None, stream=None) -> None:
+    n = len(w)
+    _check(lib().lfa_svd(c_void_p(plan), _ptrs(w, n), _ptrs(sigma, n), _ptrs(U, n), _ptrs(V, n),
+                         _stream(stream)), "lfa_svd")
+
+
+def lfa_symbols(plan: int, layer: int, w: int, out: int, stream=None) -> None:
+    _check(lib().lfa_symbols(c_void_p(plan), layer, c_void_p(w), c_void_p(out), _stream(stream)), "lfa_symbols")
+
+
+def lfa_expand(plan: int, layer: int, U: int, V: int, first: int, count: int, u_hat: int, v_hat: int,
+               stream=None) -> None:
+    _check(lib().lfa_expand(c_void_p(plan), layer, c_void_p(U or None), c_void_p(V or None), first, count,
+                            c_void_p(u_hat or None), c_void_p(v_hat or None), _stream(stream)), "lfa_expand")
+
+
+def lfa_svd_backward(plan: int, dsigma: Sequence[int], U: Sequence[int], V: Sequence[int], dw: Sequence[int],
+                     stream=None) -> None:
+    n = len(dw)
+    _check(lib().lfa_svd_backward(c_void_p(plan), _ptrs(dsigma, n), _ptrs(U, n), _ptrs(V, n), _ptrs(dw, n),
+                                  _stream(stream)), "lfa_svd_backward")
+
+
+def lfa_regulariser_grad(plan: int, sigma: Sequence[int], lam: float, dsigma: Sequence[int],
+                         loss: Optional[Sequence[int]] = None, stream=None) -> None:
+    n = len(sigma)
+    _check(lib().lfa_regulariser_grad(c_void_p(plan), _ptrs(sigma, n), float(lam), _ptrs(dsigma, n),
+                                      _ptrs(loss, n), _stream(stream)), "lfa_regulariser_grad")
+
+
+def lfa_destroy(plan: int) -> None:
+    _check(lib().lfa_destroy(c_void_p(plan)), "lfa_destroy")
+
+
+def lfa_get_info(plan: int):
+    """Returns (status, info dict); status is LFA_OK, LFA_ERR_NOT_CONVERGED or LFA_ERR_NONFINITE."""
+    info = Info()
+    st = lib().lfa_get_info(c_void_p(plan), ctypes.byref(info))
+    if st not in (LFA_OK, LFA_ERR_NOT_CONVERGED, LFA_ERR_NONFINITE):
+        raise LfaError(st, "lfa_get_info")
+    return st, info.as_dict()
+
+
+def lfa_layer_query(plan: int, layer: int, with_half_grid: bool = False):
+    F_h = c_int64()
+    r = c_int32()
+    v = c_int32()
+    _check(lib().lfa_layer_query(c_void_p(plan), layer, ctypes.byref(F_h), ctypes.byref(r), ctypes.byref(v),
+                                 None), "lfa_layer_query")
+    half = None
+    if with_half_grid:
+        buf = (c_int32 * F_h.value)()
+        _check(lib().lfa_layer_query(c_void_p(plan), layer, None, None, None, buf), "lfa_layer_query")
+        half = list(buf)
+    return {"F_h": F_h.value, "r": r.value, "variant": v.value,
+            "variant_name": lfa_variant_name(v.value), "half_grid": half}
+
+
+def lfa_status_string(status: int) -> str:
+    return lib().lfa_status_string(status).decode()
+
+
+def lfa_variant_name(variant: int) -> str:
+    return lib().lfa_variant_name(variant).decode()
+
+
+def lfa_last_cuda_error() -> int:
+    return lib().lfa_last_cuda_error()
+
+
+def lfa_version() -> int:
+    return lib().lfa_version()
+
+
+def lfa_debug_schedule(ncols: int) -> List[List[tuple]]:
+    rounds = ncols - 1
+    buf = (c_uint16 * (rounds * ncols))()
+    got = lib().lfa_debug_schedule(ncols, buf, len(buf))
+    if got < 0:
+        raise ValueError(f"lfa_debug_schedule({ncols}) failed: {got}")
+    np_ = ncols // 2
+    return [[(buf[(t * np_ + k) * 2], buf[(t * np_ + k) * 2 + 1]) for k in range(np_)] for t in range(got)]
+
+
+def lfa_debug_half_grid(n: int, m: int) -> List[int]:
+    cnt = lib().lfa_debug_half_grid(n, m, None, 0)
+    if cnt < 0:
+        raise ValueError("invalid torus")
+    buf = (c_int32 * cnt)()
+    lib().lfa_debug_half_grid(n, m, buf, cnt)
+    return list(buf)
+
+
+def lfa_debug_choose_variant(M: int, N: int, vectors: bool) -> int:
+    return lib().lfa_debug_choose_variant(M, N, int(bool(vectors)))
+
+
+def lfa_debug_variant_count() -> int:
+    return lib().lfa_debug_variant_count()

@@ -1,0 +1,128 @@
+"""Host-side checks of the CUDA library that need no GPU: it builds, loads, exports every
+symbol the headers declare, and its plan-time logic (Jacobi schedule, half grid, variant
+choice, argument validation) is right."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2506_05617_gb300 import build as B
+from paper_2506_05617_gb300 import lfa as C
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        txt = open(os.path.join(ROOT, "include", h)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names += re.findall(r"\b(lfa_[a-z_0-9]+)\s*\(", txt)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    L = C.lib()
+    decl = declared_functions()
+    assert len(decl) >= 15
+    for name in decl:
+        assert hasattr(L, name), name
+    assert set(decl) == set(C.EXPORTS)
+
+
+@pytest.mark.parametrize("ncols", [4, 8, 16, 32, 64, 128, 256, 512])
+def test_schedule_covers_every_pair_once_and_keeps_one_column(ncols):
+    rounds = C.lfa_debug_schedule(ncols)
+    assert len(rounds) == ncols - 1
+    seen = set()
+    for t, rnd in enumerate(rounds):
+        cols = [c for p in rnd for c in p]
+        assert sorted(cols) == list(range(ncols))          # a perfect matching
+        for a, b in rnd:
+            seen.add((min(a, b), max(a, b)))
+        if t + 1 < len(rounds):
+            for (a, b), (a2, b2) in zip(rnd, rounds[t + 1]):
+                assert (a == a2) != (b == b2)               # exactly one column kept, in its slot
+    assert len(seen) == ncols * (ncols - 1) // 2
+
+
+@pytest.mark.parametrize("n,m", [(1, 1), (1, 2), (2, 2), (3, 5), (8, 8), (7, 6), (224, 224), (32, 32)])
+def test_half_grid_matches_oracle(n, m):
+    assert C.lfa_debug_half_grid(n, m) == [int(f) for f in O.half_grid(n, m)]
+
+
+def test_variant_choice():
+    assert C.lfa_debug_variant_count() >= 9
+    for M, N in [(4, 4), (64, 3), (64, 64), (32, 32), (16, 8), (64, 16), (1, 1)]:
+        for vec in (False, True):
+            v = C.lfa_debug_choose_variant(M, N, vec)
+            assert v >= 0, (M, N, vec)
+            name = C.lfa_variant_name(v)
+            npairs, lanes, mr, wr = (int(x) for x in re.findall(r"\d+", name))
+            assert M <= mr * lanes and N <= 2 * npairs
+            if vec:
+                assert N <= wr * lanes
+    assert C.lfa_debug_choose_variant(65, 8, True) == -1
+    assert C.lfa_variant_name(-1) == "none"
+
+
+def test_status_strings_and_version():
+    for s in range(8):
+        assert C.lfa_status_string(s)
+    assert C.lfa_status_string(99) == "unknown status"
+    assert C.lfa_version() >= 100
+
+
+@pytest.mark.parametrize("bad", [
+    (0, 4, 3, 3, 8, 8), (4, 4, 0, 3, 8, 8), (4, 4, 3, 3, 0, 8), (4, 600, 3, 3, 8, 8),
+    (4, 4, 3, 3, 8, 8, 3, 1), (4, 4, 16, 3, 8, 8), (4, 4, 3, 3, 8, 8, -2, 0),
+])
+def test_plan_rejects_invalid_layers_without_touching_the_gpu(bad):
+    with pytest.raises(C.LfaError) as ei:
+        C.lfa_plan([bad], C.LFA_VALUES)
+    assert ei.value.status == C.LFA_ERR_INVALID_ARG
+
+
+def test_plan_rejects_bad_flags_and_counts():
+    with pytest.raises(C.LfaError) as ei:
+        C.lfa_plan([(4, 4, 3, 3, 8, 8)], 0x100)
+    assert ei.value.status == C.LFA_ERR_INVALID_ARG
+    with pytest.raises(C.LfaError) as ei:
+        C.lfa_plan([(4, 4, 3, 3, 8, 8)], C.LFA_PLAIN | C.LFA_VECTORS)
+    assert ei.value.status == C.LFA_ERR_INVALID_ARG
+    with pytest.raises(C.LfaError) as ei:
+        C.lfa_plan([], C.LFA_VALUES)
+    assert ei.value.status == C.LFA_ERR_INVALID_ARG
+
+
+def test_null_plan_calls_are_rejected():
+    L = C.lib()
+    assert L.lfa_svd(None, None, None, None, None, None) == C.LFA_ERR_INVALID_ARG
+    assert L.lfa_svd_backward(None, None, None, None, None, None) == C.LFA_ERR_INVALID_ARG
+    assert L.lfa_destroy(None) == C.LFA_OK
+    assert L.lfa_get_info(None, None) == C.LFA_ERR_INVALID_ARG
+
+
+def test_fault_injection_alloc_is_reported(monkeypatch):
+    monkeypatch.setenv("LFA_FAULT_INJECT", "alloc")
+    with pytest.raises(C.LfaError) as ei:
+        C.lfa_plan([(4, 4, 3, 3, 8, 8)], C.LFA_VALUES)
+    assert ei.value.status == C.LFA_ERR_OOM
+
+
+def test_plan_without_gpu_fails_with_a_status():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(C.LfaError) as ei:
+        C.lfa_plan([(4, 4, 3, 3, 8, 8)], C.LFA_VALUES)
+    assert ei.value.status in (C.LFA_ERR_CUDA, C.LFA_ERR_UNSUPPORTED)
