@@ -1,0 +1,463 @@
+#!/usr/bin/env python
+"""Benchmark of the LFA SVD hot path on GB300 (one JSON line on stdout, rank 0).
+
+A step is one pass of the whole path over one synthetic layer batch:
+  forward (symbol assembly fused with the batched one-sided Jacobi SVD, values and
+  vectors, one persistent graph-replayed launch) -> spectral-regulariser dL/dsigma
+  -> backward dL/dw -> lifting of the r global singular vector pairs of one frequency.
+Metric: singular values per second (full-grid count n*m*r per layer per step).
+
+Default workload: one 64->64 3x3 stride-1 periodic conv on a 32x32 torus
+(1024 frequencies, 514 decomposed on the half grid), values + vectors.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--workload NAME]
+
+With torchrun (N > 1) every rank runs the same per-GPU workload on its own seeded
+weights (independent layers: weak scaling, no collective on the data path); the
+step time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import resource
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import lfa_workloads as W  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SMS = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+LAM = 1e-2
+METRIC = "singular values/sec and layers/sec (batched+backward vs plain) at σ err ≤1e-5·σ_max"
+
+
+def nominal_svd_flops(M: int, N: int, vectors: bool) -> float:
+    """Golub-Van Loan dense SVD operation counts (M >= N), x4 for complex arithmetic."""
+    if vectors:
+        return 4.0 * (14.0 * M * N * N + 8.0 * N ** 3)
+    return 4.0 * (4.0 * M * N * N - 4.0 * N ** 3 / 3.0)
+
+
+def layer_flops(l: W.Layer, vectors: bool) -> float:
+    """Nominal flops of one forward over a layer: assembly + SVD per half-grid symbol."""
+    M, N = max(l.c_out, l.c_in), min(l.c_out, l.c_in)
+    F_h = (l.n * l.m + (1 + (l.n % 2 == 0)) * (1 + (l.m % 2 == 0))) // 2
+    return F_h * (4.0 * l.c_out * l.c_in * l.kh * l.kw + nominal_svd_flops(M, N, vectors))
+
+
+def kernel_sha16() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("jacobi.cuh", "jacobi_variants.cuh"):
+        with open(os.path.join(ROOT, "paper_2506_05617_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload: str):
+    """DRAM bytes per launch of the Jacobi kernel from the committed ncu capture, or None when
+    there is none for this workload or the kernel source changed since it was taken."""
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(prof)).get(workload)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("kernel_sha16") != kernel_sha16():
+        return None
+    return rec.get("bytes_per_launch")
+
+
+def fp32_peak_tflops() -> float:
+    return SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle leg
+def oracle_sample_step(w, lay: W.Layer, freqs, g_seed: int):
+    """One bounded sample of the step on the FP64 oracle (CPU): symbols + SVD (U, V) of the
+    sampled frequencies, regulariser gradient, their dL/dw contribution, lifted vectors."""
+    import oracle as O
+    s, U, V = O.lfa_svd(w, lay.n, lay.m, compute_uv=True, freqs=freqs)
+    g = O.regulariser_grad_sigma(s, LAM)
+    dw = O.lfa_backward(w, lay.n, lay.m, g, U, V, freqs=freqs)
+    f0 = int(freqs[0])
+    j, l = divmod(f0, lay.m)
+    uh, vh = O.lift(U[0], V[0], j, l, lay.n, lay.m)
+    return s, dw, uh, vh
+
+
+def run_oracle(lay: W.Layer, seconds: float, nfreq: int, steps: int | None = None):
+    """Times the oracle on sampled frequencies of the workload; returns the cpu_baseline dict."""
+    w = W.weights(lay)
+    rng = np.random.default_rng(123)
+    nf = min(nfreq, lay.F)
+    done, sig = 0, 0
+    t0 = time.perf_counter()
+    r0 = resource.getrusage(resource.RUSAGE_SELF)
+    times = []
+    while True:
+        freqs = np.sort(rng.choice(lay.F, nf, replace=False))
+        ts = time.perf_counter()
+        oracle_sample_step(w, lay, freqs, 0)
+        times.append(time.perf_counter() - ts)
+        done += 1
+        sig += nf * lay.r
+        if steps is not None and done >= steps:
+            break
+        if steps is None and time.perf_counter() - t0 >= seconds:
+            break
+    wall = time.perf_counter() - t0
+    r1 = resource.getrusage(resource.RUSAGE_SELF)
+    cpu = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
+    return {"value": sig / wall, "unit": "singular values/s", "cores": round(cpu / wall, 2),
+            "cores_available": os.cpu_count(), "kind": "oracle",
+            "sample": f"{done} x {nf} of {lay.F} frequencies of {lay.c_out}->{lay.c_in} k={lay.kh} n={lay.n}: "
+                      f"FP64 symbols + LAPACK SVD with U,V + regulariser grad + dL/dw + one lifted pair",
+            "seconds": round(wall, 3), "step_s": times}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_lfa(args, rank: int, world: int, local_rank: int):
+    import torch
+    from paper_2506_05617_gb300 import build as B
+    from paper_2506_05617_gb300 import lfa as C
+    from paper_2506_05617_gb300.torch_api import LfaPlan
+
+    B.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    layers = W.layers(args.workload)
+    # each rank gets its own seeded weights (independent units)
+    ws = [torch.from_numpy(W.weights(l, seed=l.seed + 1000 * rank)).to(dev) for l in layers]
+    specs = [(l.c_out, l.c_in, l.kh, l.kw, l.n, l.m, l.pad_h, l.pad_w) for l in layers]
+    plan = LfaPlan(specs, vectors=True)
+    sig, U, V = plan.alloc(dev)
+    dsig = [torch.empty_like(s) for s in sig]
+    loss = [torch.empty((), device=dev) for _ in sig]
+    dw = [torch.empty_like(w) for w in ws]
+    l0 = layers[0]
+    f_exp = 1 if l0.F > 1 else 0
+    cnt = l0.r
+    uh = torch.empty((cnt, l0.c_out, l0.n, l0.m), dtype=torch.complex64, device=dev)
+    vh = torch.empty((cnt, l0.c_in, l0.n, l0.m), dtype=torch.complex64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+    w_ptrs = [w.data_ptr() for w in ws]
+    s_ptrs = [s.data_ptr() for s in sig]
+    u_ptrs = [u.data_ptr() for u in U]
+    v_ptrs = [v.data_ptr() for v in V]
+    ds_ptrs = [d.data_ptr() for d in dsig]
+    lo_ptrs = [x.data_ptr() for x in loss]
+    dw_ptrs = [d.data_ptr() for d in dw]
+
+    def forward():
+        C.lfa_svd(plan.handle, w_ptrs, s_ptrs, u_ptrs, v_ptrs, sptr)
+
+    def rest():
+        C.lfa_regulariser_grad(plan.handle, s_ptrs, LAM, ds_ptrs, lo_ptrs, sptr)
+        C.lfa_svd_backward(plan.handle, ds_ptrs, u_ptrs, v_ptrs, dw_ptrs, sptr)
+        C.lfa_expand(plan.handle, 0, u_ptrs[0], v_ptrs[0], f_exp * l0.r, cnt, uh.data_ptr(), vh.data_ptr(), sptr)
+
+    flush = torch.empty(args.flush_mb << 20, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(max(3, args.warmup)):
+        forward()
+        rest()
+    barrier()
+    st, info = plan.info()
+    if st != C.LFA_OK:
+        raise RuntimeError(f"forward reported status {st}: {info}")
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    launches0 = C.lfa_kernel_launches()
+    clk = ClockSampler(local_rank)
+    clk.start()
+    time.sleep(0.25)
+    barrier()
+    for i in range(K):
+        flush.fill_(i & 0xff)                       # L2 flush (untimed, outside the events)
+        ev[i][0].record(stream)
+        forward()
+        ev[i][1].record(stream)
+        rest()
+        ev[i][2].record(stream)
+    barrier()
+    launches = C.lfa_kernel_launches() - launches0
+    time.sleep(0.15)
+    clocks = clk.stop()
+    step_ms = [ev[i][0].elapsed_time(ev[i][2]) for i in range(K)]
+    fwd_ms = [ev[i][0].elapsed_time(ev[i][1]) for i in range(K)]
+    total_ms = float(sum(step_ms))
+    fwd_mean = float(sum(fwd_ms) / K)
+    if dist is not None:
+        t = torch.tensor([total_ms, fwd_mean], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, fwd_mean = float(t[0]), float(t[1])
+    st, info = plan.info()
+
+    # ---- plain per-layer forward-only path (materialised symbols, per-layer launches, no graph)
+    plain = LfaPlan(specs, vectors=False, plain=True)
+    psig, _, _ = plain.alloc(dev)
+    pw = [w.data_ptr() for w in ws]
+    pp = [s.data_ptr() for s in psig]
+    for _ in range(3):
+        C.lfa_svd(plain.handle, pw, pp, None, None, sptr)
+    barrier()
+    pev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(min(K, 50))]
+    for e in pev:
+        flush.fill_(1)
+        e[0].record(stream)
+        C.lfa_svd(plain.handle, pw, pp, None, None, sptr)
+        e[1].record(stream)
+    barrier()
+    plain_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in pev]))
+
+    # ---- end to end through the public API from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        hw = [w.cpu().pin_memory() for w in ws]
+        outs = sig + U + V + dsig + dw + loss + [uh, vh]
+        hout = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
+        h2d = sum(x.numel() * x.element_size() for x in hw)
+        d2h = sum(x.numel() * x.element_size() for x in hout)
+        KE = min(K, 50)
+        eev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(KE)]
+        barrier()
+        for i in range(KE):
+            flush.fill_(2)
+            eev[i][0].record(stream)
+            for d, h in zip(ws, hw):
+                d.copy_(h, non_blocking=True)
+            forward()
+            rest()
+            for d, h in zip(outs, hout):
+                h.copy_(d, non_blocking=True)
+            eev[i][1].record(stream)
+        barrier()
+        e2e_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in eev]))
+        if dist is not None:
+            t = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t[0])
+        sig_per_step = sum(l.n_sigma for l in layers)
+        e2e = {"value": world * sig_per_step / (e2e_ms / 1e3), "unit": "singular values/s",
+               "ms_per_step": e2e_ms, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    sig_per_step = sum(l.n_sigma for l in layers)
+    ms_per_step = total_ms / K
+    value = world * sig_per_step * K / (total_ms / 1e3)
+    flops = sum(layer_flops(l, True) for l in layers)
+    peak = fp32_peak_tflops()
+    achieved = flops / (fwd_mean / 1e3) / 1e12
+    traffic = measured_traffic(args.workload)
+    peaks = {}
+    if os.path.exists(PEAKS_FILE):
+        try:
+            peaks = json.load(open(PEAKS_FILE))
+        except (OSError, ValueError):
+            peaks = {}
+
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "singular values/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded He-normal weights; the paper's weights are unstated)",
+        "config": {
+            "workload": args.workload,
+            "layers": [f"{l.c_out}x{l.c_in}x{l.kh}x{l.kw}@{l.n}x{l.m}" for l in layers],
+            "outputs": "values+vectors (U, V per half-grid frequency)",
+            "step": "fwd(assembly+Jacobi, graph) + regulariser dL/dsigma + bwd dL/dw + lift r vector pairs",
+            "l2": f"flushed between timed steps ({args.flush_mb} MB write, outside the timed events)",
+            "parallelism": f"dp{world} (independent layers per rank)",
+        },
+        "layers_per_s": world * len(layers) * K / (total_ms / 1e3),
+        "symbols_per_s": world * sum(l.F for l in layers) * K / (total_ms / 1e3),
+        "fwd_ms": fwd_mean,
+        "plain_fwd_values_ms": plain_ms,
+        "plain_layers_per_s": len(layers) / (plain_ms / 1e3),
+        "roofline": {
+            "kernel": "jacobi_kernel (fused symbol assembly + one-sided Jacobi, values+vectors)",
+            "bound": "alu",
+            "achieved": achieved,
+            "peak": peak,
+            "unit": "TFLOP/s",
+            "frac": achieved / peak,
+            "traffic": traffic,
+            "peak_source": f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz",
+            "flops_model": "nominal Golub-Van Loan complex SVD counts (x4) + symbol assembly, per half-grid symbol",
+            "executed_sweeps_per_symbol": info["sweeps"] / max(1, info["symbols"]),
+            "rotations": info["rotations"],
+        },
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+        "accuracy": {"unconverged": info["unconverged"], "nonfinite": info["nonfinite"]},
+        "measured_peaks": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")} if peaks else None,
+    }
+    if e2e is not None:
+        out["e2e"] = e2e
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = run_oracle(layers[0], args.cpu_seconds, args.cpu_freqs)
+        # the sampled oracle frequencies also give an accuracy check of this run's sigma
+        import oracle as O
+        rng = np.random.default_rng(5)
+        fr = np.sort(rng.choice(layers[0].F, min(64, layers[0].F), replace=False))
+        s_ref = O.lfa_svd(W.weights(layers[0], seed=layers[0].seed), layers[0].n, layers[0].m,
+                          compute_uv=False, freqs=fr)
+        s_gpu = sig[0].cpu().numpy()[fr]
+        cb["sigma_err_vs_oracle_rel_sigma_max"] = float(np.max(np.abs(s_gpu - s_ref)) / s_ref.max())
+        cb.pop("step_s", None)
+        out["cpu_baseline"] = cb
+    if dist is not None:
+        dist.destroy_process_group()
+    plan.close()
+    plain.close()
+    return out
+
+
+def run_reference(args):
+    """The oracle arm: the FP64 CPU oracle on bounded samples of the same workload."""
+    layers = W.layers(args.workload)
+    lay = layers[0]
+    w = W.weights(lay)
+    rng = np.random.default_rng(7)
+    nf = min(args.cpu_freqs, lay.F)
+    for _ in range(args.warmup):
+        oracle_sample_step(w, lay, np.sort(rng.choice(lay.F, nf, replace=False)), 0)
+    r0 = resource.getrusage(resource.RUSAGE_SELF)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_sample_step(w, lay, np.sort(rng.choice(lay.F, nf, replace=False)), 0)
+    wall = time.perf_counter() - t0
+    r1 = resource.getrusage(resource.RUSAGE_SELF)
+    cpu = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
+    value = args.steps * nf * lay.r / wall
+    sample = f"{nf} of {lay.F} frequencies per step (FP64 oracle: symbols, LAPACK SVD with U,V, regulariser, dL/dw, lift)"
+    return {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": "singular values/s",
+        "n_gpus": args.gpus,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": wall / args.steps * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded He-normal weights)",
+        "config": {"workload": args.workload,
+                   "layers": [f"{l.c_out}x{l.c_in}x{l.kh}x{l.kw}@{l.n}x{l.m}" for l in layers],
+                   "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "singular values/s", "cores": round(cpu / wall, 2),
+                         "cores_available": os.cpu_count(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "singular values/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["lfa", "reference"], default="lfa")
+    ap.add_argument("--workload", default="conv64_k3_n32", choices=sorted(W.WORKLOADS))
+    ap.add_argument("--flush-mb", type=int, default=256)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--cpu-freqs", type=int, default=64)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        print(json.dumps(run_reference(args)))
+        return 0
+    out = run_lfa(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(out))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -194,6 +194,9 @@ const char* lfa_status_string(lfa_status_t status);
 const char* lfa_variant_name(int32_t variant);
 /* The last CUDA runtime error seen by the library in this thread (cudaError_t as int). */
 int32_t lfa_last_cuda_error(void);
+/* Number of kernels this library has enqueued in this process so far (a replayed
+ * CUDA graph counts each of its kernel nodes). Host-side counter; for launch accounting. */
+int64_t lfa_kernel_launches(void);
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int32_t lfa_version(void);
 

@@ -133,19 +133,21 @@ def _phase(n: int, m: int, dy1: int, dy2: int) -> np.ndarray:
     return np.exp(2j * np.pi * t)
 
 
-def symbols(w, n: int, m: int, pad_h: int = -1, pad_w: int = -1) -> np.ndarray:
+def symbols(w, n: int, m: int, pad_h: int = -1, pad_w: int = -1, freqs=None) -> np.ndarray:
     """Symbols A_k = sum_{y in N} M_y exp(2 pi i <k, y>) for all n*m frequencies (Sec. III, Alg. 1 line 4).
 
     Returns complex128 [n*m, c_out, c_in]; frequency f = j*m + l is k = (j/n, l/m).
+    ``freqs`` (optional index array) restricts the output to those frequencies, in that order.
     """
     w = np.asarray(w, dtype=np.float64)
     c_out, c_in, kh, kw = w.shape
     ph, pw = origin(kh, kw, pad_h, pad_w)
-    S = np.zeros((n, m, c_out, c_in), dtype=np.complex128)
+    sel = np.arange(n * m) if freqs is None else np.asarray(freqs)
+    S = np.zeros((len(sel), c_out, c_in), dtype=np.complex128)
     for a in range(kh):
         for b in range(kw):
-            S += _phase(n, m, a - ph, b - pw)[:, :, None, None] * w[None, None, :, :, a, b]
-    return S.reshape(n * m, c_out, c_in)
+            S += _phase(n, m, a - ph, b - pw).reshape(n * m)[sel][:, None, None] * w[None, :, :, a, b]
+    return S
 
 
 def fft_symbols(w, n: int, m: int, pad_h: int = -1, pad_w: int = -1) -> np.ndarray:
@@ -167,13 +169,14 @@ def fft_symbols(w, n: int, m: int, pad_h: int = -1, pad_w: int = -1) -> np.ndarr
     return np.ascontiguousarray(Fk.transpose(2, 3, 0, 1)).reshape(n * m, c_out, c_in)
 
 
-def lfa_svd(w, n: int, m: int, pad_h: int = -1, pad_w: int = -1, compute_uv: bool = True):
+def lfa_svd(w, n: int, m: int, pad_h: int = -1, pad_w: int = -1, compute_uv: bool = True, freqs=None):
     """Algorithm 1 in FP64: a LAPACK SVD of the symbol at every frequency of T*_{n,m}.
 
     Returns ``sigma`` [n*m, r] (descending per frequency) and, when ``compute_uv``,
     ``U`` [n*m, c_out, r] and ``V`` [n*m, c_in, r] with A_k = U_k diag(sigma_k) V_k^*.
+    ``freqs`` restricts the loop to those frequencies (rows follow ``freqs``).
     """
-    S = symbols(w, n, m, pad_h, pad_w)
+    S = symbols(w, n, m, pad_h, pad_w, freqs)
     if not compute_uv:
         return np.linalg.svd(S, compute_uv=False)
     U, s, Vh = np.linalg.svd(S, full_matrices=False)
@@ -223,13 +226,14 @@ def folded_kernel(w, n: int, m: int, pad_h: int = -1, pad_w: int = -1) -> np.nda
 
 
 # --------------------------------------------------------------------------- backward
-def lfa_backward(w, n: int, m: int, g, U, V, pad_h: int = -1, pad_w: int = -1) -> np.ndarray:
+def lfa_backward(w, n: int, m: int, g, U, V, pad_h: int = -1, pad_w: int = -1, freqs=None) -> np.ndarray:
     """dL/dw from the upstream gradient ``g`` = dL/dsigma [n*m, r] and the per-frequency U, V.
 
     Uses d(sigma_s) = Re(u_s^* dA_k v_s) for a simple singular value and the symbol
     definition dA_k/dw[o,i,a,b] = exp(2 pi i <k, y_ab>) e_o e_i^T, summed over the
     full frequency grid:
         dW[o,i,a,b] = sum_k Re( sum_s g[k,s] conj(U_k[o,s]) V_k[i,s] exp(2 pi i <k, y_ab>) ).
+    ``freqs`` restricts the sum to those frequencies (rows of g, U, V follow ``freqs``).
     """
     w = np.asarray(w, dtype=np.float64)
     c_out, c_in, kh, kw = w.shape
@@ -240,6 +244,8 @@ def lfa_backward(w, n: int, m: int, g, U, V, pad_h: int = -1, pad_w: int = -1) -
     for a in range(kh):
         for b in range(kw):
             ph_k = _phase(n, m, a - ph, b - pw).reshape(n * m)
+            if freqs is not None:
+                ph_k = ph_k[np.asarray(freqs)]
             dW[:, :, a, b] = np.real(np.einsum("f,foi->oi", ph_k, H))
     return dW
 

@@ -208,7 +208,8 @@ __global__ void __launch_bounds__(256) backward_reduce_kernel(const float* parti
 // G holds g_cap symbols' G_h; the half grid is processed in blocks of whole chunks that fit.
 cudaError_t launch_backward(const LayerArgs& La, const float* dsigma, int half_output,
                             const float2* U, const float2* V, float2* G, int64_t g_cap, float* partial,
-                            int chunks, float* dw, cudaStream_t s) {
+                            int chunks, float* dw, cudaStream_t s, int* nkernels) {
+  *nkernels = 0;
   if (La.F_h <= 0) return cudaSuccess;
   const int CC = La.c_out * La.c_in;
   const int chunk = (La.F_h + chunks - 1) / chunks;
@@ -224,15 +225,18 @@ cudaError_t launch_backward(const LayerArgs& La, const float* dsigma, int half_o
     const int h1 = c1 * chunk < La.F_h ? c1 * chunk : La.F_h;
     dim3 gg((La.c_in + 31) / 32, (La.c_out + 31) / 32, h1 - h0);
     backward_g_kernel<<<gg, 256, 0, s>>>(La, dsigma, half_output, U, V, h0, G);
+    ++*nkernels;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     dim3 gd((CC + 127) / 128, c1 - c0);
     backward_dw_kernel<<<gd, 128, 0, s>>>(La, G, h0, chunk, c0, partial);
+    ++*nkernels;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   const int64_t total = (int64_t)CC * La.kh * La.kw;
   backward_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(partial, chunks, total, dw);
+  ++*nkernels;
   return cudaGetLastError();
 }
 

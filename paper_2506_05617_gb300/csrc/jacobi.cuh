@@ -215,30 +215,34 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
         const float g2 = fmaf(gr, gr, gi * gi);
         if (g2 > tol2 * (al * be)) {
           // rotation J = [[c, s e], [-s conj(e), c]] with e = gamma/|gamma|, t = tan:
-          // t solves t^2 + 2 zeta t - 1 = 0, zeta = (beta - alpha) / (2 |gamma|), |t| <= 1
+          // t solves t^2 + 2 zeta t - 1 = 0, zeta = (beta - alpha) / (2 |gamma|), |t| <= 1.
+          // Applied as x + (c - 1) x + ...: for small t, c rounds to 1 in fp32 and a rotation
+          // with c = 1, s = t would grow both norms by t^2/2; c - 1 = -t^2 / (r (1 + r)),
+          // r = sqrt(1 + t^2), keeps each rotation norm-preserving to O(eps t^2).
           const float g = sqrtf(g2);
           const float zeta = (be - al) / (2.f * g);
           const float t = copysignf(1.f, zeta) / (fabsf(zeta) + hypotf(1.f, zeta));
-          const float c = 1.f / sqrtf(fmaf(t, t, 1.f));
-          const float s = c * t;
+          const float rr2 = sqrtf(fmaf(t, t, 1.f));
+          const float cm1 = -(t * t) / (rr2 * (1.f + rr2));
+          const float s = t / rr2;
           const float er = gr / g, ei = gi / g;
           const float sr = s * er, si = s * ei;
 #pragma unroll
           for (int i = 0; i < MR; ++i) {
             const float2 A = xa[i], B = xb[i];
-            xa[i].x = fmaf(c, A.x, -fmaf(sr, B.x, si * B.y));
-            xa[i].y = fmaf(c, A.y, -fmaf(sr, B.y, -si * B.x));
-            xb[i].x = fmaf(c, B.x, fmaf(sr, A.x, -si * A.y));
-            xb[i].y = fmaf(c, B.y, fmaf(sr, A.y, si * A.x));
+            xa[i].x = fmaf(cm1, A.x, A.x) - fmaf(sr, B.x, si * B.y);
+            xa[i].y = fmaf(cm1, A.y, A.y) - fmaf(sr, B.y, -si * B.x);
+            xb[i].x = fmaf(cm1, B.x, B.x) + fmaf(sr, A.x, -si * A.y);
+            xb[i].y = fmaf(cm1, B.y, B.y) + fmaf(sr, A.y, si * A.x);
           }
           if constexpr (C::VEC) {
 #pragma unroll
             for (int i = 0; i < WR; ++i) {
               const float2 A = wa[i], B = wb[i];
-              wa[i].x = fmaf(c, A.x, -fmaf(sr, B.x, si * B.y));
-              wa[i].y = fmaf(c, A.y, -fmaf(sr, B.y, -si * B.x));
-              wb[i].x = fmaf(c, B.x, fmaf(sr, A.x, -si * A.y));
-              wb[i].y = fmaf(c, B.y, fmaf(sr, A.y, si * A.x));
+              wa[i].x = fmaf(cm1, A.x, A.x) - fmaf(sr, B.x, si * B.y);
+              wa[i].y = fmaf(cm1, A.y, A.y) - fmaf(sr, B.y, -si * B.x);
+              wb[i].x = fmaf(cm1, B.x, B.x) + fmaf(sr, A.x, -si * A.y);
+              wb[i].y = fmaf(cm1, B.y, B.y) + fmaf(sr, A.y, si * A.x);
             }
           }
           rotated = 1;
@@ -344,7 +348,23 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
     }
     al = team_sum<L>(al);
     be = team_sum<L>(be);
-    const float sa = sqrtf(al), sb = sqrtf(be);
+    float sa = sqrtf(al), sb = sqrtf(be);
+    float nwa = 1.f, nwb = 1.f;  // norms of the accumulated rotation columns (1 up to rounding)
+    if constexpr (C::VEC) {
+      float qa = 0.f, qb = 0.f;
+#pragma unroll
+      for (int i = 0; i < WR; ++i) {
+        qa = fmaf(wa[i].x, wa[i].x, fmaf(wa[i].y, wa[i].y, qa));
+        qb = fmaf(wb[i].x, wb[i].x, fmaf(wb[i].y, wb[i].y, qb));
+      }
+      qa = team_sum<L>(qa);
+      qb = team_sum<L>(qb);
+      // x_p = A w_p exactly up to rounding, so sigma_p = |x_p| / |w_p| with v_p = w_p / |w_p|
+      nwa = qa > 0.f ? sqrtf(qa) : 1.f;
+      nwb = qb > 0.f ? sqrtf(qb) : 1.f;
+      sa = sa / nwa;
+      sb = sb / nwb;
+    }
     const int N = La.N, M = La.M;
     if (lane == 0) {
       if (ca < N) ssig[ca] = sa;
@@ -382,13 +402,14 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
       if (ut == 0) *defc = 0;
       unit_sync<C>();
       const bool za = !(sa >= 1e-30f), zb = !(sb >= 1e-30f);   // zero (or NaN) column
-      const float ia = za ? 0.f : 1.f / sa, ib = zb ? 0.f : 1.f / sb;
+      const float ia = za ? 0.f : 1.f / sqrtf(al), ib = zb ? 0.f : 1.f / sqrtf(be);
+      const float iwa = 1.f / nwa, iwb = 1.f / nwb;
       if (ca < N) {
         float2* d = mbox + rka * C::CS;
 #pragma unroll
         for (int i = 0; i < MR; ++i) d[lane + L * i] = make_float2(xa[i].x * ia, xa[i].y * ia);
 #pragma unroll
-        for (int i = 0; i < WR; ++i) d[C::XR + lane + L * i] = wa[i];
+        for (int i = 0; i < WR; ++i) d[C::XR + lane + L * i] = make_float2(wa[i].x * iwa, wa[i].y * iwa);
         if (za && lane == 0) { ssig[ca] = -1.f; atomicAdd(defc, 1); }
       }
       if (cb < N) {
@@ -396,7 +417,7 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
 #pragma unroll
         for (int i = 0; i < MR; ++i) d[lane + L * i] = make_float2(xb[i].x * ib, xb[i].y * ib);
 #pragma unroll
-        for (int i = 0; i < WR; ++i) d[C::XR + lane + L * i] = wb[i];
+        for (int i = 0; i < WR; ++i) d[C::XR + lane + L * i] = make_float2(wb[i].x * iwb, wb[i].y * iwb);
         if (zb && lane == 0) { ssig[cb] = -1.f; atomicAdd(defc, 1); }
       }
       unit_sync<C>();

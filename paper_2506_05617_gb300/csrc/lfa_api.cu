@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -23,6 +24,7 @@ using namespace lfa;
 namespace {
 
 thread_local int32_t g_last_cuda_error = 0;
+std::atomic<int64_t> g_launches{0};
 
 lfa_status_t from_cuda(cudaError_t e) {
   if (e == cudaSuccess) return LFA_OK;
@@ -273,6 +275,7 @@ lfa_status_t enqueue_forward(lfa_plan_s* p, const float* const* w, float* const*
       La.symbols = p->sym_ws;
       La.item_begin = 0;
       LFA_CUDA_TRY(launch_symbols(La, p->sym_ws, s));
+      g_launches += 1;
       JacobiLaunch P{};
       P.L[0] = La;
       P.nlayers = 1;
@@ -288,6 +291,7 @@ lfa_status_t enqueue_forward(lfa_plan_s* p, const float* const* w, float* const*
       const int grid = std::max(1, std::min(P.total_items, occ * p->sms));
       if (l >= 16) LFA_CUDA_TRY(cudaMemsetAsync(&p->counters->queue[l % 16], 0, sizeof(unsigned), s));
       LFA_CUDA_TRY(vlaunch(p->variant[l], false, false, P, grid, s));
+      g_launches += 1;
     }
     return LFA_OK;
   }
@@ -504,7 +508,11 @@ lfa_status_t lfa_svd(lfa_plan_t p, const float* const* w, float* const* sigma, f
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   p->last_stream = s;
-  if (!p->use_graph) return enqueue_forward(p, w, sigma, U, V, s);
+  if (!p->use_graph) {
+    lfa_status_t st = enqueue_forward(p, w, sigma, U, V, s);
+    if (st == LFA_OK && !p->plain) g_launches += (int64_t)p->groups.size();
+    return st;
+  }
   // graph path: capture once per distinct set of buffers, then replay
   std::vector<const void*> key;
   key.reserve(4 * p->nlayers);
@@ -528,7 +536,9 @@ lfa_status_t lfa_svd(lfa_plan_t p, const float* const* w, float* const* sigma, f
     if (e != cudaSuccess) { cudaGraphDestroy(g); p->graph = nullptr; p->exec = nullptr; return from_cuda(e); }
     p->graph_key = key;
   }
-  return from_cuda(cudaGraphLaunch(p->exec, s));
+  lfa_status_t st = from_cuda(cudaGraphLaunch(p->exec, s));
+  if (st == LFA_OK) g_launches += (int64_t)p->groups.size();
+  return st;
 }
 
 lfa_status_t lfa_symbols(lfa_plan_t p, int32_t layer, const float* w, float* out, void* stream) {
@@ -536,6 +546,7 @@ lfa_status_t lfa_symbols(lfa_plan_t p, int32_t layer, const float* w, float* out
     return LFA_ERR_INVALID_ARG;
   LayerArgs La = p->args[layer];
   La.w = w;
+  g_launches += 1;
   return from_cuda(launch_symbols(La, reinterpret_cast<float2*>(out), static_cast<cudaStream_t>(stream)));
 }
 
@@ -546,6 +557,7 @@ lfa_status_t lfa_expand(lfa_plan_t p, int32_t layer, const float* U, const float
   const int64_t total = (int64_t)La.n * La.m * La.r;
   if (first < 0 || count < 0 || first + count > total || count > 0x7fffffff) return LFA_ERR_INVALID_ARG;
   if ((u_hat && !U) || (v_hat && !V)) return LFA_ERR_INVALID_ARG;
+  if (count > 0) g_launches += 1;
   return from_cuda(launch_expand(La, reinterpret_cast<const float2*>(U), reinterpret_cast<const float2*>(V),
                                  first, count, reinterpret_cast<float2*>(u_hat),
                                  reinterpret_cast<float2*>(v_hat), static_cast<cudaStream_t>(stream)));
@@ -562,9 +574,11 @@ lfa_status_t lfa_svd_backward(lfa_plan_t p, const float* const* dsigma, const fl
     const LayerArgs& La = p->args[l];
     const int64_t CC = (int64_t)La.c_out * La.c_in;
     const int64_t g_cap = p->g_cap_bytes / (CC * 8);
+    int nk = 0;
     LFA_CUDA_TRY(launch_backward(La, dsigma[l], p->half_output, reinterpret_cast<const float2*>(U[l]),
                                  reinterpret_cast<const float2*>(V[l]), p->g_ws, g_cap, p->partial_ws,
-                                 p->bw_chunks[l], dw[l], s));
+                                 p->bw_chunks[l], dw[l], s, &nk));
+    g_launches += nk;
   }
   return LFA_OK;
 }
@@ -578,6 +592,7 @@ lfa_status_t lfa_regulariser_grad(lfa_plan_t p, const float* const* sigma, float
   for (int l = 0; l < p->nlayers; ++l)
     LFA_CUDA_TRY(launch_regulariser(p->args[l], p->half_output, sigma[l], lam, dsigma[l],
                                     loss ? loss[l] : nullptr, s));
+    g_launches += 1;
   return LFA_OK;
 }
 
@@ -641,6 +656,7 @@ const char* lfa_variant_name(int32_t v) {
 }
 
 int32_t lfa_last_cuda_error(void) { return g_last_cuda_error; }
+int64_t lfa_kernel_launches(void) { return g_launches.load(); }
 int32_t lfa_version(void) { return 100; }
 
 // ----------------------------------------------------------------------------- host-logic hooks

@@ -73,7 +73,7 @@ cudaError_t launch_expand(const LayerArgs& La, const float2* U, const float2* V,
                           int64_t count, float2* u_hat, float2* v_hat, cudaStream_t s);
 cudaError_t launch_backward(const LayerArgs& La, const float* dsigma, int half_output,
                             const float2* U, const float2* V, float2* G, int64_t g_cap,
-                            float* partial, int chunks, float* dw, cudaStream_t s);
+                            float* partial, int chunks, float* dw, cudaStream_t s, int* nkernels);
 cudaError_t launch_regulariser(const LayerArgs& La, int half_output, const float* sigma, float lam,
                                float* dsigma, float* loss, cudaStream_t s);
 

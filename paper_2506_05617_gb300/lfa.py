@@ -39,7 +39,7 @@ LFA_ERR_TIMEOUT = 7
 EXPORTS = [
     "lfa_plan", "lfa_svd", "lfa_symbols", "lfa_expand", "lfa_svd_backward", "lfa_regulariser_grad",
     "lfa_destroy", "lfa_get_info", "lfa_layer_query", "lfa_status_string", "lfa_variant_name",
-    "lfa_last_cuda_error", "lfa_version",
+    "lfa_last_cuda_error", "lfa_kernel_launches", "lfa_version",
     "lfa_debug_schedule", "lfa_debug_half_grid", "lfa_debug_choose_variant", "lfa_debug_variant_count",
 ]
 
@@ -102,6 +102,7 @@ def lib():
         "lfa_variant_name": (c_char_p, [c_int32]),
         "lfa_last_cuda_error": (c_int32, []),
         "lfa_version": (c_int32, []),
+        "lfa_kernel_launches": (c_int64, []),
         "lfa_debug_schedule": (c_int32, [c_int32, POINTER(c_uint16), c_int64]),
         "lfa_debug_half_grid": (c_int64, [c_int32, c_int32, POINTER(c_int32), c_int64]),
         "lfa_debug_choose_variant": (c_int32, [c_int32, c_int32, c_int32]),
@@ -225,6 +226,10 @@ def lfa_variant_name(variant: int) -> str:
 
 def lfa_last_cuda_error() -> int:
     return lib().lfa_last_cuda_error()
+
+
+def lfa_kernel_launches() -> int:
+    return lib().lfa_kernel_launches()
 
 
 def lfa_version() -> int:
