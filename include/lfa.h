@@ -175,6 +175,33 @@ lfa_status_t lfa_svd_backward(lfa_plan_t plan, const float* const* dsigma, const
 lfa_status_t lfa_regulariser_grad(lfa_plan_t plan, const float* const* sigma, float lam,
                                   float* const* dsigma, float* const* loss, void* stream);
 
+/* Size in bytes of the fixed device scratch array of lfa_svd_backward_noalloc (32 MiB). */
+#define LFA_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* Backward pass that allocates nothing. The paper has no counterpart: it exists for
+ * callers that cannot call cudaMalloc -- code whose device memory is owned entirely by
+ * another allocator (a framework's caching allocator, a serving runtime that reserves
+ * HBM at start-up), or a latency-critical loop that cannot pay for cudaMalloc/cudaFree,
+ * which may synchronise the device. It needs no plan (lfa_plan allocates) and computes
+ * what lfa_svd_backward computes for one layer:
+ *   layer   host pointer to the layer description (see lfa_layer_desc_t)
+ *   flags   0 (dsigma on the full grid, [n*m][r]) or LFA_HALF_OUTPUT ([F_h][r])
+ *   dsigma  device float32 dL/dsigma in that layout; U, V: the layer's lfa_svd outputs
+ *   dw      device float32 [c_out][c_in][kh][kw], overwritten
+ * Its scratch (twiddles, half-grid list, G_k workspace, partial sums) lives in one
+ * file-scope device array of LFA_NOALLOC_SCRATCH_BYTES that every GPU loading the
+ * library holds until the process exits. The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress) and caches it; make that first call
+ * before any stream capture. All calls share the array and it keeps the last call's
+ * contents (each call writes what it reads, nothing must start at zero); calls that
+ * overlap on the GPU race. A layer needs about 4*c_out*c_in*kh*kw bytes of partial
+ * sums per chunk (at least one chunk in half the array) and 8*c_out*c_in bytes of G per
+ * half-grid frequency of a chunk in the other half; layers that do not fit (e.g.
+ * c_out = c_in = 512 with k = 3) are rejected with LFA_ERR_UNSUPPORTED before any work.
+ * Asynchronous on `stream`. Errors: LFA_ERR_INVALID_ARG, LFA_ERR_UNSUPPORTED, LFA_ERR_CUDA. */
+lfa_status_t lfa_svd_backward_noalloc(const lfa_layer_desc_t* layer, uint32_t flags, const float* dsigma,
+                                      const float* U, const float* V, float* dw, void* stream);
+
 /* Frees the plan's device memory and the plan. NULL is accepted. Synchronises
  * the device work the plan issued. */
 lfa_status_t lfa_destroy(lfa_plan_t plan);

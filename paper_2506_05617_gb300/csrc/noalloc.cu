@@ -1,0 +1,171 @@
+// lfa_svd_backward_noalloc: the backward pass (dL/dw from dL/dsigma) for callers that
+// cannot allocate device memory. It needs no plan (creating a plan allocates) and
+// takes its scratch space -- the twiddle tables, the per-frequency G_k block workspace
+// and the per-chunk partial sums -- from one fixed array in the library's own
+// device image instead of cudaMalloc.
+//
+// Who cannot allocate: a caller whose device memory is wholly owned by another
+// allocator (a framework's caching allocator, or a serving runtime that reserves
+// HBM at start-up and hands out fixed budgets) gets no room for a private
+// cudaMalloc; and a caller in a latency-critical loop cannot pay for
+// cudaMalloc/cudaFree, which may synchronise the device.
+//
+// The scratch array is LFA_NOALLOC_SCRATCH_BYTES large. Every GPU that loads this
+// library holds it until the process exits. All calls share it and it keeps the last
+// call's contents; nothing in it has to start at zero (each call writes every byte it
+// later reads). Calls that overlap on the GPU (on different streams, or from different
+// host threads without ordering) race on it.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <mutex>
+
+#include "../../include/lfa.h"
+#include "lfa_internal.cuh"
+
+namespace {
+
+constexpr size_t kScratchBytes = (size_t)LFA_NOALLOC_SCRATCH_BYTES;
+constexpr int kMaxDevices = 64;
+
+// The scratch itself. In host code this name is only a host-side stand-in for the
+// device array, never a device address: the kernels get the address that
+// cudaGetSymbolAddress returns for the current device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+std::mutex g_setup_mutex;
+void* g_scratch_ptr[kMaxDevices] = {};
+
+// Set-up, once per device, with that device current: the device address of the array.
+cudaError_t scratch_for_current_device(unsigned char** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_setup_mutex);
+  if (g_scratch_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_ptr[dev] = p;
+  }
+  *out = static_cast<unsigned char*>(g_scratch_ptr[dev]);
+  return cudaSuccess;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// T[t] = exp(2 pi i t / n), evaluated in fp64 on the device and rounded to fp32.
+__global__ void twiddle_kernel(float2* tw_n, int n, float2* tw_m, int m) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) {
+    double s, c;
+    sincospi(2.0 * (double)t / (double)n, &s, &c);
+    tw_n[t] = make_float2((float)c, (float)s);
+  }
+  if (t < m) {
+    double s, c;
+    sincospi(2.0 * (double)t / (double)m, &s, &c);
+    tw_m[t] = make_float2((float)c, (float)s);
+  }
+}
+
+// The half grid in increasing row-major order, written arithmetically: row 0 and
+// (n even) row n/2 hold l = 0 .. floor(m/2); rows 1 .. ceil(n/2)-1 hold all l.
+__global__ void half_grid_kernel(int32_t* half, int n, int m, int F_h) {
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= F_h) return;
+  const int c0 = m / 2 + 1;
+  const int full_rows = (n - 1) / 2;       // rows j with 0 < j < n - j
+  int f;
+  if (h < c0) {
+    f = h;
+  } else if (h < c0 + full_rows * m) {
+    const int q = h - c0;
+    f = (1 + q / m) * m + q % m;
+  } else {
+    f = (n / 2) * m + (h - c0 - full_rows * m);
+  }
+  half[h] = f;
+}
+
+}  // namespace
+
+extern "C" lfa_status_t lfa_svd_backward_noalloc(const lfa_layer_desc_t* layer, uint32_t flags,
+                                                 const float* dsigma, const float* U, const float* V,
+                                                 float* dw, void* stream) {
+  using namespace lfa;
+  if (layer == nullptr || dsigma == nullptr || U == nullptr || V == nullptr || dw == nullptr)
+    return LFA_ERR_INVALID_ARG;
+  if (flags & ~(uint32_t)LFA_HALF_OUTPUT) return LFA_ERR_INVALID_ARG;
+  const lfa_layer_desc_t& d = *layer;
+  if (d.c_out < 1 || d.c_in < 1 || d.c_out > 512 || d.c_in > 512 || d.kh < 1 || d.kw < 1 || d.kh > 15 ||
+      d.kw > 15 || d.n < 1 || d.m < 1 || d.n > 65536 || d.m > 65536 || (int64_t)d.n * d.m > 0x7fffffffLL ||
+      d.pad_h < -1 || d.pad_h >= d.kh || d.pad_w < -1 || d.pad_w >= d.kw)
+    return LFA_ERR_INVALID_ARG;
+
+  LayerArgs La;
+  La.w = nullptr;
+  La.sigma = nullptr;
+  La.U = nullptr;
+  La.V = nullptr;
+  La.symbols = nullptr;
+  La.c_out = d.c_out; La.c_in = d.c_in; La.kh = d.kh; La.kw = d.kw; La.n = d.n; La.m = d.m;
+  La.ph = d.pad_h < 0 ? d.kh / 2 : d.pad_h;
+  La.pw = d.pad_w < 0 ? d.kw / 2 : d.pad_w;
+  La.r = d.c_out < d.c_in ? d.c_out : d.c_in;
+  La.M = d.c_out > d.c_in ? d.c_out : d.c_in;
+  La.N = La.r;
+  La.wide = d.c_in > d.c_out ? 1 : 0;
+  const int s_self = (1 + (d.n % 2 == 0)) * (1 + (d.m % 2 == 0));
+  La.F_h = (int)(((int64_t)d.n * d.m + s_self) / 2);
+  La.item_begin = 0;
+  La.tol2 = 0.f;
+
+  // scratch layout: half-grid list | twiddles n | twiddles m | partial sums | G workspace.
+  // The partial sums get at most half the array; G gets the rest and must hold one chunk.
+  const int64_t CC = (int64_t)d.c_out * d.c_in;
+  const int64_t kk = (int64_t)d.kh * d.kw;
+  const size_t fixed = align256((size_t)La.F_h * 4) + align256((size_t)d.n * 8) + align256((size_t)d.m * 8);
+  if (fixed >= kScratchBytes / 2) return LFA_ERR_UNSUPPORTED;
+  const size_t part_budget = kScratchBytes / 2 - fixed;
+  int64_t chunks = (int64_t)(part_budget / (size_t)(CC * kk * 4));
+  if (chunks < 1) return LFA_ERR_UNSUPPORTED;                       // one partial slab does not fit
+  chunks = chunks < La.F_h ? chunks : La.F_h;
+  chunks = chunks < 4096 ? chunks : 4096;
+  int64_t chunk = (La.F_h + chunks - 1) / chunks;
+  if (chunk > 65535) return LFA_ERR_UNSUPPORTED;
+  chunks = (La.F_h + chunk - 1) / chunk;
+  const size_t part_bytes = align256((size_t)(chunks * CC * kk * 4));
+  const size_t g_bytes = kScratchBytes - fixed - part_bytes;
+  const int64_t g_cap = (int64_t)(g_bytes / (size_t)(CC * 8));
+  if (g_cap < chunk) return LFA_ERR_UNSUPPORTED;                    // one chunk of G does not fit
+
+  unsigned char* base = nullptr;
+  cudaError_t e = scratch_for_current_device(&base);
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LFA_ERR_OOM : LFA_ERR_CUDA;
+  int32_t* half = reinterpret_cast<int32_t*>(base);
+  float2* tw_n = reinterpret_cast<float2*>(base + align256((size_t)La.F_h * 4));
+  float2* tw_m = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(tw_n) + align256((size_t)d.n * 8));
+  float* partial = reinterpret_cast<float*>(base + fixed);
+  float2* G = reinterpret_cast<float2*>(base + fixed + part_bytes);
+  La.half = half;
+  La.tw_n = tw_n;
+  La.tw_m = tw_m;
+
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int nm_max = d.n > d.m ? d.n : d.m;
+  twiddle_kernel<<<(nm_max + 255) / 256, 256, 0, s>>>(tw_n, d.n, tw_m, d.m);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    half_grid_kernel<<<(La.F_h + 255) / 256, 256, 0, s>>>(half, d.n, d.m, La.F_h);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    int nk = 0;
+    e = launch_backward(La, dsigma, (flags & LFA_HALF_OUTPUT) ? 1 : 0, reinterpret_cast<const float2*>(U),
+                        reinterpret_cast<const float2*>(V), G, g_cap, partial, (int)chunks, dw, s, &nk);
+  }
+  return e == cudaSuccess ? LFA_OK : LFA_ERR_CUDA;
+}

@@ -37,7 +37,8 @@ LFA_ERR_TIMEOUT = 7
 
 # every symbol include/lfa.h and include/lfa_debug.h declare
 EXPORTS = [
-    "lfa_plan", "lfa_svd", "lfa_symbols", "lfa_expand", "lfa_svd_backward", "lfa_regulariser_grad",
+    "lfa_plan", "lfa_svd", "lfa_symbols", "lfa_expand", "lfa_svd_backward", "lfa_svd_backward_noalloc",
+    "lfa_regulariser_grad",
     "lfa_destroy", "lfa_get_info", "lfa_layer_query", "lfa_status_string", "lfa_variant_name",
     "lfa_last_cuda_error", "lfa_kernel_launches", "lfa_version",
     "lfa_debug_schedule", "lfa_debug_half_grid", "lfa_debug_choose_variant", "lfa_debug_variant_count",
@@ -93,6 +94,7 @@ def lib():
         "lfa_symbols": (c_int32, [P, c_int32, P, P, P]),
         "lfa_expand": (c_int32, [P, c_int32, P, P, c_int64, c_int64, P, P, P]),
         "lfa_svd_backward": (c_int32, [P, PP, PP, PP, PP, P]),
+        "lfa_svd_backward_noalloc": (c_int32, [POINTER(LayerDesc), c_uint32, P, P, P, P, P]),
         "lfa_regulariser_grad": (c_int32, [P, PP, c_float, PP, PP, P]),
         "lfa_destroy": (c_int32, [P]),
         "lfa_get_info": (c_int32, [P, POINTER(Info)]),
@@ -179,6 +181,15 @@ def lfa_svd_backward(plan: int, dsigma: Sequence[int], U: Sequence[int], V: Sequ
     n = len(dw)
     _check(lib().lfa_svd_backward(c_void_p(plan), _ptrs(dsigma, n), _ptrs(U, n), _ptrs(V, n), _ptrs(dw, n),
                                   _stream(stream)), "lfa_svd_backward")
+
+
+def lfa_svd_backward_noalloc(layer, flags: int, dsigma: int, U: int, V: int, dw: int, stream=None) -> None:
+    """Backward of one layer without any device allocation (no plan); see include/lfa.h."""
+    d = tuple(int(x) for x in layer)
+    d = d if len(d) == 8 else d + (-1, -1)
+    desc = LayerDesc(*d)
+    _check(lib().lfa_svd_backward_noalloc(ctypes.byref(desc), int(flags), c_void_p(dsigma), c_void_p(U),
+                                          c_void_p(V), c_void_p(dw), _stream(stream)), "lfa_svd_backward_noalloc")
 
 
 def lfa_regulariser_grad(plan: int, sigma: Sequence[int], lam: float, dsigma: Sequence[int],
