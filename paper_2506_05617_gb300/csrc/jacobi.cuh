@@ -2,52 +2,64 @@
 // assembly (arXiv 2506.05617, Sec. III: symbol A_k = sum_y M_y exp(2 pi i <k,y>)
 // and its SVD A_k = U_k S_k V_k^*, Algorithm 1 lines 4-5).
 //
-// Design (sm_103a, one symbol per "team group"):
-//  * The N columns of X (X = A_k or A_k^*, M x N, N = r) are paired; each pair
-//    (p, q) is owned by a team of L lanes, each lane holding MR rows of x_p and
-//    x_q (and WR rows of the accumulated rotations w_p, w_q) in registers.
+// Design (sm_103a):
+//  * The N columns of X (X = A_k or A_k^*, M x N, N = r, padded to NC = 2 NP) are
+//    paired; each pair is owned by a team of L lanes, each lane holding MR rows of
+//    both columns of X (and WR rows of the accumulated rotations W) in registers.
 //    Rows are interleaved: lane l holds rows l, l + L, l + 2L, ...
-//  * One round: every team forms alpha = |x_p|^2, beta = |x_q|^2,
-//    gamma = x_p^* x_q (a butterfly over its L lanes) and applies the complex
-//    Jacobi rotation that makes x_p, x_q orthogonal when
-//    |gamma| > tol * sqrt(alpha beta). The N/2 pairs of a round are disjoint.
-//  * Rounds follow the circle-method round robin (all N(N-1)/2 pairs once per
-//    sweep). Teams are relabelled between rounds so that each team keeps one
-//    of its columns in registers and receives one through shared memory (half
-//    the columns move per round); at a sweep boundary every team reloads its
-//    round-0 pair. The schedule table is built on the host at plan time.
-//  * Sweeps repeat until no pair of a sweep was rotated (or max_sweeps).
-//    Singular values are the final column norms (recomputed, not updated);
-//    U (or V for wide symbols) columns are the normalised X columns; the other
-//    factor is the accumulated rotation matrix W.
+//  * One round: every team forms alpha = |x_p|^2, beta = |x_q|^2, gamma = x_p^* x_q
+//    by an xor butterfly over its L lanes (bitwise identical on every lane, so the
+//    team takes one decision) and, when |gamma| > tol sqrt(alpha beta), applies the
+//    complex rotation that makes x_p, x_q orthogonal, to X and W.
+//  * Rounds follow the circle-method round robin: at round t the pair at position i
+//    is (c(t+i), c(t-i)) for i >= 1 and (c(t), NC-1) for i = 0, c(x) = x mod NC-1.
+//    Between rounds the team at position i keeps one column and sends the other to
+//    the neighbouring position (0 -> 1, odd i -> i-1, even i -> i+1); teams move by
+//    the fixed involution pi = (1 2)(3 4)...(NP-3 NP-2), so team k sits at position k
+//    on even rounds and pi(k) on odd ones. Each team receives exactly one column per
+//    round into its own slot of a shared-memory mailbox (double-buffered by round
+//    parity, so one barrier per round suffices). No schedule table is needed.
+//  * With CS > 1 the teams of one symbol are spread over a thread-block cluster of CS
+//    CTAs; columns move through distributed shared memory and the per-round barrier
+//    is the cluster barrier. This keeps symbols up to 512 columns register-resident.
+//  * Sweeps (NC-1 rounds) repeat until no pair of a sweep rotates (or max_sweeps).
+//    sigma_p = |x_p| / |w_p| (recomputed), U (V for wide symbols) columns x_p/|x_p|,
+//    the other factor w_p/|w_p|.
 //  * Symbol assembly is fused: each lane assembles its own entries of X from the
-//    weights (read through L1/L2) and the k_h x k_w phase grid of the frequency,
-//    which is built in shared memory from the fp32 twiddle tables.
-//  * Work is pulled from a queue (one atomic ticket per item), so one persistent
-//    launch serves all layers of the same variant, with uneven F_h.
+//    weights (L1/L2) and the k_h x k_w phase grid of the frequency (shared memory).
+//  * Work items (symbol tiles) come from an atomic queue: one persistent launch per
+//    variant serves every layer of that variant.
 #pragma once
+
+#include <cooperative_groups.h>
 
 #include "lfa_internal.cuh"
 
 namespace lfa {
 
-template <int NP_, int L_, int MR_, int WR_, bool VEC_>
+namespace cg = cooperative_groups;
+
+template <int NP_, int L_, int MR_, int WR_, bool VEC_, int CS_>
 struct JCfg {
-  static constexpr int NP = NP_, L = L_, MR = MR_, WR = WR_;
+  static constexpr int NP = NP_, L = L_, MR = MR_, WR = WR_, CS = CS_;
   static constexpr bool VEC = VEC_;
-  static constexpr int T = NP * L;               // threads per symbol
-  static constexpr int UT = T <= 32 ? 32 : T;    // threads per unit (warp or CTA)
-  static constexpr int SPU = T <= 32 ? 32 / T : 1;
-  static constexpr int BLOCK = T <= 32 ? 128 : T;
-  static constexpr int UPB = BLOCK / UT;         // units per CTA
-  static constexpr int NC = 2 * NP;              // column slots (N padded to even)
-  static constexpr int XR = MR * L;              // X row capacity
-  static constexpr int WRC = WR * L;             // W row capacity (also staged when !VEC? no)
-  static constexpr int CS = XR + (VEC ? WRC : 0) + 2;   // mailbox column stride (float2)
-  static constexpr int MAILBOX = NC * CS;
-  static constexpr size_t SYM_BYTES = (size_t)(MAILBOX + kMaxTaps) * 8 + NC * 4 + 64;
+  static_assert(NP % 2 == 0 && NP % CS == 0, "pairs must be even and split evenly over the cluster");
+  static constexpr int TPC = NP / CS;             // teams per CTA
+  static constexpr int TC = TPC * L;              // threads per CTA per symbol
+  static constexpr int UT = TC <= 32 ? 32 : TC;   // threads per unit (a warp, or the CTA)
+  static constexpr int SPU = TC <= 32 ? 32 / TC : 1;
+  static constexpr int BLOCK = TC <= 32 ? 128 : TC;
+  static constexpr int UPB = BLOCK / UT;          // units per CTA
+  static constexpr int NC = 2 * NP;               // column slots
+  static constexpr int XR = MR * L;               // X row capacity
+  static constexpr int WRC = VEC ? WR * L : 0;    // W row capacity
+  // slot stride = L mod 16 (float2): neighbouring teams of a warp hit different banks
+  static constexpr int RS = XR + WRC + (((L - (XR + WRC)) % 16) + 16) % 16;
+  static constexpr int MBOX = 2 * TPC * RS;       // [parity][team][RS] float2
+  static constexpr size_t SYM_BYTES = (size_t)(MBOX + kMaxTaps) * 8 + NC * 4 + 64;
   static constexpr size_t UNIT_BYTES = SPU * SYM_BYTES + 64;
   static constexpr size_t SMEM = UPB * UNIT_BYTES;
+  static_assert((size_t)NC * (XR + WRC) <= (size_t)MBOX || CS > 1, "staging must fit the mailbox");
 };
 
 template <int T>
@@ -63,6 +75,15 @@ __device__ __forceinline__ float team_sum(float v) {
   return v;
 }
 
+// Barrier over the threads that share a symbol's data (warp, CTA or cluster).
+template <class C>
+__device__ __forceinline__ void sym_sync() {
+  if constexpr (C::CS > 1) cg::this_cluster().sync();
+  else if constexpr (C::UT == 32) __syncwarp();
+  else __syncthreads();
+}
+
+// Barrier over the threads of this CTA's unit.
 template <class C>
 __device__ __forceinline__ void unit_sync() {
   if constexpr (C::UT == 32) __syncwarp();
@@ -88,7 +109,14 @@ __device__ __forceinline__ float unit_sum(float v, float* red) {
   }
 }
 
-// Entry X[row][col] of the symbol of frequency (phases in `phs`), or 0 outside M x N.
+// The fixed team movement between rounds: (1 2)(3 4)...(NP-3 NP-2); 0 and NP-1 stay.
+template <int NP>
+__device__ __forceinline__ int pi_pos(int p) {
+  if (p == 0 || p == NP - 1) return p;
+  return (p & 1) ? p + 1 : p - 1;
+}
+
+// Entry X[row][col] of the symbol (phases in `phs`), or 0 outside M x N.
 template <bool FUSED>
 __device__ __forceinline__ float2 x_entry(const LayerArgs& La, int h, int row, int col,
                                           const float2* phs, int kk) {
@@ -112,25 +140,40 @@ __device__ __forceinline__ float2 x_entry(const LayerArgs& La, int h, int row, i
   return make_float2(re, La.wide ? -im : im);
 }
 
+// x_a' = x_a + cm1 x_a - conj(e s) x_b ; x_b' = x_b + cm1 x_b + (e s) x_a  (e s = sr + i si)
+__device__ __forceinline__ void rotate(float2& A, float2& B, float cm1, float sr, float si) {
+  const float2 a = A, b = B;
+  A.x = fmaf(cm1, a.x, a.x) - fmaf(sr, b.x, si * b.y);
+  A.y = fmaf(cm1, a.y, a.y) - fmaf(sr, b.y, -si * b.x);
+  B.x = fmaf(cm1, b.x, b.x) + fmaf(sr, a.x, -si * a.y);
+  B.y = fmaf(cm1, b.y, b.y) + fmaf(sr, a.y, si * a.x);
+}
+
 template <class C, bool FUSED>
 __global__ void __launch_bounds__(C::BLOCK)
 jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
-  constexpr int NP = C::NP, L = C::L, MR = C::MR, WR = C::WR, T = C::T, NC = C::NC;
-  constexpr int Cn = NC - 1;  // rounds per sweep
+  constexpr int NP = C::NP, L = C::L, MR = C::MR, WR = C::WR, TC = C::TC, NC = C::NC;
+  constexpr int TPC = C::TPC, CS = C::CS, RS = C::RS;
+  constexpr int Cn = NC - 1;      // rounds per sweep
+  constexpr int FIX = NC - 1;     // the column that stays at position 0
+  constexpr int WN = C::VEC ? WR : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
 
   const int unit = threadIdx.x / C::UT;
   const int ut = threadIdx.x % C::UT;
-  const int sym = ut / T;
-  const int st = ut % T;
-  const int team = st / L;
+  const int sym = ut / TC;
+  const int st = ut % TC;
+  const int lteam = st / L;
   const int lane = st % L;
+  int crank = 0;
+  if constexpr (CS > 1) crank = (int)cg::this_cluster().block_rank();
+  const int team = crank * TPC + lteam;
   unsigned char* ubase = smem_raw + (size_t)unit * C::UNIT_BYTES;
   float2* mbox = reinterpret_cast<float2*>(ubase + (size_t)sym * C::SYM_BYTES);
-  float2* phs = mbox + C::MAILBOX;
+  float2* phs = mbox + C::MBOX;
   float* ssig = reinterpret_cast<float*>(phs + kMaxTaps);
-  int* ubox = reinterpret_cast<int*>(ubase + (size_t)C::SPU * C::SYM_BYTES);  // item, flags
-  float* ured = reinterpret_cast<float*>(ubox + 4);                          // reductions
+  int* ubox = reinterpret_cast<int*>(ubase + (size_t)C::SPU * C::SYM_BYTES);  // item, vote[2], zeros
+  float* ured = reinterpret_cast<float*>(ubox + 4);
 
   Counters* ctr = P.counters;
   unsigned int* queue = &ctr->queue[P.queue_slot];
@@ -138,7 +181,17 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
   for (;;) {
     // ---------------------------------------------------------------- fetch a work item
     int item;
-    if constexpr (C::UT == 32) {
+    if constexpr (CS > 1) {
+      cg::cluster_group cl = cg::this_cluster();
+      if (crank == 0 && threadIdx.x == 0) {
+        const int it = (int)atomicAdd(queue, 1u);
+        for (int r = 0; r < CS; ++r) *cl.map_shared_rank(&ubox[0], r) = it;
+        ubox[1] = 0;
+        ubox[2] = 0;
+      }
+      cl.sync();
+      item = ubox[0];
+    } else if constexpr (C::UT == 32) {
       int v = 0;
       if (ut == 0) v = (int)atomicAdd(queue, 1u);
       item = __shfl_sync(0xffffffffu, v, 0);
@@ -158,10 +211,11 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
     const int f = active ? La.half[h] : 0;
     const int jj = f / La.m;
     const int ll = f - jj * La.m;
+    const int N = La.N, M = La.M;
 
     // ---------------------------------------------------------------- phases exp(2 pi i <k, y_ab>)
     if constexpr (FUSED) {
-      for (int t = st; t < kk; t += T) {
+      for (int t = st; t < kk; t += TC) {
         const int a = t / La.kw, b = t - a * La.kw;
         int ia = (jj * (a - La.ph)) % La.n;
         if (ia < 0) ia += La.n;
@@ -173,33 +227,31 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
       unit_sync<C>();
     }
 
-    // ---------------------------------------------------------------- assemble the round-0 pair
-    ushort2 cur = P.sched[team];
-    int ca = cur.x, cb = cur.y;
-    float2 xa[MR], xb[MR];
-    float2 wa[C::VEC ? WR : 1], wb[C::VEC ? WR : 1];
+    // ---------------------------------------------------------------- round-0 pair of this team
+    int ca = team;                        // c(0 + team)
+    int cb = team == 0 ? FIX : Cn - team; // c(0 - team), or the fixed column
+    float2 xa[MR], xb[MR], wa[WN], wb[WN];
 #pragma unroll
     for (int i = 0; i < MR; ++i) {
       const int row = lane + L * i;
       xa[i] = active ? x_entry<FUSED>(La, h, row, ca, phs, kk) : make_float2(0.f, 0.f);
       xb[i] = active ? x_entry<FUSED>(La, h, row, cb, phs, kk) : make_float2(0.f, 0.f);
     }
-    if constexpr (C::VEC) {
 #pragma unroll
-      for (int i = 0; i < WR; ++i) {
-        const int row = lane + L * i;
-        wa[i] = make_float2(row == ca && row < La.N ? 1.f : 0.f, 0.f);
-        wb[i] = make_float2(row == cb && row < La.N ? 1.f : 0.f, 0.f);
-      }
+    for (int i = 0; i < WN; ++i) {
+      const int row = lane + L * i;
+      wa[i] = make_float2(C::VEC && row == ca && row < N ? 1.f : 0.f, 0.f);
+      wb[i] = make_float2(C::VEC && row == cb && row < N ? 1.f : 0.f, 0.f);
     }
 
     // ---------------------------------------------------------------- sweeps
     const float tol2 = La.tol2;
     int sweeps = 0, nrot = 0;
     bool converged = false;
+    int t = 0;   // global round counter
     for (int sw = 0; sw < P.max_sweeps; ++sw) {
       int rotated = 0;
-      for (int rr = 0; rr < Cn; ++rr) {
+      for (int rr = 0; rr < Cn; ++rr, ++t) {
         float al = 0.f, be = 0.f, gr = 0.f, gi = 0.f;
 #pragma unroll
         for (int i = 0; i < MR; ++i) {
@@ -214,114 +266,89 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
         gi = team_sum<L>(gi);
         const float g2 = fmaf(gr, gr, gi * gi);
         if (g2 > tol2 * (al * be)) {
-          // rotation J = [[c, s e], [-s conj(e), c]] with e = gamma/|gamma|, t = tan:
-          // t solves t^2 + 2 zeta t - 1 = 0, zeta = (beta - alpha) / (2 |gamma|), |t| <= 1.
-          // Applied as x + (c - 1) x + ...: for small t, c rounds to 1 in fp32 and a rotation
-          // with c = 1, s = t would grow both norms by t^2/2; c - 1 = -t^2 / (r (1 + r)),
-          // r = sqrt(1 + t^2), keeps each rotation norm-preserving to O(eps t^2).
-          const float g = sqrtf(g2);
-          const float zeta = (be - al) / (2.f * g);
-          const float t = copysignf(1.f, zeta) / (fabsf(zeta) + hypotf(1.f, zeta));
-          const float rr2 = sqrtf(fmaf(t, t, 1.f));
-          const float cm1 = -(t * t) / (rr2 * (1.f + rr2));
-          const float s = t / rr2;
-          const float er = gr / g, ei = gi / g;
-          const float sr = s * er, si = s * ei;
+          // J = [[c, s e], [-s conj(e), c]], e = gamma/|gamma|, t = tan solves
+          // t^2 + 2 zeta t - 1 = 0 with zeta = (beta - alpha)/(2|gamma|), |t| <= 1.
+          // The angle may be approximate; unitarity rests on e, s and c-1, which are
+          // formed with correctly rounded reciprocals / reciprocal square roots.
+          // Applied as x + (c-1) x + ...: c - 1 = -t^2/(r(1+r)), r = sqrt(1+t^2) (for
+          // small t fp32 rounds c to 1, and c = 1, s = t would grow norms by t^2/2).
+          const float ig = __frsqrt_rn(g2);                  // 1/|gamma|
+          const float zeta = (be - al) * (0.5f * ig);
+          const float az = fabsf(zeta);
+          const float q = fmaf(az, az, 1.f);
+          const float hz = az < 1e18f ? q * rsqrtf(q) : az;  // ~ sqrt(1 + zeta^2)
+          const float tt = copysignf(__fdividef(1.f, az + hz), zeta);
+          const float r2 = fmaf(tt, tt, 1.f);
+          const float ir = __frsqrt_rn(r2);
+          const float s = tt * ir;
+          const float r = r2 * ir;
+          const float cm1 = -(tt * s) * __frcp_rn(1.f + r);
+          const float sr = s * (gr * ig), si = s * (gi * ig);
 #pragma unroll
-          for (int i = 0; i < MR; ++i) {
-            const float2 A = xa[i], B = xb[i];
-            xa[i].x = fmaf(cm1, A.x, A.x) - fmaf(sr, B.x, si * B.y);
-            xa[i].y = fmaf(cm1, A.y, A.y) - fmaf(sr, B.y, -si * B.x);
-            xb[i].x = fmaf(cm1, B.x, B.x) + fmaf(sr, A.x, -si * A.y);
-            xb[i].y = fmaf(cm1, B.y, B.y) + fmaf(sr, A.y, si * A.x);
-          }
+          for (int i = 0; i < MR; ++i) rotate(xa[i], xb[i], cm1, sr, si);
           if constexpr (C::VEC) {
 #pragma unroll
-            for (int i = 0; i < WR; ++i) {
-              const float2 A = wa[i], B = wb[i];
-              wa[i].x = fmaf(cm1, A.x, A.x) - fmaf(sr, B.x, si * B.y);
-              wa[i].y = fmaf(cm1, A.y, A.y) - fmaf(sr, B.y, -si * B.x);
-              wb[i].x = fmaf(cm1, B.x, B.x) + fmaf(sr, A.x, -si * A.y);
-              wb[i].y = fmaf(cm1, B.y, B.y) + fmaf(sr, A.y, si * A.x);
-            }
+            for (int i = 0; i < WR; ++i) rotate(wa[i], wb[i], cm1, sr, si);
           }
           rotated = 1;
           ++nrot;
         }
         // -------------------------------------------------------------- exchange
-        const int rn = (rr + 1 == Cn) ? 0 : rr + 1;
-        const ushort2 nx = P.sched[rn * NP + team];
-        if (rn != 0) {
-          // keep-one transition: exactly one of the team's columns stays in its slot
-          const bool keep_a = (nx.x == ca);
-          float2* dst = mbox + (keep_a ? cb : ca) * C::CS;
+        const int pos = (t & 1) ? pi_pos<NP>(team) : team;
+        int dp;
+        bool send_a, recv_a, shift;
+        if (pos == NP - 1) { send_a = true; dp = pos - 1; recv_a = false; shift = true; }
+        else if (pos == 0) { send_a = true; dp = 1; recv_a = true; shift = false; }
+        else if (pos & 1) { send_a = true; dp = pos - 1; recv_a = true; shift = false; }
+        else { send_a = false; dp = pos + 1; recv_a = false; shift = false; }
+        const int dest = ((t + 1) & 1) ? pi_pos<NP>(dp) : dp;
+        const int par = t & 1;
+        float2* dst = mbox + (size_t)(par * TPC + dest % TPC) * RS;
+        if constexpr (CS > 1) dst = cg::this_cluster().map_shared_rank(dst, dest / TPC);
 #pragma unroll
-          for (int i = 0; i < MR; ++i) dst[lane + L * i] = keep_a ? xb[i] : xa[i];
-          if constexpr (C::VEC) {
+        for (int i = 0; i < MR; ++i) dst[lane + L * i] = send_a ? xa[i] : xb[i];
+        if constexpr (C::VEC) {
 #pragma unroll
-            for (int i = 0; i < WR; ++i) dst[C::XR + lane + L * i] = keep_a ? wb[i] : wa[i];
-          }
-          unit_sync<C>();
-          const int in = keep_a ? nx.y : nx.x;
-          const float2* src = mbox + in * C::CS;
-          if (keep_a) {
+          for (int i = 0; i < WR; ++i) dst[C::XR + lane + L * i] = send_a ? wa[i] : wb[i];
+        }
+        if (shift) {
 #pragma unroll
-            for (int i = 0; i < MR; ++i) xb[i] = src[lane + L * i];
-            if constexpr (C::VEC) {
+          for (int i = 0; i < MR; ++i) xa[i] = xb[i];
 #pragma unroll
-              for (int i = 0; i < WR; ++i) wb[i] = src[C::XR + lane + L * i];
-            }
-            cb = in;
-          } else {
+          for (int i = 0; i < WN; ++i) wa[i] = wb[i];
+        }
+        sym_sync<C>();
+        const float2* src = mbox + (size_t)(par * TPC + lteam) * RS;
 #pragma unroll
-            for (int i = 0; i < MR; ++i) xa[i] = src[lane + L * i];
-            if constexpr (C::VEC) {
+        for (int i = 0; i < MR; ++i) {
+          const float2 v = src[lane + L * i];
+          xa[i] = recv_a ? v : xa[i];
+          xb[i] = recv_a ? xb[i] : v;
+        }
+        if constexpr (C::VEC) {
 #pragma unroll
-              for (int i = 0; i < WR; ++i) wa[i] = src[C::XR + lane + L * i];
-            }
-            ca = in;
-          }
-        } else {
-          // sweep boundary: every team reloads its round-0 pair
-          float2* da = mbox + ca * C::CS;
-          float2* db = mbox + cb * C::CS;
-#pragma unroll
-          for (int i = 0; i < MR; ++i) {
-            da[lane + L * i] = xa[i];
-            db[lane + L * i] = xb[i];
-          }
-          if constexpr (C::VEC) {
-#pragma unroll
-            for (int i = 0; i < WR; ++i) {
-              da[C::XR + lane + L * i] = wa[i];
-              db[C::XR + lane + L * i] = wb[i];
-            }
-          }
-          unit_sync<C>();
-          ca = nx.x;
-          cb = nx.y;
-          const float2* sa = mbox + ca * C::CS;
-          const float2* sb = mbox + cb * C::CS;
-#pragma unroll
-          for (int i = 0; i < MR; ++i) {
-            xa[i] = sa[lane + L * i];
-            xb[i] = sb[lane + L * i];
-          }
-          if constexpr (C::VEC) {
-#pragma unroll
-            for (int i = 0; i < WR; ++i) {
-              wa[i] = sa[C::XR + lane + L * i];
-              wb[i] = sb[C::XR + lane + L * i];
-            }
+          for (int i = 0; i < WR; ++i) {
+            const float2 v = src[C::XR + lane + L * i];
+            wa[i] = recv_a ? v : wa[i];
+            wb[i] = recv_a ? wb[i] : v;
           }
         }
       }
       ++sweeps;
       // a symbol has converged when none of its pairs rotated in this sweep
       bool any_sym, any_unit;
-      if constexpr (C::UT == 32) {
+      if constexpr (CS > 1) {
+        cg::cluster_group cl = cg::this_cluster();
+        const int q = sw & 1;
+        const int mine = __syncthreads_or(rotated);
+        if (threadIdx.x == 0 && mine) atomicOr(cl.map_shared_rank(&ubox[1 + q], 0), 1);
+        cl.sync();
+        any_unit = *cl.map_shared_rank(&ubox[1 + q], 0) != 0;
+        if (crank == 0 && threadIdx.x == 0) ubox[2 - q] = 0;   // the other parity, used next sweep
+        any_sym = any_unit;
+      } else if constexpr (C::UT == 32) {
         const unsigned bal = __ballot_sync(0xffffffffu, rotated != 0);
-        any_sym = (bal & sym_mask<T>(sym)) != 0u;
+        any_sym = (bal & sym_mask<TC>(sym)) != 0u;
         any_unit = bal != 0u;
       } else {
         any_unit = __syncthreads_or(rotated) != 0;
@@ -329,17 +356,23 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
       }
       if (!any_sym && !converged) {
         converged = true;
-        if (st == 0 && active) atomicAdd(&ctr->sweeps, (unsigned long long)sweeps);
+        if (st == 0 && crank == 0 && active) atomicAdd(&ctr->sweeps, (unsigned long long)sweeps);
       }
       if (!any_unit) break;
     }
-    if (!converged && st == 0 && active) {
+    if (!converged && st == 0 && crank == 0 && active) {
       atomicAdd(&ctr->sweeps, (unsigned long long)sweeps);
       atomicAdd(&ctr->unconverged, 1ull);
     }
     if (lane == 0 && nrot && active) atomicAdd(&ctr->rotations, (unsigned long long)nrot);
 
     // ---------------------------------------------------------------- singular values, order
+    {
+      const int pos = (t & 1) ? pi_pos<NP>(team) : team;
+      const int tm = t % Cn;
+      ca = (tm + pos) % Cn;
+      cb = pos == 0 ? FIX : (tm - pos + Cn) % Cn;
+    }
     float al = 0.f, be = 0.f;
 #pragma unroll
     for (int i = 0; i < MR; ++i) {
@@ -359,27 +392,37 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
       }
       qa = team_sum<L>(qa);
       qb = team_sum<L>(qb);
-      // x_p = A w_p exactly up to rounding, so sigma_p = |x_p| / |w_p| with v_p = w_p / |w_p|
+      // x_p = A w_p up to rounding, so sigma_p = |x_p| / |w_p| with v_p = w_p / |w_p|
       nwa = qa > 0.f ? sqrtf(qa) : 1.f;
       nwb = qb > 0.f ? sqrtf(qb) : 1.f;
       sa = sa / nwa;
       sb = sb / nwb;
     }
-    const int N = La.N, M = La.M;
     if (lane == 0) {
-      if (ca < N) ssig[ca] = sa;
-      if (cb < N) ssig[cb] = sb;
+      if constexpr (CS > 1) {
+        cg::cluster_group cl = cg::this_cluster();
+        for (int r = 0; r < CS; ++r) {
+          float* rs = cl.map_shared_rank(ssig, r);
+          if (ca < N) rs[ca] = sa;
+          if (cb < N) rs[cb] = sb;
+        }
+      } else {
+        if (ca < N) ssig[ca] = sa;
+        if (cb < N) ssig[cb] = sb;
+      }
     }
-    unit_sync<C>();
+    sym_sync<C>();
     int rka = 0, rkb = 0;
     bool finite = true;
+    float smax = 0.f;
     for (int q = 0; q < N; ++q) {
       const float v = ssig[q];
       finite = finite && isfinite(v);
+      smax = fmaxf(smax, v);
       rka += (v > sa) || (v == sa && q < ca);
       rkb += (v > sb) || (v == sb && q < cb);
     }
-    if (active && st == 0 && !finite) atomicAdd(&ctr->nonfinite, 1ull);
+    if (active && st == 0 && crank == 0 && !finite) atomicAdd(&ctr->nonfinite, 1ull);
     if (active && lane == 0) {
       const int r = La.r;
       float* row = La.sigma + (size_t)(P.half_output ? h : f) * r;
@@ -396,96 +439,121 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
     }
 
     if constexpr (C::VEC) {
-      // -------------------------------------------------------------- stage U / V by rank
-      // normalised X columns -> mailbox column `rank` rows [0, XR); W columns -> rows [XR, XR+WRC)
-      int* defc = ubox + 1;  // count of zero columns of this unit's symbols (any symbol)
-      if (ut == 0) *defc = 0;
-      unit_sync<C>();
-      const bool za = !(sa >= 1e-30f), zb = !(sb >= 1e-30f);   // zero (or NaN) column
-      const float ia = za ? 0.f : 1.f / sqrtf(al), ib = zb ? 0.f : 1.f / sqrtf(be);
+      // A column far below sigma_max (or whose squared norm is denormal) carries no direction:
+      // treat it as a zero singular value (or NaN) and complete it below.
+      const bool za = !(sa > 1e-12f * smax) || !(al > 1e-36f);
+      const bool zb = !(sb > 1e-12f * smax) || !(be > 1e-36f);
+      const float ia = za ? 0.f : __frsqrt_rn(al), ib = zb ? 0.f : __frsqrt_rn(be);
       const float iwa = 1.f / nwa, iwb = 1.f / nwb;
-      if (ca < N) {
-        float2* d = mbox + rka * C::CS;
+      float2* Xo = La.wide ? La.V : La.U;     // normalised X columns
+      float2* Wo = La.wide ? La.U : La.V;     // accumulated rotations
+      if constexpr (CS > 1) {
+        // columns are spread over the cluster: write them straight to their rank in HBM
+        if (active) {
+          float2* xo = Xo + (size_t)h * M * N;
+          float2* wo = Wo + (size_t)h * N * N;
 #pragma unroll
-        for (int i = 0; i < MR; ++i) d[lane + L * i] = make_float2(xa[i].x * ia, xa[i].y * ia);
+          for (int i = 0; i < MR; ++i) {
+            const int row = lane + L * i;
+            if (row < M) {
+              if (ca < N) xo[(size_t)row * N + rka] = make_float2(xa[i].x * ia, xa[i].y * ia);
+              if (cb < N) xo[(size_t)row * N + rkb] = make_float2(xb[i].x * ib, xb[i].y * ib);
+            }
+          }
 #pragma unroll
-        for (int i = 0; i < WR; ++i) d[C::XR + lane + L * i] = make_float2(wa[i].x * iwa, wa[i].y * iwa);
-        if (za && lane == 0) { ssig[ca] = -1.f; atomicAdd(defc, 1); }
-      }
-      if (cb < N) {
-        float2* d = mbox + rkb * C::CS;
-#pragma unroll
-        for (int i = 0; i < MR; ++i) d[lane + L * i] = make_float2(xb[i].x * ib, xb[i].y * ib);
-#pragma unroll
-        for (int i = 0; i < WR; ++i) d[C::XR + lane + L * i] = make_float2(wb[i].x * iwb, wb[i].y * iwb);
-        if (zb && lane == 0) { ssig[cb] = -1.f; atomicAdd(defc, 1); }
-      }
-      unit_sync<C>();
-      // -------------------------------------------------------------- complete zero columns
-      // A zero singular value leaves x_p = 0; its left vector is any unit vector orthogonal to
-      // the others: Gram-Schmidt of the canonical vectors e_k against the accepted columns.
-      if (*defc > 0) {
-        for (int sidx = 0; sidx < C::SPU; ++sidx) {
-          float2* mb = reinterpret_cast<float2*>(ubase + (size_t)sidx * C::SYM_BYTES);
-          float* sg = reinterpret_cast<float*>(mb + C::MAILBOX + kMaxTaps);
-          float2* tmp = mb + C::MAILBOX;  // phases are no longer needed
-          const int hh = (item - La.item_begin) * C::SPU + sidx;
-          if (hh >= La.F_h) continue;
-          // ranks of zero columns: sg[col] == -1; the rank order among them follows col index
-          int kstart = 0;
-          for (int d = 0; d < N; ++d) {
-            // rank d is zero if the column holding rank d has sg == -1; recover by counting
-            int zero_cnt = 0;
-            for (int q = 0; q < N; ++q) zero_cnt += (sg[q] == -1.f);
-            if (d < N - zero_cnt) continue;          // zero columns take the last ranks
-            for (int k = kstart; k < M; ++k) {
-              float nrm = 0.f;
-              for (int row = ut; row < M; row += C::UT) {
-                float vr = (row == k) ? 1.f : 0.f, vi = 0.f;
-                for (int q = 0; q < N; ++q) {
-                  if (q >= N - zero_cnt && q >= d) continue;  // not yet accepted
-                  const float2 uq = mb[q * C::CS + row];
-                  const float2 uk = mb[q * C::CS + k];
-                  // v -= u_q conj(u_q[k])
-                  vr -= uq.x * uk.x + uq.y * uk.y;
-                  vi -= uq.y * uk.x - uq.x * uk.y;
-                }
-                tmp[row] = make_float2(vr, vi);
-                nrm += vr * vr + vi * vi;
-              }
-              nrm = unit_sum<C>(nrm, ured);
-              if (nrm > 0.25f) {
-                const float inv = 1.f / sqrtf(nrm);
-                for (int row = ut; row < M; row += C::UT)
-                  mb[d * C::CS + row] = make_float2(tmp[row].x * inv, tmp[row].y * inv);
-                kstart = k + 1;
-                unit_sync<C>();
-                break;
-              }
-              unit_sync<C>();
+          for (int i = 0; i < WR; ++i) {
+            const int row = lane + L * i;
+            if (row < N) {
+              if (ca < N) wo[(size_t)row * N + rka] = make_float2(wa[i].x * iwa, wa[i].y * iwa);
+              if (cb < N) wo[(size_t)row * N + rkb] = make_float2(wb[i].x * iwb, wb[i].y * iwb);
             }
           }
         }
+      } else {
+        // ------------------------------------------------------------ stage U / V by rank
+        // mailbox column `rank`: normalised X rows [0, XR), W rows [XR, XR + WRC)
+        constexpr int CSx = C::XR + C::WRC;
+        int* defc = ubox + 3;
+        if (ut == 0) *defc = 0;
         unit_sync<C>();
-      }
-      // -------------------------------------------------------------- coalesced write-out
-      if (active) {
-        float2* Xo = La.wide ? La.V : La.U;     // normalised X columns
-        float2* Wo = La.wide ? La.U : La.V;     // accumulated rotations
-        float2* xo = Xo + (size_t)h * M * N;
-        for (int e = st; e < M * N; e += T) {
-          const int row = e / N, s = e - row * N;
-          xo[e] = mbox[s * C::CS + row];
+        if (ca < N) {
+          float2* d = mbox + (size_t)rka * CSx;
+#pragma unroll
+          for (int i = 0; i < MR; ++i) d[lane + L * i] = make_float2(xa[i].x * ia, xa[i].y * ia);
+#pragma unroll
+          for (int i = 0; i < WR; ++i) d[C::XR + lane + L * i] = make_float2(wa[i].x * iwa, wa[i].y * iwa);
+          if (za && lane == 0) { ssig[ca] = -1.f; atomicAdd(defc, 1); }
         }
-        float2* wo = Wo + (size_t)h * N * N;
-        for (int e = st; e < N * N; e += T) {
-          const int row = e / N, s = e - row * N;
-          wo[e] = mbox[s * C::CS + C::XR + row];
+        if (cb < N) {
+          float2* d = mbox + (size_t)rkb * CSx;
+#pragma unroll
+          for (int i = 0; i < MR; ++i) d[lane + L * i] = make_float2(xb[i].x * ib, xb[i].y * ib);
+#pragma unroll
+          for (int i = 0; i < WR; ++i) d[C::XR + lane + L * i] = make_float2(wb[i].x * iwb, wb[i].y * iwb);
+          if (zb && lane == 0) { ssig[cb] = -1.f; atomicAdd(defc, 1); }
+        }
+        unit_sync<C>();
+        // ------------------------------------------------------------ complete zero columns
+        // A zero singular value leaves x_p = 0; its left vector is any unit vector orthogonal
+        // to the others: Gram-Schmidt of the canonical vectors e_k against the accepted columns
+        // (the ranks before it), in rank order.
+        if (*defc > 0) {
+          for (int sidx = 0; sidx < C::SPU; ++sidx) {
+            float2* mb = reinterpret_cast<float2*>(ubase + (size_t)sidx * C::SYM_BYTES);
+            const float* sg = reinterpret_cast<const float*>(mb + C::MBOX + kMaxTaps);
+            float2* tmp = mb + C::MBOX;  // the phase grid is no longer needed
+            const int hh = (item - La.item_begin) * C::SPU + sidx;
+            if (hh >= La.F_h) continue;
+            int zc = 0;
+            for (int q = 0; q < N; ++q) zc += (sg[q] == -1.f);
+            int kstart = 0;
+            for (int d = N - zc; d < N; ++d) {
+              for (int k = kstart; k < M; ++k) {
+                float nrm = 0.f;
+                for (int row = ut; row < M; row += C::UT) {
+                  float vr = (row == k) ? 1.f : 0.f, vi = 0.f;
+                  for (int q = 0; q < d; ++q) {
+                    const float2 uq = mb[(size_t)q * CSx + row];
+                    const float2 uk = mb[(size_t)q * CSx + k];
+                    vr -= uq.x * uk.x + uq.y * uk.y;   // v -= u_q conj(u_q[k])
+                    vi -= uq.y * uk.x - uq.x * uk.y;
+                  }
+                  tmp[row] = make_float2(vr, vi);
+                  nrm += vr * vr + vi * vi;
+                }
+                nrm = unit_sum<C>(nrm, ured);
+                if (nrm > 0.25f) {
+                  const float inv = __frsqrt_rn(nrm);
+                  for (int row = ut; row < M; row += C::UT)
+                    mb[(size_t)d * CSx + row] = make_float2(tmp[row].x * inv, tmp[row].y * inv);
+                  kstart = k + 1;
+                  unit_sync<C>();
+                  break;
+                }
+                unit_sync<C>();
+              }
+            }
+          }
+          unit_sync<C>();
+        }
+        // ------------------------------------------------------------ coalesced write-out
+        if (active) {
+          float2* xo = Xo + (size_t)h * M * N;
+          for (int e = st; e < M * N; e += TC) {
+            const int row = e / N, s = e - row * N;
+            xo[e] = mbox[(size_t)s * CSx + row];
+          }
+          float2* wo = Wo + (size_t)h * N * N;
+          for (int e = st; e < N * N; e += TC) {
+            const int row = e / N, s = e - row * N;
+            wo[e] = mbox[(size_t)s * CSx + C::XR + row];
+          }
         }
       }
     }
-    unit_sync<C>();
+    sym_sync<C>();
   }
+  if constexpr (CS > 1) cg::this_cluster().sync();   // no CTA leaves while others may address it
 }
 
 }  // namespace lfa

@@ -1,84 +1,148 @@
 // Register-resident Jacobi variants: (pairs NP, lanes per pair L, X rows per lane MR,
-// W rows per lane WR). A variant serves symbols with M <= MR*L rows and
-// N <= min(2*NP, WR*L) columns (X = A_k or A_k^*, N = r = min(c_out, c_in)).
+// W rows per lane WR, CTAs per cluster CS, vectors supported). A variant serves symbols
+// with M <= MR*L rows and N <= 2*NP columns (with vectors also N <= WR*L), where
+// X = A_k or A_k^* and N = r = min(c_out, c_in). Variants with CS > 1 spread one symbol
+// over a thread-block cluster; vectors are instantiated only where they fit registers.
 #pragma once
 #include "jacobi.cuh"
 
-// X(id, NP, L, MR, WR)
-#define LFA_JACOBI_VARIANTS(X) \
-  X(0, 2, 4, 2, 1)             \
-  X(1, 2, 8, 8, 1)             \
-  X(2, 4, 4, 4, 2)             \
-  X(3, 4, 8, 8, 1)             \
-  X(4, 8, 4, 8, 4)             \
-  X(5, 8, 8, 8, 2)             \
-  X(6, 16, 8, 4, 4)            \
-  X(7, 16, 8, 8, 4)            \
-  X(8, 32, 8, 8, 8)            \
-  X(9, 32, 4, 16, 16)
+// X(id, NP, L, MR, WR, CS, VEC_OK)
+#define LFA_JACOBI_VARIANTS(X)     \
+  X(0, 2, 4, 2, 1, 1, 1)           \
+  X(1, 2, 8, 8, 1, 1, 1)           \
+  X(2, 4, 4, 4, 2, 1, 1)           \
+  X(3, 4, 8, 8, 1, 1, 1)           \
+  X(4, 8, 4, 8, 4, 1, 1)           \
+  X(5, 8, 8, 8, 2, 1, 1)           \
+  X(6, 16, 8, 4, 4, 1, 1)          \
+  X(7, 16, 8, 8, 4, 1, 1)          \
+  X(8, 32, 8, 8, 8, 1, 1)          \
+  X(9, 32, 4, 16, 16, 1, 1)        \
+  X(10, 32, 16, 8, 4, 1, 1)        \
+  X(11, 64, 16, 8, 8, 2, 1)        \
+  X(12, 64, 16, 8, 8, 1, 0)        \
+  X(13, 64, 32, 8, 4, 4, 1)        \
+  X(14, 128, 32, 8, 8, 8, 1)       \
+  X(15, 128, 32, 16, 8, 8, 0)      \
+  X(16, 256, 32, 16, 16, 16, 0)
 
 namespace lfa {
 
-template <int NP, int L, int MR, int WR, bool VEC, bool FUSED>
+template <int NP, int L, int MR, int WR, int CS, bool VEC, bool FUSED>
 cudaError_t jacobi_launch_t(const JacobiLaunch& P, int grid, cudaStream_t s) {
-  using C = JCfg<NP, L, MR, WR, VEC>;
-  jacobi_kernel<C, FUSED><<<grid, C::BLOCK, C::SMEM, s>>>(P);
-  return cudaGetLastError();
+  using C = JCfg<NP, L, MR, WR, VEC, CS>;
+  if constexpr (CS == 1) {
+    jacobi_kernel<C, FUSED><<<grid, C::BLOCK, C::SMEM, s>>>(P);
+    return cudaGetLastError();
+  } else {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid, 1, 1);
+    cfg.blockDim = dim3(C::BLOCK, 1, 1);
+    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, jacobi_kernel<C, FUSED>, P);
+  }
 }
 
-template <int NP, int L, int MR, int WR, bool VEC, bool FUSED>
+template <int NP, int L, int MR, int WR, int CS, bool VEC, bool FUSED>
 cudaError_t jacobi_prepare_t() {
-  using C = JCfg<NP, L, MR, WR, VEC>;
-  return cudaFuncSetAttribute(jacobi_kernel<C, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)C::SMEM);
+  using C = JCfg<NP, L, MR, WR, VEC, CS>;
+  cudaError_t e = cudaFuncSetAttribute(jacobi_kernel<C, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)C::SMEM);
+  if (e == cudaSuccess && CS > 8)
+    e = cudaFuncSetAttribute(jacobi_kernel<C, FUSED>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
 }
 
-template <int NP, int L, int MR, int WR, bool VEC, bool FUSED>
-cudaError_t jacobi_occupancy_t(int* blocks) {
-  using C = JCfg<NP, L, MR, WR, VEC>;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, jacobi_kernel<C, FUSED>, C::BLOCK,
-                                                       C::SMEM);
+// Largest grid (in CTAs) that is fully co-resident: blocks per SM x SMs, or clusters x CS.
+template <int NP, int L, int MR, int WR, int CS, bool VEC, bool FUSED>
+cudaError_t jacobi_grid_t(int sms, int* grid) {
+  using C = JCfg<NP, L, MR, WR, VEC, CS>;
+  if constexpr (CS == 1) {
+    int b = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, jacobi_kernel<C, FUSED>, C::BLOCK, C::SMEM);
+    *grid = b * sms;
+    return e;
+  } else {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(CS * 64), 1, 1);
+    cfg.blockDim = dim3(C::BLOCK, 1, 1);
+    cfg.dynamicSmemBytes = C::SMEM;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&nc, jacobi_kernel<C, FUSED>, &cfg);
+    *grid = nc * CS;
+    return e;
+  }
 }
 
-// Per-translation-unit dispatch over the variant list for one (VEC, FUSED) pair.
-#define LFA_DEFINE_JACOBI_DISPATCH(NAME, VEC, FUSED)                                        \
-  cudaError_t NAME##_launch(int id, const JacobiLaunch& P, int grid, cudaStream_t s) {    \
-    switch (id) {                                                                          \
-      LFA_JACOBI_VARIANTS(LFA_CASE_LAUNCH_##VEC##_##FUSED)                                 \
-      default: return cudaErrorInvalidValue;                                               \
-    }                                                                                      \
-  }                                                                                        \
-  cudaError_t NAME##_prepare(int id) {                                                     \
-    switch (id) {                                                                          \
-      LFA_JACOBI_VARIANTS(LFA_CASE_PREPARE_##VEC##_##FUSED)                                \
-      default: return cudaErrorInvalidValue;                                               \
-    }                                                                                      \
-  }                                                                                        \
-  cudaError_t NAME##_occupancy(int id, int* b) {                                           \
-    switch (id) {                                                                          \
-      LFA_JACOBI_VARIANTS(LFA_CASE_OCC_##VEC##_##FUSED)                                    \
-      default: return cudaErrorInvalidValue;                                               \
-    }                                                                                      \
+#define LFA_DEFINE_JACOBI_DISPATCH(NAME, VEC, FUSED)                                         \
+  cudaError_t NAME##_launch(int id, const JacobiLaunch& P, int grid, cudaStream_t s) {     \
+    switch (id) {                                                                           \
+      LFA_JACOBI_VARIANTS(LFA_CASE_LAUNCH_##VEC##_##FUSED)                                  \
+      default: return cudaErrorInvalidValue;                                                \
+    }                                                                                       \
+  }                                                                                         \
+  cudaError_t NAME##_prepare(int id) {                                                      \
+    switch (id) {                                                                           \
+      LFA_JACOBI_VARIANTS(LFA_CASE_PREPARE_##VEC##_##FUSED)                                 \
+      default: return cudaErrorInvalidValue;                                                \
+    }                                                                                       \
+  }                                                                                         \
+  cudaError_t NAME##_grid(int id, int sms, int* g) {                                        \
+    switch (id) {                                                                           \
+      LFA_JACOBI_VARIANTS(LFA_CASE_GRID_##VEC##_##FUSED)                                    \
+      default: return cudaErrorInvalidValue;                                                \
+    }                                                                                       \
   }
 
-#define LFA_CASE_LAUNCH_true_true(id, NP, L, MR, WR) case id: return jacobi_launch_t<NP, L, MR, WR, true, true>(P, grid, s);
-#define LFA_CASE_LAUNCH_false_true(id, NP, L, MR, WR) case id: return jacobi_launch_t<NP, L, MR, WR, false, true>(P, grid, s);
-#define LFA_CASE_LAUNCH_false_false(id, NP, L, MR, WR) case id: return jacobi_launch_t<NP, L, MR, WR, false, false>(P, grid, s);
-#define LFA_CASE_PREPARE_true_true(id, NP, L, MR, WR) case id: return jacobi_prepare_t<NP, L, MR, WR, true, true>();
-#define LFA_CASE_PREPARE_false_true(id, NP, L, MR, WR) case id: return jacobi_prepare_t<NP, L, MR, WR, false, true>();
-#define LFA_CASE_PREPARE_false_false(id, NP, L, MR, WR) case id: return jacobi_prepare_t<NP, L, MR, WR, false, false>();
-#define LFA_CASE_OCC_true_true(id, NP, L, MR, WR) case id: return jacobi_occupancy_t<NP, L, MR, WR, true, true>(b);
-#define LFA_CASE_OCC_false_true(id, NP, L, MR, WR) case id: return jacobi_occupancy_t<NP, L, MR, WR, false, true>(b);
-#define LFA_CASE_OCC_false_false(id, NP, L, MR, WR) case id: return jacobi_occupancy_t<NP, L, MR, WR, false, false>(b);
+// values-only instantiations exist for every variant; vector ones only where VEC_OK
+#define LFA_CASE_LAUNCH_false_true(id, NP, L, MR, WR, CS, OK) \
+  case id: return jacobi_launch_t<NP, L, MR, WR, CS, false, true>(P, grid, s);
+#define LFA_CASE_LAUNCH_false_false(id, NP, L, MR, WR, CS, OK) \
+  case id: return jacobi_launch_t<NP, L, MR, WR, CS, false, false>(P, grid, s);
+#define LFA_CASE_LAUNCH_true_true(id, NP, L, MR, WR, CS, OK)                              \
+  case id:                                                                                 \
+    if constexpr (OK) return jacobi_launch_t<NP, L, MR, WR, CS, true, true>(P, grid, s); \
+    else return cudaErrorInvalidValue;
+#define LFA_CASE_PREPARE_false_true(id, NP, L, MR, WR, CS, OK) \
+  case id: return jacobi_prepare_t<NP, L, MR, WR, CS, false, true>();
+#define LFA_CASE_PREPARE_false_false(id, NP, L, MR, WR, CS, OK) \
+  case id: return jacobi_prepare_t<NP, L, MR, WR, CS, false, false>();
+#define LFA_CASE_PREPARE_true_true(id, NP, L, MR, WR, CS, OK)                    \
+  case id:                                                                        \
+    if constexpr (OK) return jacobi_prepare_t<NP, L, MR, WR, CS, true, true>();  \
+    else return cudaErrorInvalidValue;
+#define LFA_CASE_GRID_false_true(id, NP, L, MR, WR, CS, OK) \
+  case id: return jacobi_grid_t<NP, L, MR, WR, CS, false, true>(sms, g);
+#define LFA_CASE_GRID_false_false(id, NP, L, MR, WR, CS, OK) \
+  case id: return jacobi_grid_t<NP, L, MR, WR, CS, false, false>(sms, g);
+#define LFA_CASE_GRID_true_true(id, NP, L, MR, WR, CS, OK)                           \
+  case id:                                                                            \
+    if constexpr (OK) return jacobi_grid_t<NP, L, MR, WR, CS, true, true>(sms, g);   \
+    else return cudaErrorInvalidValue;
 
 cudaError_t jacobi_vec_fused_launch(int id, const JacobiLaunch& P, int grid, cudaStream_t s);
 cudaError_t jacobi_vec_fused_prepare(int id);
-cudaError_t jacobi_vec_fused_occupancy(int id, int* b);
+cudaError_t jacobi_vec_fused_grid(int id, int sms, int* g);
 cudaError_t jacobi_val_fused_launch(int id, const JacobiLaunch& P, int grid, cudaStream_t s);
 cudaError_t jacobi_val_fused_prepare(int id);
-cudaError_t jacobi_val_fused_occupancy(int id, int* b);
+cudaError_t jacobi_val_fused_grid(int id, int sms, int* g);
 cudaError_t jacobi_val_plain_launch(int id, const JacobiLaunch& P, int grid, cudaStream_t s);
 cudaError_t jacobi_val_plain_prepare(int id);
-cudaError_t jacobi_val_plain_occupancy(int id, int* b);
+cudaError_t jacobi_val_plain_grid(int id, int sms, int* g);
 
 }  // namespace lfa

@@ -58,61 +58,27 @@ void build_half_grid(int n, int m, std::vector<int32_t>& out) {
 }
 
 // --------------------------------------------------------------------------- schedule
-// Circle-method round robin over NC columns (NC even): round t pairs the fixed column
-// NC-1 with t, and (t+i) with (t-i) mod NC-1 for i = 1 .. NC/2-1. Teams are relabelled
-// between consecutive rounds of a sweep by a bipartite matching so that every team keeps
-// one column (in its slot) and receives one. Returns false if a matching fails.
+// The Jacobi pair schedule the kernel follows, written out on the host (for tests): the
+// circle-method round robin over NC columns, team k at position k on even rounds and at
+// pi(k) on odd ones, pi = (1 2)(3 4)...(NP-3 NP-2). Position i holds (c(t+i), c(t-i)),
+// position 0 holds (c(t), NC-1), c(x) = x mod NC-1. Returns false for odd NC.
 bool build_schedule(int NC, std::vector<ushort2>& out) {
+  if (NC < 2 || (NC & 1)) return false;
   const int NP = NC / 2, Cn = NC - 1;
-  auto round_pairs = [&](int t, std::vector<std::pair<int, int>>& pr) {
-    pr.clear();
-    pr.push_back({NC - 1, t % Cn});
-    for (int i = 1; i < NP; ++i) pr.push_back({(t + i) % Cn, ((t - i) % Cn + Cn) % Cn});
-  };
-  std::vector<std::pair<int, int>> teams, pr;
-  round_pairs(0, teams);
+  auto pi = [&](int p) { return (p == 0 || p == NP - 1) ? p : ((p & 1) ? p + 1 : p - 1); };
   out.assign((size_t)Cn * NP, ushort2{0, 0});
-  for (int k = 0; k < NP; ++k) out[k] = ushort2{(unsigned short)teams[k].first, (unsigned short)teams[k].second};
-  for (int t = 1; t < Cn; ++t) {
-    round_pairs(t, pr);
-    auto shares = [&](int k, int i) {
-      const int a = teams[k].first, b = teams[k].second;
-      const int c = (pr[i].first == a || pr[i].first == b) + (pr[i].second == a || pr[i].second == b);
-      return c == 1;
-    };
-    std::vector<int> match_p(NP, -1);
-    std::vector<char> seen;
-    std::function<bool(int)> aug = [&](int k) -> bool {
-      for (int i = 0; i < NP; ++i) {
-        if (seen[i] || !shares(k, i)) continue;
-        seen[i] = 1;
-        if (match_p[i] < 0 || aug(match_p[i])) { match_p[i] = k; return true; }
-      }
-      return false;
-    };
+  for (int t = 0; t < Cn; ++t)
     for (int k = 0; k < NP; ++k) {
-      seen.assign(NP, 0);
-      if (!aug(k)) return false;
+      const int i = (t & 1) ? pi(k) : k;
+      const int a = (t + i) % Cn;
+      const int b = i == 0 ? NC - 1 : ((t - i) % Cn + Cn) % Cn;
+      out[(size_t)t * NP + k] = ushort2{(unsigned short)a, (unsigned short)b};
     }
-    std::vector<std::pair<int, int>> nt(NP);
-    for (int i = 0; i < NP; ++i) {
-      const int k = match_p[i];
-      int a = teams[k].first, b = teams[k].second;
-      const int p = pr[i].first, q = pr[i].second;
-      if (a == p || a == q) b = (a == p) ? q : p;   // keep a in slot 0
-      else a = (b == p) ? q : p;                     // keep b in slot 1
-      nt[k] = {a, b};
-    }
-    teams = nt;
-    for (int k = 0; k < NP; ++k)
-      out[(size_t)t * NP + k] = ushort2{(unsigned short)teams[k].first, (unsigned short)teams[k].second};
-  }
-  // every pair exactly once per sweep
   std::vector<char> hit((size_t)NC * NC, 0);
   for (int t = 0; t < Cn; ++t)
     for (int k = 0; k < NP; ++k) {
       const int a = out[(size_t)t * NP + k].x, b = out[(size_t)t * NP + k].y;
-      if (a == b || a >= NC || b >= NC) return false;
+      if (a == b) return false;
       const size_t idx = (size_t)std::min(a, b) * NC + std::max(a, b);
       if (hit[idx]) return false;
       hit[idx] = 1;
@@ -121,15 +87,15 @@ bool build_schedule(int NC, std::vector<ushort2>& out) {
 }
 
 // --------------------------------------------------------------------------- variants
-struct VDesc { int NP, L, MR, WR; };
+struct VDesc { int NP, L, MR, WR, CS, vec_ok; };
 const VDesc kVariants[] = {
-#define LFA_VD(id, NP, L, MR, WR) {NP, L, MR, WR},
+#define LFA_VD(id, NP, L, MR, WR, CS, OK) {NP, L, MR, WR, CS, OK},
     LFA_JACOBI_VARIANTS(LFA_VD)
 #undef LFA_VD
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 const char* kVariantNames[] = {
-#define LFA_VN(id, NP, L, MR, WR) "reg_np" #NP "_l" #L "_mr" #MR "_wr" #WR,
+#define LFA_VN(id, NP, L, MR, WR, CS, OK) "reg_np" #NP "_l" #L "_mr" #MR "_wr" #WR "_cs" #CS,
     LFA_JACOBI_VARIANTS(LFA_VN)
 #undef LFA_VN
 };
@@ -140,17 +106,24 @@ int variant_cols(int v, bool vec) {
   return vec ? std::min(c, kVariants[v].WR * kVariants[v].L) : c;
 }
 bool variant_fits(int v, int M, int N, bool vec) {
-  return v >= 0 && v < kNumVariants && M <= variant_rows(v) && N <= variant_cols(v, vec);
+  return v >= 0 && v < kNumVariants && (!vec || kVariants[v].vec_ok) && M <= variant_rows(v) &&
+         N <= variant_cols(v, vec);
 }
 // Default choice: the smallest padded problem (2*NP columns x MR*L rows) that holds M x N;
-// ties go to the larger team (more lanes per pair, fewer registers per lane).
+// ties go to the smaller cluster, then to the larger team (fewer registers per lane).
 int choose_variant(int M, int N, bool vec) {
   int best = -1;
   long best_area = 0;
   for (int v = 0; v < kNumVariants; ++v) {
     if (!variant_fits(v, M, N, vec)) continue;
     const long area = (long)(2 * kVariants[v].NP) * variant_rows(v);
-    if (best < 0 || area < best_area || (area == best_area && kVariants[v].L > kVariants[best].L)) {
+    bool better = best < 0 || area < best_area;
+    if (!better && area == best_area) {
+      const VDesc& a = kVariants[v];
+      const VDesc& b = kVariants[best];
+      better = a.CS < b.CS || (a.CS == b.CS && a.L > b.L);
+    }
+    if (better) {
       best = v;
       best_area = area;
     }
@@ -164,10 +137,10 @@ cudaError_t vprepare(int id, bool vec, bool fused) {
   if (!vec && !fused) return jacobi_val_plain_prepare(id);
   return cudaErrorInvalidValue;
 }
-cudaError_t voccupancy(int id, bool vec, bool fused, int* b) {
-  if (vec && fused) return jacobi_vec_fused_occupancy(id, b);
-  if (!vec && fused) return jacobi_val_fused_occupancy(id, b);
-  if (!vec && !fused) return jacobi_val_plain_occupancy(id, b);
+cudaError_t vgrid(int id, bool vec, bool fused, int sms, int* g) {
+  if (vec && fused) return jacobi_vec_fused_grid(id, sms, g);
+  if (!vec && fused) return jacobi_val_fused_grid(id, sms, g);
+  if (!vec && !fused) return jacobi_val_plain_grid(id, sms, g);
   return cudaErrorInvalidValue;
 }
 cudaError_t vlaunch(int id, bool vec, bool fused, const JacobiLaunch& P, int grid, cudaStream_t s) {
@@ -177,9 +150,10 @@ cudaError_t vlaunch(int id, bool vec, bool fused, const JacobiLaunch& P, int gri
   return cudaErrorInvalidValue;
 }
 int variant_spu(int id) {
-  const int T = kVariants[id].NP * kVariants[id].L;
-  return T <= 32 ? 32 / T : 1;
+  const int TC = kVariants[id].NP / kVariants[id].CS * kVariants[id].L;
+  return TC <= 32 ? 32 / TC : 1;
 }
+int variant_cs(int id) { return kVariants[id].CS; }
 
 // Optional autotuner cache: text lines "M N vec variant" (first match wins).
 int tuned_variant(const char* path, int M, int N, bool vec) {
@@ -216,7 +190,7 @@ struct lfa_plan_s {
   // variant groups: one persistent launch each
   struct Group { int variant; std::vector<int> layers; int items; int grid; };
   std::vector<Group> groups;
-  std::vector<const ushort2*> sched_dev;  // per variant id (NC) or null
+  std::vector<int> plain_grid;            // per layer (plain path)
   // device memory
   void* dmem = nullptr;
   size_t dbytes = 0;
@@ -281,14 +255,11 @@ lfa_status_t enqueue_forward(lfa_plan_s* p, const float* const* w, float* const*
       P.nlayers = 1;
       const int spu = variant_spu(p->variant[l]);
       P.total_items = (La.F_h + spu - 1) / spu;
-      P.sched = p->sched_dev[p->variant[l]];
       P.max_sweeps = p->max_sweeps;
       P.half_output = p->half_output;
       P.queue_slot = l % 16;
       P.counters = p->counters;
-      int occ = 1;
-      LFA_CUDA_TRY(voccupancy(p->variant[l], false, false, &occ));
-      const int grid = std::max(1, std::min(P.total_items, occ * p->sms));
+      const int grid = p->plain_grid[l];
       if (l >= 16) LFA_CUDA_TRY(cudaMemsetAsync(&p->counters->queue[l % 16], 0, sizeof(unsigned), s));
       LFA_CUDA_TRY(vlaunch(p->variant[l], false, false, P, grid, s));
       g_launches += 1;
@@ -312,7 +283,6 @@ lfa_status_t enqueue_forward(lfa_plan_s* p, const float* const* w, float* const*
     }
     P.nlayers = (int)g.layers.size();
     P.total_items = items;
-    P.sched = p->sched_dev[g.variant];
     P.max_sweeps = p->max_sweeps;
     P.half_output = p->half_output;
     P.queue_slot = slot++;
@@ -364,12 +334,12 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
   p->variant.resize(nlayers);
   p->half_host.resize(nlayers);
   p->bw_chunks.resize(nlayers);
+  p->plain_grid.assign(nlayers, 1);
 
   // ---- per-layer host tables and variant choice
   size_t bytes = align256(sizeof(Counters));
   std::vector<size_t> off_half(nlayers), off_twn(nlayers), off_twm(nlayers);
   size_t sym_bytes = 0, g_need = 0, part_bytes = 0;
-  std::vector<char> need_sched(kNumVariants, 0);
   for (int l = 0; l < nlayers; ++l) {
     const lfa_layer_desc_t& d = layers[l];
     LayerArgs& La = p->args[l];
@@ -391,7 +361,6 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
     if (v < 0) v = choose_variant(La.M, La.N, p->vec);
     if (v < 0) { free_plan(p); return LFA_ERR_UNSUPPORTED; }
     p->variant[l] = v;
-    need_sched[v] = 1;
     off_half[l] = bytes; bytes += align256((size_t)La.F_h * 4);
     off_twn[l] = bytes; bytes += align256((size_t)d.n * 8);
     off_twm[l] = bytes; bytes += align256((size_t)d.m * 8);
@@ -416,14 +385,6 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
       p->bw_chunks[l] = (int)chunks;
       part_bytes = std::max(part_bytes, (size_t)(chunks * CC * La.kh * La.kw * 4));
     }
-  }
-  std::vector<std::vector<ushort2>> sched(kNumVariants);
-  std::vector<size_t> off_sched(kNumVariants, 0);
-  for (int v = 0; v < kNumVariants; ++v) {
-    if (!need_sched[v]) continue;
-    if (!build_schedule(2 * kVariants[v].NP, sched[v])) { free_plan(p); return LFA_ERR_UNSUPPORTED; }
-    off_sched[v] = bytes;
-    bytes += align256(sched[v].size() * sizeof(ushort2));
   }
   const size_t off_sym = bytes; bytes += align256(sym_bytes);
   const size_t off_g = bytes; bytes += align256(g_bytes);
@@ -462,13 +423,6 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
     twiddles(La.m);
     e = cudaMemcpy(base + off_twm[l], tw.data(), (size_t)La.m * 8, cudaMemcpyHostToDevice);
   }
-  p->sched_dev.assign(kNumVariants, nullptr);
-  for (int v = 0; v < kNumVariants && e == cudaSuccess; ++v) {
-    if (!need_sched[v]) continue;
-    e = cudaMemcpy(base + off_sched[v], sched[v].data(), sched[v].size() * sizeof(ushort2),
-                   cudaMemcpyHostToDevice);
-    p->sched_dev[v] = reinterpret_cast<const ushort2*>(base + off_sched[v]);
-  }
   if (e == cudaSuccess) e = cudaMemset(p->counters, 0, sizeof(Counters));
   // ---- variant groups (one persistent launch per variant) and kernel attributes
   for (int v = 0; v < kNumVariants && e == cudaSuccess; ++v) {
@@ -484,12 +438,19 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
     const bool fused = !p->plain;
     e = vprepare(v, p->vec, fused);
     if (e != cudaSuccess) break;
-    int occ = 0;
-    e = voccupancy(v, p->vec, fused, &occ);
+    int full = 0;
+    e = vgrid(v, p->vec, fused, p->sms, &full);
     if (e != cudaSuccess) break;
-    if (occ < 1) { e = cudaErrorInvalidConfiguration; break; }
-    g.grid = std::max(1, std::min(g.items, occ * p->sms));
+    if (full < 1) { e = cudaErrorInvalidConfiguration; break; }
+    // a persistent grid: no more CTAs than can be co-resident, none without an item
+    const int cs = variant_cs(v);
+    g.grid = std::max(cs, std::min(g.items * cs, full) / cs * cs);
     p->groups.push_back(g);
+    if (p->plain)
+      for (int l : g.layers) {
+        const int items = (p->args[l].F_h + variant_spu(v) - 1) / variant_spu(v);
+        p->plain_grid[l] = std::max(cs, std::min(items * cs, full) / cs * cs);
+      }
   }
   if (e == cudaSuccess && p->groups.size() > 16) e = cudaErrorInvalidValue;
   if (e == cudaSuccess && p->use_graph) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);

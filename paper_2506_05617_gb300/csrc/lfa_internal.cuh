@@ -42,30 +42,11 @@ struct JacobiLaunch {
   LayerArgs L[kMaxLayers];
   int32_t nlayers;
   int32_t total_items;
-  const ushort2* sched;     // [NC - 1 rounds][NC / 2 teams] column ids (a, b)
   int32_t max_sweeps;
   int32_t half_output;
   int32_t queue_slot;
   Counters* counters;
 };
-
-// Host-side launchers implemented in the kernel translation units.
-struct VariantInfo {
-  int id;
-  int NP, L, MR, WR;        // pairs, lanes per pair, X rows per lane, W rows per lane
-  int block;                // threads per CTA
-  int spu;                  // symbols per work item
-  size_t smem;              // dynamic shared memory per CTA (bytes)
-  int max_rows;             // M capacity
-  int max_cols;             // N capacity
-};
-
-int jacobi_variant_count();
-const VariantInfo* jacobi_variant(int id);
-cudaError_t jacobi_prepare(int id, bool vec, bool fused);             // set smem attributes
-cudaError_t jacobi_occupancy(int id, bool vec, bool fused, int* blocks_per_sm);
-cudaError_t jacobi_launch(int id, bool vec, bool fused, const JacobiLaunch& P, int grid,
-                          cudaStream_t s);
 
 // Auxiliary kernels (aux_kernels.cu).
 cudaError_t launch_symbols(const LayerArgs& La, float2* out, cudaStream_t s);

@@ -1,0 +1,136 @@
+"""Parity of the large-channel kernels (one symbol per CTA with up to 1024 threads, or per
+thread-block cluster of 2 to 16 CTAs) with the FP64 oracle, and the full-size multi-layer
+workloads checked on sampled frequencies and by identities that hold at any size.
+
+Tolerances as in test_gpu_parity.py: sigma within 1e-5 * sigma_max; vectors by residual,
+reconstruction and orthonormality within 1e-5 (* sigma_max where scaled)."""
+import numpy as np
+import pytest
+import torch
+
+import lfa_workloads as W
+import oracle as O
+from paper_2506_05617_gb300 import lfa as C
+from paper_2506_05617_gb300.torch_api import LfaPlan
+
+from test_gpu_parity import check_sigma, check_vectors, gpu_svd, rand_w, SIG_TOL, VEC_TOL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_05617_gb300 import build as B
+    B.build()
+
+
+LARGE = [
+    # c_out, c_in, k, n, m, vectors
+    (128, 64, 3, 4, 3, True),     # tall 128 x 64
+    (64, 128, 3, 3, 4, True),     # wide
+    (128, 128, 3, 4, 3, True),    # cluster of 2
+    (128, 128, 3, 4, 3, False),   # one CTA of 1024 threads
+    (100, 77, 3, 3, 3, True),     # ragged
+    (256, 128, 3, 3, 3, True),    # cluster of 4
+    (256, 256, 3, 3, 2, True),    # cluster of 8
+    (200, 200, 1, 2, 3, True),
+    (256, 256, 3, 3, 3, False),
+    (512, 256, 3, 2, 3, False),   # cluster of 8, 16 rows per lane
+    (512, 512, 3, 2, 3, False),   # cluster of 16
+    (300, 450, 3, 2, 2, False),
+]
+
+
+@pytest.mark.parametrize("spec", LARGE, ids=lambda s: "x".join(str(v) for v in s[:5]) + ("v" if s[5] else ""))
+def test_large_channels_match_oracle(spec):
+    c_out, c_in, k, n, m, vec = spec
+    w = rand_w(c_out, c_in, k, k, seed=c_out + 7 * c_in)
+    plan, (s, U, V), st, info = gpu_svd(w, n, m, vectors=vec)
+    assert st == C.LFA_OK, info
+    check_sigma(w, n, m, s)
+    assert np.all(np.diff(s, axis=1) <= 0)
+    if vec:
+        check_vectors(w, n, m, s, U, V)
+    plan.close()
+
+
+def test_large_backward_matches_oracle():
+    c_out, c_in, k, n, m = 128, 96, 3, 3, 4
+    w = rand_w(c_out, c_in, k, k, seed=5)
+    g = W.upstream_gradient((n * m, min(c_out, c_in)), seed=6)
+    plan, (s, U, V), st, _ = gpu_svd(w, n, m)
+    dw = plan.backward([torch.from_numpy(g).cuda()], [torch.from_numpy(U).cuda()],
+                       [torch.from_numpy(V).cuda()])[0].cpu().numpy()
+    s_ref, U_ref, V_ref = O.lfa_svd(w, n, m)
+    dw_ref = O.lfa_backward(w, n, m, g, U_ref, V_ref)
+    assert np.linalg.norm(dw - dw_ref) / np.linalg.norm(dw_ref) <= 1e-4
+    plan.close()
+
+
+def sampled_sigma_check(w, lay, s, nsample, seed):
+    rng = np.random.default_rng(seed)
+    fr = np.sort(rng.choice(lay.F, min(nsample, lay.F), replace=False))
+    s_ref = O.lfa_svd(w, lay.n, lay.m, compute_uv=False, freqs=fr)
+    # sigma_max of the whole layer from the GPU values (checked against the oracle's sample)
+    smax = float(s.max())
+    assert np.max(np.abs(s[fr].astype(np.float64) - s_ref)) <= SIG_TOL * smax
+    # Parseval over every frequency: sum sigma^2 = n m ||w||_F^2 (k <= n)
+    np.testing.assert_allclose(np.sum(s.astype(np.float64) ** 2), lay.n * lay.m * np.sum(w.astype(np.float64) ** 2),
+                               rtol=2e-5)
+
+
+def test_resnet18_body_all_layers_one_plan():
+    """The 16-layer ResNet-18-shaped stack (uneven c_out, c_in and n) in one plan, values only."""
+    lays = W.layers("resnet18_body")
+    ws = [W.weights(l) for l in lays]
+    plan = LfaPlan([(l.c_out, l.c_in, l.kh, l.kw, l.n, l.m) for l in lays], vectors=False)
+    sig, _, _ = plan.svd([torch.from_numpy(w).cuda() for w in ws])
+    torch.cuda.synchronize()
+    st, info = plan.info()
+    assert st == C.LFA_OK, info
+    assert info["symbols"] == sum((l.F + (1 + (l.n % 2 == 0)) * (1 + (l.m % 2 == 0))) // 2 for l in lays)
+    for i, (l, w, s) in enumerate(zip(lays, ws, sig)):
+        sampled_sigma_check(w, l, s.cpu().numpy(), 24, seed=i)
+    plan.close()
+
+
+def test_regulariser_workload_c128_full_size():
+    """4 layers 128->128 on 32x32, k = 3, 5, 3, 5: values + vectors + backward.
+
+    Checks at full size: sampled sigma against the oracle, residuals of sampled symbols, and the
+    closed-form gradient of sum sigma^2 (= 2 n m w) through the hand-written backward."""
+    lays = W.layers("reg4_c128_n32")
+    ws = [W.weights(l) for l in lays]
+    plan = LfaPlan([(l.c_out, l.c_in, l.kh, l.kw, l.n, l.m) for l in lays], vectors=True)
+    sig, U, V = plan.svd([torch.from_numpy(w).cuda() for w in ws])
+    torch.cuda.synchronize()
+    st, info = plan.info()
+    assert st == C.LFA_OK, info
+    dw = plan.backward([2 * s for s in sig], U, V)
+    for i, (l, w) in enumerate(zip(lays, ws)):
+        s = sig[i].cpu().numpy()
+        sampled_sigma_check(w, l, s, 16, seed=10 + i)
+        half = O.half_grid(l.n, l.m)
+        pick = np.random.default_rng(i).choice(len(half), 8, replace=False)
+        S = O.symbols(w, l.n, l.m, freqs=half[pick])
+        Uu = U[i][torch.from_numpy(pick).cuda()].cpu().numpy().astype(np.complex128)
+        Vv = V[i][torch.from_numpy(pick).cuda()].cpu().numpy().astype(np.complex128)
+        ss = s[half[pick]].astype(np.float64)
+        res = np.einsum("hoi,his->hos", S, Vv) - Uu * ss[:, None, :]
+        assert np.max(np.linalg.norm(res, axis=1)) <= VEC_TOL * s.max()
+        assert np.max(np.abs(np.einsum("hos,hot->hst", np.conj(Vv), Vv) - np.eye(l.r))) <= VEC_TOL
+        ref = 2 * l.n * l.m * w.astype(np.float64)
+        got = dw[i].cpu().numpy()
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-4
+    plan.close()
+
+
+def test_conv512_values_sampled():
+    lay = W.layers("conv512_k3_n64")[0]
+    w = W.weights(lay)
+    plan, (s, _, _), st, info = gpu_svd(w, lay.n, lay.m, vectors=False)
+    assert st == C.LFA_OK, info
+    sampled_sigma_check(w, lay, s, 6, seed=3)
+    plan.close()

@@ -51,7 +51,7 @@ def test_schedule_covers_every_pair_once_and_keeps_one_column(ncols):
             seen.add((min(a, b), max(a, b)))
         if t + 1 < len(rounds):
             for (a, b), (a2, b2) in zip(rnd, rounds[t + 1]):
-                assert (a == a2) != (b == b2)               # exactly one column kept, in its slot
+                assert len({a, b} & {a2, b2}) == 1          # each team keeps exactly one column
     assert len(seen) == ncols * (ncols - 1) // 2
 
 
@@ -62,16 +62,19 @@ def test_half_grid_matches_oracle(n, m):
 
 def test_variant_choice():
     assert C.lfa_debug_variant_count() >= 9
-    for M, N in [(4, 4), (64, 3), (64, 64), (32, 32), (16, 8), (64, 16), (1, 1)]:
+    for M, N in [(4, 4), (64, 3), (64, 64), (32, 32), (16, 8), (64, 16), (1, 1), (128, 64), (128, 128),
+                 (256, 128), (256, 256)]:
         for vec in (False, True):
             v = C.lfa_debug_choose_variant(M, N, vec)
             assert v >= 0, (M, N, vec)
             name = C.lfa_variant_name(v)
-            npairs, lanes, mr, wr = (int(x) for x in re.findall(r"\d+", name))
+            npairs, lanes, mr, wr, cs = (int(x) for x in re.findall(r"\d+", name))
             assert M <= mr * lanes and N <= 2 * npairs
             if vec:
                 assert N <= wr * lanes
-    assert C.lfa_debug_choose_variant(65, 8, True) == -1
+    assert C.lfa_debug_choose_variant(513, 8, True) == -1
+    assert C.lfa_debug_choose_variant(512, 512, True) == -1      # vectors at c = 512 need more registers
+    assert C.lfa_debug_choose_variant(512, 512, False) >= 0
     assert C.lfa_variant_name(-1) == "none"
 
 
