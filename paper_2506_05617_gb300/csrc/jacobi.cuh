@@ -56,7 +56,7 @@ struct JCfg {
   // slot stride = L mod 16 (float2): neighbouring teams of a warp hit different banks
   static constexpr int RS = XR + WRC + (((L - (XR + WRC)) % 16) + 16) % 16;
   static constexpr int MBOX = 2 * TPC * RS;       // [parity][team][RS] float2
-  static constexpr size_t SYM_BYTES = (size_t)(MBOX + kMaxTaps) * 8 + NC * 4 + 64;
+  static constexpr size_t SYM_BYTES = (size_t)(MBOX + kMaxTaps) * 8 + NC * 4 + 2 * TPC * 4 + 64;
   static constexpr size_t UNIT_BYTES = SPU * SYM_BYTES + 64;
   static constexpr size_t SMEM = UPB * UNIT_BYTES;
   static_assert((size_t)NC * (XR + WRC) <= (size_t)MBOX || CS > 1, "staging must fit the mailbox");
@@ -140,13 +140,90 @@ __device__ __forceinline__ float2 x_entry(const LayerArgs& La, int h, int row, i
   return make_float2(re, La.wide ? -im : im);
 }
 
-// x_a' = x_a + cm1 x_a - conj(e s) x_b ; x_b' = x_b + cm1 x_b + (e s) x_a  (e s = sr + i si)
+// x_a' = x_a + cm1 x_a - conj(e s) x_b ; x_b' = x_b + cm1 x_b + (e s) x_a  (e s = sr + i si),
+// three fused multiply-adds per real component.
 __device__ __forceinline__ void rotate(float2& A, float2& B, float cm1, float sr, float si) {
   const float2 a = A, b = B;
-  A.x = fmaf(cm1, a.x, a.x) - fmaf(sr, b.x, si * b.y);
-  A.y = fmaf(cm1, a.y, a.y) - fmaf(sr, b.y, -si * b.x);
-  B.x = fmaf(cm1, b.x, b.x) + fmaf(sr, a.x, -si * a.y);
-  B.y = fmaf(cm1, b.y, b.y) + fmaf(sr, a.y, si * a.x);
+  A.x = fmaf(-sr, b.x, fmaf(-si, b.y, fmaf(cm1, a.x, a.x)));
+  A.y = fmaf(-sr, b.y, fmaf(si, b.x, fmaf(cm1, a.y, a.y)));
+  B.x = fmaf(sr, a.x, fmaf(-si, a.y, fmaf(cm1, b.x, b.x)));
+  B.y = fmaf(sr, a.y, fmaf(si, a.x, fmaf(cm1, b.y, b.y)));
+}
+
+// One Jacobi round on the team's pair (x0, x1) (symmetric in the two columns): dots, butterfly,
+// rotation of X and W. Returns whether a rotation was applied.
+template <class C>
+__device__ __forceinline__ bool pair_step(float2 (&x0)[C::MR], float2 (&x1)[C::MR], float2 (&w0)[C::VEC ? C::WR : 1],
+                                          float2 (&w1)[C::VEC ? C::WR : 1], float tol2) {
+  constexpr int MR = C::MR, WR = C::WR, L = C::L;
+  float al = 0.f, be = 0.f, gr = 0.f, gi = 0.f;
+#pragma unroll
+  for (int i = 0; i < MR; ++i) {
+    al = fmaf(x0[i].x, x0[i].x, fmaf(x0[i].y, x0[i].y, al));
+    be = fmaf(x1[i].x, x1[i].x, fmaf(x1[i].y, x1[i].y, be));
+    gr = fmaf(x0[i].x, x1[i].x, fmaf(x0[i].y, x1[i].y, gr));   // Re(conj(x0) x1)
+    gi = fmaf(x0[i].x, x1[i].y, fmaf(-x0[i].y, x1[i].x, gi));  // Im(conj(x0) x1)
+  }
+  al = team_sum<L>(al);
+  be = team_sum<L>(be);
+  gr = team_sum<L>(gr);
+  gi = team_sum<L>(gi);
+  const float g2 = fmaf(gr, gr, gi * gi);
+  if (!(g2 > tol2 * (al * be))) return false;
+  // J = [[c, s e], [-s conj(e), c]], e = gamma/|gamma|, t = tan solves t^2 + 2 zeta t - 1 = 0
+  // with zeta = (beta - alpha)/(2|gamma|), |t| <= 1. The angle may be approximate; unitarity
+  // rests on e, s and c-1, which are formed with correctly rounded reciprocals / reciprocal
+  // square roots. Applied as x + (c-1) x + ...: c - 1 = -t^2/(r(1+r)), r = sqrt(1+t^2) (for
+  // small t fp32 rounds c to 1, and c = 1, s = t would grow norms by t^2/2).
+  const float ig = __frsqrt_rn(g2);                  // 1/|gamma|
+  const float zeta = (be - al) * (0.5f * ig);
+  const float az = fabsf(zeta);
+  const float q = fmaf(az, az, 1.f);
+  const float hz = az < 1e18f ? q * rsqrtf(q) : az;  // ~ sqrt(1 + zeta^2)
+  const float tt = copysignf(__fdividef(1.f, az + hz), zeta);
+  const float r2 = fmaf(tt, tt, 1.f);
+  const float ir = __frsqrt_rn(r2);
+  const float s = tt * ir;
+  const float r = r2 * ir;
+  const float cm1 = -(tt * s) * __frcp_rn(1.f + r);
+  const float sr = s * (gr * ig), si = s * (gi * ig);
+#pragma unroll
+  for (int i = 0; i < MR; ++i) rotate(x0[i], x1[i], cm1, sr, si);
+  if constexpr (C::VEC) {
+#pragma unroll
+    for (int i = 0; i < WR; ++i) rotate(w0[i], w1[i], cm1, sr, si);
+  }
+  return true;
+}
+
+// Write array `xa` (W part `wa`, column id `ida`) to a mailbox slot. No barrier inside: the
+// caller may branch around this (team 0 moves a different array); the barrier that follows
+// must be reached by every thread in uniform control flow (aligned CTA / cluster barriers).
+template <class C>
+__device__ __forceinline__ void put_column(const float2 (&xa)[C::MR], const float2 (&wa)[C::VEC ? C::WR : 1],
+                                           int ida, float2* dst, int* dst_id, int lane) {
+  constexpr int MR = C::MR, WR = C::WR, L = C::L;
+#pragma unroll
+  for (int i = 0; i < MR; ++i) dst[lane + L * i] = xa[i];
+  if constexpr (C::VEC) {
+#pragma unroll
+    for (int i = 0; i < WR; ++i) dst[C::XR + lane + L * i] = wa[i];
+  }
+  if (lane == 0) *dst_id = ida;
+}
+
+// Read this team's mailbox slot into array `xa` (after the barrier).
+template <class C>
+__device__ __forceinline__ void get_column(float2 (&xa)[C::MR], float2 (&wa)[C::VEC ? C::WR : 1], int& ida,
+                                           const float2* src, const int* src_id, int lane) {
+  constexpr int MR = C::MR, WR = C::WR, L = C::L;
+#pragma unroll
+  for (int i = 0; i < MR; ++i) xa[i] = src[lane + L * i];
+  if constexpr (C::VEC) {
+#pragma unroll
+    for (int i = 0; i < WR; ++i) wa[i] = src[C::XR + lane + L * i];
+  }
+  ida = *src_id;
 }
 
 template <class C, bool FUSED>
@@ -177,6 +254,34 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
 
   Counters* ctr = P.counters;
   unsigned int* queue = &ctr->queue[P.queue_slot];
+
+  // Mailbox addresses for the two round parities (loop invariant). Position at even rounds
+  // is the team index, at odd rounds pi(team); the column a position sends goes to the
+  // neighbouring position (0 -> 1, odd -> i-1, even -> i+1), held after the move by team
+  // dp (next round odd) or pi(dp) (next round even).
+  float2 *dst_e, *dst_o;
+  int *dst_id_e, *dst_id_o;
+  int* mids = reinterpret_cast<int*>(ssig + NC);   // column ids that travel with the columns
+  {
+    auto target = [&](int pos) { return pos == 0 ? 1 : ((pos & 1) ? pos - 1 : pos + 1); };
+    const int dest_e = pi_pos<NP>(target(team));           // sent at an even round
+    const int dest_o = target(pi_pos<NP>(team));           // sent at an odd round
+    dst_e = mbox + (size_t)(0 * TPC + dest_e % TPC) * RS;
+    dst_o = mbox + (size_t)(1 * TPC + dest_o % TPC) * RS;
+    dst_id_e = mids + 0 * TPC + dest_e % TPC;
+    dst_id_o = mids + 1 * TPC + dest_o % TPC;
+    if constexpr (CS > 1) {
+      cg::cluster_group cl = cg::this_cluster();
+      dst_e = cl.map_shared_rank(dst_e, dest_e / TPC);
+      dst_o = cl.map_shared_rank(dst_o, dest_o / TPC);
+      dst_id_e = cl.map_shared_rank(dst_id_e, dest_e / TPC);
+      dst_id_o = cl.map_shared_rank(dst_id_o, dest_o / TPC);
+    }
+  }
+  const float2* src_e = mbox + (size_t)(0 * TPC + lteam) * RS;
+  const float2* src_o = mbox + (size_t)(1 * TPC + lteam) * RS;
+  const int* src_id_e = mids + 0 * TPC + lteam;
+  const int* src_id_o = mids + 1 * TPC + lteam;
 
   for (;;) {
     // ---------------------------------------------------------------- fetch a work item
@@ -228,118 +333,42 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
     }
 
     // ---------------------------------------------------------------- round-0 pair of this team
-    int ca = team;                        // c(0 + team)
-    int cb = team == 0 ? FIX : Cn - team; // c(0 - team), or the fixed column
-    float2 xa[MR], xb[MR], wa[WN], wb[WN];
+    // Two register arrays per team. Every team except team 0 keeps its newest column and
+    // sends its older one, so at round t the column that moves is the one in array (t & 1):
+    // arrays alternate by round parity and the moving array is static in the 2-way unrolled
+    // loop. Team 0 keeps the fixed column NC-1 in array 0 and moves array 1 every round.
+    // Round 0: position k holds (c(k), c(-k)), or (c(0), NC-1) for k = 0; the column that
+    // leaves first goes to array 0 (array 1 for team 0).
+    int id0, id1;
+    if (team == 0) { id0 = FIX; id1 = 0; }
+    else if ((team & 1) || team == NP - 1) { id0 = team; id1 = Cn - team; }
+    else { id0 = Cn - team; id1 = team; }
+    float2 x0[MR], x1[MR], w0[WN], w1[WN];
 #pragma unroll
     for (int i = 0; i < MR; ++i) {
       const int row = lane + L * i;
-      xa[i] = active ? x_entry<FUSED>(La, h, row, ca, phs, kk) : make_float2(0.f, 0.f);
-      xb[i] = active ? x_entry<FUSED>(La, h, row, cb, phs, kk) : make_float2(0.f, 0.f);
+      x0[i] = active ? x_entry<FUSED>(La, h, row, id0, phs, kk) : make_float2(0.f, 0.f);
+      x1[i] = active ? x_entry<FUSED>(La, h, row, id1, phs, kk) : make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int i = 0; i < WN; ++i) {
       const int row = lane + L * i;
-      wa[i] = make_float2(C::VEC && row == ca && row < N ? 1.f : 0.f, 0.f);
-      wb[i] = make_float2(C::VEC && row == cb && row < N ? 1.f : 0.f, 0.f);
+      w0[i] = make_float2(C::VEC && row == id0 && row < N ? 1.f : 0.f, 0.f);
+      w1[i] = make_float2(C::VEC && row == id1 && row < N ? 1.f : 0.f, 0.f);
     }
 
     // ---------------------------------------------------------------- sweeps
     const float tol2 = La.tol2;
-    int sweeps = 0, nrot = 0;
+    int sweeps = 0, nrot = 0, rr = 0, rotated = 0;
     bool converged = false;
-    int t = 0;   // global round counter
-    for (int sw = 0; sw < P.max_sweeps; ++sw) {
-      int rotated = 0;
-      for (int rr = 0; rr < Cn; ++rr, ++t) {
-        float al = 0.f, be = 0.f, gr = 0.f, gi = 0.f;
-#pragma unroll
-        for (int i = 0; i < MR; ++i) {
-          al = fmaf(xa[i].x, xa[i].x, fmaf(xa[i].y, xa[i].y, al));
-          be = fmaf(xb[i].x, xb[i].x, fmaf(xb[i].y, xb[i].y, be));
-          gr = fmaf(xa[i].x, xb[i].x, fmaf(xa[i].y, xb[i].y, gr));   // Re(conj(xa) xb)
-          gi = fmaf(xa[i].x, xb[i].y, fmaf(-xa[i].y, xb[i].x, gi));  // Im(conj(xa) xb)
-        }
-        al = team_sum<L>(al);
-        be = team_sum<L>(be);
-        gr = team_sum<L>(gr);
-        gi = team_sum<L>(gi);
-        const float g2 = fmaf(gr, gr, gi * gi);
-        if (g2 > tol2 * (al * be)) {
-          // J = [[c, s e], [-s conj(e), c]], e = gamma/|gamma|, t = tan solves
-          // t^2 + 2 zeta t - 1 = 0 with zeta = (beta - alpha)/(2|gamma|), |t| <= 1.
-          // The angle may be approximate; unitarity rests on e, s and c-1, which are
-          // formed with correctly rounded reciprocals / reciprocal square roots.
-          // Applied as x + (c-1) x + ...: c - 1 = -t^2/(r(1+r)), r = sqrt(1+t^2) (for
-          // small t fp32 rounds c to 1, and c = 1, s = t would grow norms by t^2/2).
-          const float ig = __frsqrt_rn(g2);                  // 1/|gamma|
-          const float zeta = (be - al) * (0.5f * ig);
-          const float az = fabsf(zeta);
-          const float q = fmaf(az, az, 1.f);
-          const float hz = az < 1e18f ? q * rsqrtf(q) : az;  // ~ sqrt(1 + zeta^2)
-          const float tt = copysignf(__fdividef(1.f, az + hz), zeta);
-          const float r2 = fmaf(tt, tt, 1.f);
-          const float ir = __frsqrt_rn(r2);
-          const float s = tt * ir;
-          const float r = r2 * ir;
-          const float cm1 = -(tt * s) * __frcp_rn(1.f + r);
-          const float sr = s * (gr * ig), si = s * (gi * ig);
-#pragma unroll
-          for (int i = 0; i < MR; ++i) rotate(xa[i], xb[i], cm1, sr, si);
-          if constexpr (C::VEC) {
-#pragma unroll
-            for (int i = 0; i < WR; ++i) rotate(wa[i], wb[i], cm1, sr, si);
-          }
-          rotated = 1;
-          ++nrot;
-        }
-        // -------------------------------------------------------------- exchange
-        const int pos = (t & 1) ? pi_pos<NP>(team) : team;
-        int dp;
-        bool send_a, recv_a, shift;
-        if (pos == NP - 1) { send_a = true; dp = pos - 1; recv_a = false; shift = true; }
-        else if (pos == 0) { send_a = true; dp = 1; recv_a = true; shift = false; }
-        else if (pos & 1) { send_a = true; dp = pos - 1; recv_a = true; shift = false; }
-        else { send_a = false; dp = pos + 1; recv_a = false; shift = false; }
-        const int dest = ((t + 1) & 1) ? pi_pos<NP>(dp) : dp;
-        const int par = t & 1;
-        float2* dst = mbox + (size_t)(par * TPC + dest % TPC) * RS;
-        if constexpr (CS > 1) dst = cg::this_cluster().map_shared_rank(dst, dest / TPC);
-#pragma unroll
-        for (int i = 0; i < MR; ++i) dst[lane + L * i] = send_a ? xa[i] : xb[i];
-        if constexpr (C::VEC) {
-#pragma unroll
-          for (int i = 0; i < WR; ++i) dst[C::XR + lane + L * i] = send_a ? wa[i] : wb[i];
-        }
-        if (shift) {
-#pragma unroll
-          for (int i = 0; i < MR; ++i) xa[i] = xb[i];
-#pragma unroll
-          for (int i = 0; i < WN; ++i) wa[i] = wb[i];
-        }
-        sym_sync<C>();
-        const float2* src = mbox + (size_t)(par * TPC + lteam) * RS;
-#pragma unroll
-        for (int i = 0; i < MR; ++i) {
-          const float2 v = src[lane + L * i];
-          xa[i] = recv_a ? v : xa[i];
-          xb[i] = recv_a ? xb[i] : v;
-        }
-        if constexpr (C::VEC) {
-#pragma unroll
-          for (int i = 0; i < WR; ++i) {
-            const float2 v = src[C::XR + lane + L * i];
-            wa[i] = recv_a ? v : wa[i];
-            wb[i] = recv_a ? wb[i] : v;
-          }
-        }
-      }
+    // a sweep ends every Cn rounds; returns true when the unit stops
+    auto sweep_end = [&]() -> bool {
+      rr = 0;
       ++sweeps;
-      // a symbol has converged when none of its pairs rotated in this sweep
       bool any_sym, any_unit;
       if constexpr (CS > 1) {
         cg::cluster_group cl = cg::this_cluster();
-        const int q = sw & 1;
+        const int q = sweeps & 1;
         const int mine = __syncthreads_or(rotated);
         if (threadIdx.x == 0 && mine) atomicOr(cl.map_shared_rank(&ubox[1 + q], 0), 1);
         cl.sync();
@@ -354,11 +383,28 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
         any_unit = __syncthreads_or(rotated) != 0;
         any_sym = any_unit;
       }
+      rotated = 0;
       if (!any_sym && !converged) {
         converged = true;
         if (st == 0 && crank == 0 && active) atomicAdd(&ctr->sweeps, (unsigned long long)sweeps);
       }
-      if (!any_unit) break;
+      return !any_unit || sweeps >= P.max_sweeps;
+    };
+    for (;;) {
+      // even round: teams move array 0, team 0 moves array 1
+      if (pair_step<C>(x0, x1, w0, w1, tol2)) { rotated = 1; ++nrot; }
+      if (team == 0) put_column<C>(x1, w1, id1, dst_e, dst_id_e, lane);
+      else put_column<C>(x0, w0, id0, dst_e, dst_id_e, lane);
+      sym_sync<C>();
+      if (team == 0) get_column<C>(x1, w1, id1, src_e, src_id_e, lane);
+      else get_column<C>(x0, w0, id0, src_e, src_id_e, lane);
+      if (++rr == Cn && sweep_end()) break;
+      // odd round: every team moves array 1
+      if (pair_step<C>(x0, x1, w0, w1, tol2)) { rotated = 1; ++nrot; }
+      put_column<C>(x1, w1, id1, dst_o, dst_id_o, lane);
+      sym_sync<C>();
+      get_column<C>(x1, w1, id1, src_o, src_id_o, lane);
+      if (++rr == Cn && sweep_end()) break;
     }
     if (!converged && st == 0 && crank == 0 && active) {
       atomicAdd(&ctr->sweeps, (unsigned long long)sweeps);
@@ -367,12 +413,11 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
     if (lane == 0 && nrot && active) atomicAdd(&ctr->rotations, (unsigned long long)nrot);
 
     // ---------------------------------------------------------------- singular values, order
-    {
-      const int pos = (t & 1) ? pi_pos<NP>(team) : team;
-      const int tm = t % Cn;
-      ca = (tm + pos) % Cn;
-      cb = pos == 0 ? FIX : (tm - pos + Cn) % Cn;
-    }
+    const int ca = id0, cb = id1;
+    float2 (&xa)[MR] = x0;
+    float2 (&xb)[MR] = x1;
+    float2 (&wa)[WN] = w0;
+    float2 (&wb)[WN] = w1;
     float al = 0.f, be = 0.f;
 #pragma unroll
     for (int i = 0; i < MR; ++i) {
