@@ -35,11 +35,14 @@ sys.path.insert(0, ROOT)
 import lfa_workloads as W  # noqa: E402
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+DEFAULT_TUNE = os.path.join(ROOT, "paper_2506_05617_gb300", "tune_gb300.txt")
 SMS = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 LAM = 1e-2
 METRIC = "singular values/sec and layers/sec (batched+backward vs plain) at σ err ≤1e-5·σ_max"
+# workloads whose configuration asks for singular values only
+VALUES_ONLY = {"resnet18_body", "paper_c16_k3_n256"}
 
 
 def nominal_svd_flops(M: int, N: int, vectors: bool) -> float:
@@ -128,10 +131,13 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- oracle leg
-def oracle_sample_step(w, lay: W.Layer, freqs, g_seed: int):
+def oracle_sample_step(w, lay: W.Layer, freqs, g_seed: int, vectors: bool = True):
     """One bounded sample of the step on the FP64 oracle (CPU): symbols + SVD (U, V) of the
-    sampled frequencies, regulariser gradient, their dL/dw contribution, lifted vectors."""
+    sampled frequencies, regulariser gradient, their dL/dw contribution, lifted vectors
+    (values only: symbols + SVD values)."""
     import oracle as O
+    if not vectors:
+        return O.lfa_svd(w, lay.n, lay.m, compute_uv=False, freqs=freqs), None, None, None
     s, U, V = O.lfa_svd(w, lay.n, lay.m, compute_uv=True, freqs=freqs)
     g = O.regulariser_grad_sigma(s, LAM)
     dw = O.lfa_backward(w, lay.n, lay.m, g, U, V, freqs=freqs)
@@ -141,7 +147,7 @@ def oracle_sample_step(w, lay: W.Layer, freqs, g_seed: int):
     return s, dw, uh, vh
 
 
-def run_oracle(lay: W.Layer, seconds: float, nfreq: int, steps: int | None = None):
+def run_oracle(lay: W.Layer, seconds: float, nfreq: int, steps: int | None = None, vectors: bool = True):
     """Times the oracle on sampled frequencies of the workload; returns the cpu_baseline dict."""
     w = W.weights(lay)
     rng = np.random.default_rng(123)
@@ -153,7 +159,7 @@ def run_oracle(lay: W.Layer, seconds: float, nfreq: int, steps: int | None = Non
     while True:
         freqs = np.sort(rng.choice(lay.F, nf, replace=False))
         ts = time.perf_counter()
-        oracle_sample_step(w, lay, freqs, 0)
+        oracle_sample_step(w, lay, freqs, 0, vectors)
         times.append(time.perf_counter() - ts)
         done += 1
         sig += nf * lay.r
@@ -167,7 +173,8 @@ def run_oracle(lay: W.Layer, seconds: float, nfreq: int, steps: int | None = Non
     return {"value": sig / wall, "unit": "singular values/s", "cores": round(cpu / wall, 2),
             "cores_available": os.cpu_count(), "kind": "oracle",
             "sample": f"{done} x {nf} of {lay.F} frequencies of {lay.c_out}->{lay.c_in} k={lay.kh} n={lay.n}: "
-                      f"FP64 symbols + LAPACK SVD with U,V + regulariser grad + dL/dw + one lifted pair",
+                      + ("FP64 symbols + LAPACK SVD with U,V + regulariser grad + dL/dw + one lifted pair"
+                         if vectors else "FP64 symbols + LAPACK SVD values"),
             "seconds": round(wall, 3), "step_s": times}
 
 
@@ -187,33 +194,41 @@ def run_lfa(args, rank: int, world: int, local_rank: int):
         dist.init_process_group("nccl", device_id=dev)
 
     layers = W.layers(args.workload)
+    vectors = not (args.values_only or args.workload in VALUES_ONLY)
     # each rank gets its own seeded weights (independent units)
     ws = [torch.from_numpy(W.weights(l, seed=l.seed + 1000 * rank)).to(dev) for l in layers]
     specs = [(l.c_out, l.c_in, l.kh, l.kw, l.n, l.m, l.pad_h, l.pad_w) for l in layers]
-    plan = LfaPlan(specs, vectors=True)
+    plan = LfaPlan(specs, vectors=vectors, tune_cache=args.tune_cache)
     sig, U, V = plan.alloc(dev)
-    dsig = [torch.empty_like(s) for s in sig]
-    loss = [torch.empty((), device=dev) for _ in sig]
-    dw = [torch.empty_like(w) for w in ws]
-    l0 = layers[0]
-    f_exp = 1 if l0.F > 1 else 0
-    cnt = l0.r
-    uh = torch.empty((cnt, l0.c_out, l0.n, l0.m), dtype=torch.complex64, device=dev)
-    vh = torch.empty((cnt, l0.c_in, l0.n, l0.m), dtype=torch.complex64, device=dev)
     stream = torch.cuda.current_stream(dev)
     sptr = stream.cuda_stream
     w_ptrs = [w.data_ptr() for w in ws]
     s_ptrs = [s.data_ptr() for s in sig]
-    u_ptrs = [u.data_ptr() for u in U]
-    v_ptrs = [v.data_ptr() for v in V]
-    ds_ptrs = [d.data_ptr() for d in dsig]
-    lo_ptrs = [x.data_ptr() for x in loss]
-    dw_ptrs = [d.data_ptr() for d in dw]
+    outs = list(sig)
+    if vectors:
+        dsig = [torch.empty_like(s) for s in sig]
+        loss = [torch.empty((), device=dev) for _ in sig]
+        dw = [torch.empty_like(w) for w in ws]
+        l0 = layers[0]
+        f_exp = 1 if l0.F > 1 else 0
+        cnt = l0.r
+        uh = torch.empty((cnt, l0.c_out, l0.n, l0.m), dtype=torch.complex64, device=dev)
+        vh = torch.empty((cnt, l0.c_in, l0.n, l0.m), dtype=torch.complex64, device=dev)
+        u_ptrs = [u.data_ptr() for u in U]
+        v_ptrs = [v.data_ptr() for v in V]
+        ds_ptrs = [d.data_ptr() for d in dsig]
+        lo_ptrs = [x.data_ptr() for x in loss]
+        dw_ptrs = [d.data_ptr() for d in dw]
+        outs += list(U) + list(V) + dsig + dw + loss + [uh, vh]
+    else:
+        u_ptrs = v_ptrs = None
 
     def forward():
         C.lfa_svd(plan.handle, w_ptrs, s_ptrs, u_ptrs, v_ptrs, sptr)
 
     def rest():
+        if not vectors:
+            return
         C.lfa_regulariser_grad(plan.handle, s_ptrs, LAM, ds_ptrs, lo_ptrs, sptr)
         C.lfa_svd_backward(plan.handle, ds_ptrs, u_ptrs, v_ptrs, dw_ptrs, sptr)
         C.lfa_expand(plan.handle, 0, u_ptrs[0], v_ptrs[0], f_exp * l0.r, cnt, uh.data_ptr(), vh.data_ptr(), sptr)
@@ -282,7 +297,6 @@ def run_lfa(args, rank: int, world: int, local_rank: int):
     e2e = None
     if not args.no_e2e:
         hw = [w.cpu().pin_memory() for w in ws]
-        outs = sig + U + V + dsig + dw + loss + [uh, vh]
         hout = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
         h2d = sum(x.numel() * x.element_size() for x in hw)
         d2h = sum(x.numel() * x.element_size() for x in hout)
@@ -312,7 +326,7 @@ def run_lfa(args, rank: int, world: int, local_rank: int):
     sig_per_step = sum(l.n_sigma for l in layers)
     ms_per_step = total_ms / K
     value = world * sig_per_step * K / (total_ms / 1e3)
-    flops = sum(layer_flops(l, True) for l in layers)
+    flops = sum(layer_flops(l, vectors) for l in layers)
     peak = fp32_peak_tflops()
     achieved = flops / (fwd_mean / 1e3) / 1e12
     traffic = measured_traffic(args.workload)
@@ -339,8 +353,9 @@ def run_lfa(args, rank: int, world: int, local_rank: int):
         "config": {
             "workload": args.workload,
             "layers": [f"{l.c_out}x{l.c_in}x{l.kh}x{l.kw}@{l.n}x{l.m}" for l in layers],
-            "outputs": "values+vectors (U, V per half-grid frequency)",
-            "step": "fwd(assembly+Jacobi, graph) + regulariser dL/dsigma + bwd dL/dw + lift r vector pairs",
+            "outputs": "values+vectors (U, V per half-grid frequency)" if vectors else "values only",
+            "step": ("fwd(assembly+Jacobi, graph) + regulariser dL/dsigma + bwd dL/dw + lift r vector pairs"
+                     if vectors else "fwd(assembly+Jacobi, all layers in one graph-replayed launch per variant)"),
             "l2": f"flushed between timed steps ({args.flush_mb} MB write, outside the timed events)",
             "parallelism": f"dp{world} (independent layers per rank)",
         },
@@ -350,7 +365,8 @@ def run_lfa(args, rank: int, world: int, local_rank: int):
         "plain_fwd_values_ms": plain_ms,
         "plain_layers_per_s": len(layers) / (plain_ms / 1e3),
         "roofline": {
-            "kernel": "jacobi_kernel (fused symbol assembly + one-sided Jacobi, values+vectors)",
+            "kernel": "jacobi_kernel (fused symbol assembly + one-sided Jacobi, %s)" % (
+                "values+vectors" if vectors else "values"),
             "bound": "alu",
             "achieved": achieved,
             "peak": peak,
@@ -370,7 +386,7 @@ def run_lfa(args, rank: int, world: int, local_rank: int):
     if e2e is not None:
         out["e2e"] = e2e
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb = run_oracle(layers[0], args.cpu_seconds, args.cpu_freqs)
+        cb = run_oracle(layers[0], args.cpu_seconds, args.cpu_freqs, vectors=vectors)
         # the sampled oracle frequencies also give an accuracy check of this run's sigma
         import oracle as O
         rng = np.random.default_rng(5)
@@ -391,21 +407,24 @@ def run_lfa(args, rank: int, world: int, local_rank: int):
 def run_reference(args):
     """The oracle arm: the FP64 CPU oracle on bounded samples of the same workload."""
     layers = W.layers(args.workload)
+    vectors = not (args.values_only or args.workload in VALUES_ONLY)
     lay = layers[0]
     w = W.weights(lay)
     rng = np.random.default_rng(7)
     nf = min(args.cpu_freqs, lay.F)
     for _ in range(args.warmup):
-        oracle_sample_step(w, lay, np.sort(rng.choice(lay.F, nf, replace=False)), 0)
+        oracle_sample_step(w, lay, np.sort(rng.choice(lay.F, nf, replace=False)), 0, vectors)
     r0 = resource.getrusage(resource.RUSAGE_SELF)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle_sample_step(w, lay, np.sort(rng.choice(lay.F, nf, replace=False)), 0)
+        oracle_sample_step(w, lay, np.sort(rng.choice(lay.F, nf, replace=False)), 0, vectors)
     wall = time.perf_counter() - t0
     r1 = resource.getrusage(resource.RUSAGE_SELF)
     cpu = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
     value = args.steps * nf * lay.r / wall
-    sample = f"{nf} of {lay.F} frequencies per step (FP64 oracle: symbols, LAPACK SVD with U,V, regulariser, dL/dw, lift)"
+    sample = f"{nf} of {lay.F} frequencies per step of layer 0 " + (
+        "(FP64 oracle: symbols, LAPACK SVD with U,V, regulariser, dL/dw, lift)" if vectors
+        else "(FP64 oracle: symbols, LAPACK SVD values)")
     return {
         "impl": "reference",
         "metric": METRIC,
@@ -441,6 +460,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--cpu-freqs", type=int, default=64)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--values-only", action="store_true", help="values only (no vectors, backward, lifting)")
+    ap.add_argument("--tune-cache", default=DEFAULT_TUNE if os.path.exists(DEFAULT_TUNE) else None,
+                    help="autotuner cache file read by lfa_plan")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))

@@ -1,0 +1,128 @@
+"""Autotuner for the Jacobi kernel variants.
+
+For every distinct Jacobi problem (M = max(c_out, c_in), N = min(c_out, c_in), with or
+without vectors) of the given layers, each register-resident variant that can hold it is
+timed through the C ABI (`lfa_svd` on a one-layer plan forced to that variant, CUDA
+events around graph replays), and the fastest is written to a text cache, one line per
+problem: ``M N vectors variant  # name ms``. `lfa_plan` reads that file when it is passed
+as `lfa_options.tune_cache`; problems without a line use the built-in choice.
+
+    python -m paper_2506_05617_gb300.autotune --workload conv64_k3_n32 --out tune.txt
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+from typing import Dict, Iterable, List, Tuple
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def candidates(M: int, N: int, vectors: bool) -> List[int]:
+    """Variant ids that can hold an M x N problem (per the library's own capacity rules)."""
+    import re
+    from . import lfa as C
+    out = []
+    for v in range(C.lfa_debug_variant_count()):
+        npairs, lanes, mr, wr, cs = (int(x) for x in re.findall(r"\d+", C.lfa_variant_name(v)))
+        if M > mr * lanes or N > 2 * npairs or (vectors and N > wr * lanes):
+            continue
+        out.append(v)
+    return out
+
+
+def time_variant(layer: Tuple[int, ...], vectors: bool, variant: int, reps: int = 5) -> float:
+    """Median milliseconds of lfa_svd for one layer forced to `variant` (inf if it cannot run)."""
+    import numpy as np
+    import torch
+    from . import lfa as C
+    from .torch_api import LfaPlan
+    try:
+        plan = LfaPlan([layer], vectors=vectors, variant=variant)
+    except C.LfaError:
+        return float("inf")
+    if plan.meta[0]["variant"] != variant:
+        plan.close()
+        return float("inf")
+    c_out, c_in, kh, kw = layer[:4]
+    w = torch.randn(c_out, c_in, kh, kw, device="cuda") / (c_in * kh * kw) ** 0.5
+    out = plan.alloc()
+    for _ in range(2):
+        plan.svd([w], out=out)
+    ts = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        plan.svd([w], out=out)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    st, info = plan.info()
+    plan.close()
+    if st != C.LFA_OK:
+        return float("inf")
+    return float(np.median(ts))
+
+
+def tune(layers: Iterable[Tuple[int, ...]], vectors: bool, verbose: bool = True) -> Dict[Tuple[int, int, int], Tuple[int, float]]:
+    from . import lfa as C
+    best: Dict[Tuple[int, int, int], Tuple[int, float]] = {}
+    for layer in layers:
+        c_out, c_in = layer[:2]
+        key = (max(c_out, c_in), min(c_out, c_in), int(vectors))
+        if key in best:
+            continue
+        res = []
+        for v in candidates(key[0], key[1], vectors):
+            ms = time_variant(tuple(layer), vectors, v)
+            res.append((ms, v))
+            if verbose:
+                print(f"  M={key[0]} N={key[1]} vec={int(vectors)} {C.lfa_variant_name(v):32s} {ms:9.3f} ms",
+                      file=sys.stderr)
+        res.sort()
+        if res and res[0][0] < float("inf"):
+            best[key] = (res[0][1], res[0][0])
+    return best
+
+
+def write_cache(path: str, best: Dict[Tuple[int, int, int], Tuple[int, float]]):
+    from . import lfa as C
+    old = {}
+    if os.path.exists(path):
+        for line in open(path):
+            parts = line.split("#")[0].split()
+            if len(parts) == 4:
+                old[tuple(int(x) for x in parts[:3])] = line.rstrip("\n")
+    for (M, N, vec), (v, ms) in best.items():
+        old[(M, N, vec)] = f"{M} {N} {vec} {v}  # {C.lfa_variant_name(v)} {ms:.3f} ms"
+    with open(path, "w") as fh:
+        fh.write("# LFA Jacobi variant cache: M N vectors variant  (written by paper_2506_05617_gb300.autotune)\n")
+        for k in sorted(old):
+            fh.write(old[k] + "\n")
+
+
+def main():
+    sys.path.insert(0, ROOT)
+    import lfa_workloads as W
+    from . import build as B
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", action="append", default=None, choices=sorted(W.WORKLOADS))
+    ap.add_argument("--out", required=True)
+    ap.add_argument("--values", action="store_true", help="tune the values-only kernels too")
+    a = ap.parse_args()
+    B.build()
+    names = a.workload or ["conv64_k3_n32"]
+    layers = []
+    for nm in names:
+        layers += [(l.c_out, l.c_in, l.kh, l.kw, l.n, l.m) for l in W.layers(nm)]
+    best = tune(layers, vectors=True)
+    if a.values:
+        best.update(tune(layers, vectors=False))
+    write_cache(a.out, best)
+    print(open(a.out).read())
+
+
+if __name__ == "__main__":
+    main()

@@ -52,7 +52,10 @@ struct JCfg {
   static constexpr int UPB = BLOCK / UT;          // units per CTA
   static constexpr int NC = 2 * NP;               // column slots
   static constexpr int XR = MR * L;               // X row capacity
-  static constexpr int WRC = VEC ? WR * L : 0;    // W row capacity
+  static_assert(MR % 2 == 0, "X rows are held as pairs");
+  static constexpr int MH = MR / 2;               // X row pairs per lane
+  static constexpr int WH = (WR + 1) / 2;         // W row pairs per lane (last one half padding if WR odd)
+  static constexpr int WRC = VEC ? 2 * WH * L : 0;  // W row capacity in the mailbox
   // slot stride = L mod 16 (float2): neighbouring teams of a warp hit different banks
   static constexpr int RS = XR + WRC + (((L - (XR + WRC)) % 16) + 16) % 16;
   static constexpr int MBOX = 2 * TPC * RS;       // [parity][team][RS] float2
@@ -140,30 +143,49 @@ __device__ __forceinline__ float2 x_entry(const LayerArgs& La, int h, int row, i
   return make_float2(re, La.wide ? -im : im);
 }
 
-// x_a' = x_a + cm1 x_a - conj(e s) x_b ; x_b' = x_b + cm1 x_b + (e s) x_a  (e s = sr + i si),
-// three fused multiply-adds per real component.
-__device__ __forceinline__ void rotate(float2& A, float2& B, float cm1, float sr, float si) {
-  const float2 a = A, b = B;
-  A.x = fmaf(-sr, b.x, fmaf(-si, b.y, fmaf(cm1, a.x, a.x)));
-  A.y = fmaf(-sr, b.y, fmaf(si, b.x, fmaf(cm1, a.y, a.y)));
-  B.x = fmaf(sr, a.x, fmaf(-si, a.y, fmaf(cm1, b.x, b.x)));
-  B.y = fmaf(sr, a.y, fmaf(si, a.x, fmaf(cm1, b.y, b.y)));
+// A column of X (and of W) held by one lane as real/imaginary planes over row pairs: pair k
+// holds rows lane + L k (.x) and lane + L (k + MH) (.y) of X; for W the pair partner row is
+// lane + L (k + WH). Every complex operation on a column is then an elementwise operation on
+// pairs, issued as paired fp32 instructions (two fused multiply-adds per instruction).
+template <class C>
+struct Planes {
+  float2 xr[C::MH], xi[C::MH];
+  float2 wr[C::VEC ? C::WH : 1], wi[C::VEC ? C::WH : 1];
+};
+
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+
+// 1/sqrt(x) for normal x > 0: the hardware estimate refined by one Newton-Raphson step for
+// the reciprocal square root, y <- y (3 - x y^2) / 2, which brings it to about one ulp. The
+// rotation's unitarity rests on e = gamma/|gamma| and s having unit modulus to this accuracy.
+__device__ __forceinline__ float rsqrt_nr(float x) {
+  const float y = rsqrtf(x);
+  const float h = 0.5f * x * y;
+  return fmaf(y, fmaf(-h, y, 0.5f), y);   // y + y (1/2 - x y^2 / 2)
 }
 
-// One Jacobi round on the team's pair (x0, x1) (symmetric in the two columns): dots, butterfly,
+// One Jacobi round on the team's pair (a, b) (symmetric in the two columns): dots, butterfly,
 // rotation of X and W. Returns whether a rotation was applied.
 template <class C>
-__device__ __forceinline__ bool pair_step(float2 (&x0)[C::MR], float2 (&x1)[C::MR], float2 (&w0)[C::VEC ? C::WR : 1],
-                                          float2 (&w1)[C::VEC ? C::WR : 1], float tol2) {
-  constexpr int MR = C::MR, WR = C::WR, L = C::L;
-  float al = 0.f, be = 0.f, gr = 0.f, gi = 0.f;
+__device__ __forceinline__ bool pair_step(Planes<C>& a, Planes<C>& b, float tol2) {
+  constexpr int MH = C::MH, WH = C::WH, L = C::L;
+  // real and imaginary planes accumulate separately: eight independent chains
+  float2 alr = f2(0.f), ali = f2(0.f), ber = f2(0.f), bei = f2(0.f);
+  float2 grr = f2(0.f), gri = f2(0.f), gp2 = f2(0.f), gm2 = f2(0.f);
 #pragma unroll
-  for (int i = 0; i < MR; ++i) {
-    al = fmaf(x0[i].x, x0[i].x, fmaf(x0[i].y, x0[i].y, al));
-    be = fmaf(x1[i].x, x1[i].x, fmaf(x1[i].y, x1[i].y, be));
-    gr = fmaf(x0[i].x, x1[i].x, fmaf(x0[i].y, x1[i].y, gr));   // Re(conj(x0) x1)
-    gi = fmaf(x0[i].x, x1[i].y, fmaf(-x0[i].y, x1[i].x, gi));  // Im(conj(x0) x1)
+  for (int k = 0; k < MH; ++k) {
+    alr = __ffma2_rn(a.xr[k], a.xr[k], alr);
+    ali = __ffma2_rn(a.xi[k], a.xi[k], ali);
+    ber = __ffma2_rn(b.xr[k], b.xr[k], ber);
+    bei = __ffma2_rn(b.xi[k], b.xi[k], bei);
+    grr = __ffma2_rn(a.xr[k], b.xr[k], grr);   // Re(conj(a) b) = ar br + ai bi
+    gri = __ffma2_rn(a.xi[k], b.xi[k], gri);
+    gp2 = __ffma2_rn(a.xr[k], b.xi[k], gp2);   // Im(conj(a) b) = ar bi - ai br
+    gm2 = __ffma2_rn(a.xi[k], b.xr[k], gm2);
   }
+  const float2 al2 = __fadd2_rn(alr, ali), be2 = __fadd2_rn(ber, bei), gr2 = __fadd2_rn(grr, gri);
+  float al = al2.x + al2.y, be = be2.x + be2.y, gr = gr2.x + gr2.y;
+  float gi = (gp2.x + gp2.y) - (gm2.x + gm2.y);
   al = team_sum<L>(al);
   be = team_sum<L>(be);
   gr = team_sum<L>(gr);
@@ -175,55 +197,93 @@ __device__ __forceinline__ bool pair_step(float2 (&x0)[C::MR], float2 (&x1)[C::M
   // rests on e, s and c-1, which are formed with correctly rounded reciprocals / reciprocal
   // square roots. Applied as x + (c-1) x + ...: c - 1 = -t^2/(r(1+r)), r = sqrt(1+t^2) (for
   // small t fp32 rounds c to 1, and c = 1, s = t would grow norms by t^2/2).
-  const float ig = __frsqrt_rn(g2);                  // 1/|gamma|
+  const float ig = rsqrt_nr(g2);                     // 1/|gamma|
   const float zeta = (be - al) * (0.5f * ig);
   const float az = fabsf(zeta);
   const float q = fmaf(az, az, 1.f);
   const float hz = az < 1e18f ? q * rsqrtf(q) : az;  // ~ sqrt(1 + zeta^2)
   const float tt = copysignf(__fdividef(1.f, az + hz), zeta);
   const float r2 = fmaf(tt, tt, 1.f);
-  const float ir = __frsqrt_rn(r2);
+  const float ir = rsqrt_nr(r2);
   const float s = tt * ir;
   const float r = r2 * ir;
-  const float cm1 = -(tt * s) * __frcp_rn(1.f + r);
+  const float cm1 = __fdividef(-(tt * s), 1.f + r);  // tiny for small t: its relative error is harmless
   const float sr = s * (gr * ig), si = s * (gi * ig);
+  // a' = a + (c-1) a - conj(e s) b ; b' = b + (c-1) b + (e s) a,  e s = sr + i si:
+  //   a'r = ar + cm1 ar - sr br - si bi     a'i = ai + cm1 ai - sr bi + si br
+  //   b'r = br + cm1 br + sr ar - si ai     b'i = bi + cm1 bi + sr ai + si ar
+  const float2 c2 = f2(cm1), s2 = f2(sr), ns2 = f2(-sr), t2 = f2(si), nt2 = f2(-si);
 #pragma unroll
-  for (int i = 0; i < MR; ++i) rotate(x0[i], x1[i], cm1, sr, si);
+  for (int k = 0; k < MH; ++k) {
+    const float2 Ar = a.xr[k], Ai = a.xi[k], Br = b.xr[k], Bi = b.xi[k];
+    a.xr[k] = __ffma2_rn(nt2, Bi, __ffma2_rn(ns2, Br, __ffma2_rn(c2, Ar, Ar)));
+    a.xi[k] = __ffma2_rn(t2, Br, __ffma2_rn(ns2, Bi, __ffma2_rn(c2, Ai, Ai)));
+    b.xr[k] = __ffma2_rn(nt2, Ai, __ffma2_rn(s2, Ar, __ffma2_rn(c2, Br, Br)));
+    b.xi[k] = __ffma2_rn(t2, Ar, __ffma2_rn(s2, Ai, __ffma2_rn(c2, Bi, Bi)));
+  }
   if constexpr (C::VEC) {
 #pragma unroll
-    for (int i = 0; i < WR; ++i) rotate(w0[i], w1[i], cm1, sr, si);
+    for (int k = 0; k < WH; ++k) {
+      const float2 Ar = a.wr[k], Ai = a.wi[k], Br = b.wr[k], Bi = b.wi[k];
+      a.wr[k] = __ffma2_rn(nt2, Bi, __ffma2_rn(ns2, Br, __ffma2_rn(c2, Ar, Ar)));
+      a.wi[k] = __ffma2_rn(t2, Br, __ffma2_rn(ns2, Bi, __ffma2_rn(c2, Ai, Ai)));
+      b.wr[k] = __ffma2_rn(nt2, Ai, __ffma2_rn(s2, Ar, __ffma2_rn(c2, Br, Br)));
+      b.wi[k] = __ffma2_rn(t2, Ar, __ffma2_rn(s2, Ai, __ffma2_rn(c2, Bi, Bi)));
+    }
   }
   return true;
 }
 
-// Write array `xa` (W part `wa`, column id `ida`) to a mailbox slot. No barrier inside: the
+// Write column `a` (id `ida`) to a mailbox slot, planes lane-interleaved. No barrier inside: the
 // caller may branch around this (team 0 moves a different array); the barrier that follows
 // must be reached by every thread in uniform control flow (aligned CTA / cluster barriers).
 template <class C>
-__device__ __forceinline__ void put_column(const float2 (&xa)[C::MR], const float2 (&wa)[C::VEC ? C::WR : 1],
-                                           int ida, float2* dst, int* dst_id, int lane) {
-  constexpr int MR = C::MR, WR = C::WR, L = C::L;
+__device__ __forceinline__ void put_column(const Planes<C>& a, int ida, float2* dst, int* dst_id, int lane) {
+  constexpr int MH = C::MH, WH = C::WH, L = C::L;
 #pragma unroll
-  for (int i = 0; i < MR; ++i) dst[lane + L * i] = xa[i];
+  for (int k = 0; k < MH; ++k) {
+    dst[(2 * k) * L + lane] = a.xr[k];
+    dst[(2 * k + 1) * L + lane] = a.xi[k];
+  }
   if constexpr (C::VEC) {
 #pragma unroll
-    for (int i = 0; i < WR; ++i) dst[C::XR + lane + L * i] = wa[i];
+    for (int k = 0; k < WH; ++k) {
+      dst[C::XR + (2 * k) * L + lane] = a.wr[k];
+      dst[C::XR + (2 * k + 1) * L + lane] = a.wi[k];
+    }
   }
   if (lane == 0) *dst_id = ida;
 }
 
-// Read this team's mailbox slot into array `xa` (after the barrier).
+// Read this team's mailbox slot into column `a` (after the barrier).
 template <class C>
-__device__ __forceinline__ void get_column(float2 (&xa)[C::MR], float2 (&wa)[C::VEC ? C::WR : 1], int& ida,
-                                           const float2* src, const int* src_id, int lane) {
-  constexpr int MR = C::MR, WR = C::WR, L = C::L;
+__device__ __forceinline__ void get_column(Planes<C>& a, int& ida, const float2* src, const int* src_id, int lane) {
+  constexpr int MH = C::MH, WH = C::WH, L = C::L;
 #pragma unroll
-  for (int i = 0; i < MR; ++i) xa[i] = src[lane + L * i];
+  for (int k = 0; k < MH; ++k) {
+    a.xr[k] = src[(2 * k) * L + lane];
+    a.xi[k] = src[(2 * k + 1) * L + lane];
+  }
   if constexpr (C::VEC) {
 #pragma unroll
-    for (int i = 0; i < WR; ++i) wa[i] = src[C::XR + lane + L * i];
+    for (int k = 0; k < WH; ++k) {
+      a.wr[k] = src[C::XR + (2 * k) * L + lane];
+      a.wi[k] = src[C::XR + (2 * k + 1) * L + lane];
+    }
   }
   ida = *src_id;
+}
+
+// Row slot s (row lane + L s) of the X part / W part as a complex value.
+template <class C>
+__device__ __forceinline__ float2 x_at(const Planes<C>& a, int s) {
+  const int k = s < C::MH ? s : s - C::MH;
+  return s < C::MH ? make_float2(a.xr[k].x, a.xi[k].x) : make_float2(a.xr[k].y, a.xi[k].y);
+}
+template <class C>
+__device__ __forceinline__ float2 w_at(const Planes<C>& a, int s) {
+  const int k = s < C::WH ? s : s - C::WH;
+  return s < C::WH ? make_float2(a.wr[k].x, a.wi[k].x) : make_float2(a.wr[k].y, a.wi[k].y);
 }
 
 template <class C, bool FUSED>
@@ -343,18 +403,30 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
     if (team == 0) { id0 = FIX; id1 = 0; }
     else if ((team & 1) || team == NP - 1) { id0 = team; id1 = Cn - team; }
     else { id0 = Cn - team; id1 = team; }
-    float2 x0[MR], x1[MR], w0[WN], w1[WN];
+    Planes<C> c0, c1;
 #pragma unroll
-    for (int i = 0; i < MR; ++i) {
-      const int row = lane + L * i;
-      x0[i] = active ? x_entry<FUSED>(La, h, row, id0, phs, kk) : make_float2(0.f, 0.f);
-      x1[i] = active ? x_entry<FUSED>(La, h, row, id1, phs, kk) : make_float2(0.f, 0.f);
+    for (int k = 0; k < C::MH; ++k) {
+      const int r0 = lane + L * k, r1 = lane + L * (k + C::MH);
+      const float2 a0 = active ? x_entry<FUSED>(La, h, r0, id0, phs, kk) : make_float2(0.f, 0.f);
+      const float2 a1 = active ? x_entry<FUSED>(La, h, r1, id0, phs, kk) : make_float2(0.f, 0.f);
+      const float2 b0 = active ? x_entry<FUSED>(La, h, r0, id1, phs, kk) : make_float2(0.f, 0.f);
+      const float2 b1 = active ? x_entry<FUSED>(La, h, r1, id1, phs, kk) : make_float2(0.f, 0.f);
+      c0.xr[k] = make_float2(a0.x, a1.x);
+      c0.xi[k] = make_float2(a0.y, a1.y);
+      c1.xr[k] = make_float2(b0.x, b1.x);
+      c1.xi[k] = make_float2(b0.y, b1.y);
     }
+    if constexpr (C::VEC) {
+      // W starts as the identity; rows beyond WR per lane are padding and stay zero
 #pragma unroll
-    for (int i = 0; i < WN; ++i) {
-      const int row = lane + L * i;
-      w0[i] = make_float2(C::VEC && row == id0 && row < N ? 1.f : 0.f, 0.f);
-      w1[i] = make_float2(C::VEC && row == id1 && row < N ? 1.f : 0.f, 0.f);
+      for (int k = 0; k < C::WH; ++k) {
+        const int r0 = lane + L * k, r1 = lane + L * (k + C::WH);
+        const bool v1 = k + C::WH < WR;
+        c0.wr[k] = make_float2(r0 == id0 && r0 < N ? 1.f : 0.f, v1 && r1 == id0 && r1 < N ? 1.f : 0.f);
+        c1.wr[k] = make_float2(r0 == id1 && r0 < N ? 1.f : 0.f, v1 && r1 == id1 && r1 < N ? 1.f : 0.f);
+        c0.wi[k] = make_float2(0.f, 0.f);
+        c1.wi[k] = make_float2(0.f, 0.f);
+      }
     }
 
     // ---------------------------------------------------------------- sweeps
@@ -392,18 +464,18 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
     };
     for (;;) {
       // even round: teams move array 0, team 0 moves array 1
-      if (pair_step<C>(x0, x1, w0, w1, tol2)) { rotated = 1; ++nrot; }
-      if (team == 0) put_column<C>(x1, w1, id1, dst_e, dst_id_e, lane);
-      else put_column<C>(x0, w0, id0, dst_e, dst_id_e, lane);
+      if (pair_step<C>(c0, c1, tol2)) { rotated = 1; ++nrot; }
+      if (team == 0) put_column<C>(c1, id1, dst_e, dst_id_e, lane);
+      else put_column<C>(c0, id0, dst_e, dst_id_e, lane);
       sym_sync<C>();
-      if (team == 0) get_column<C>(x1, w1, id1, src_e, src_id_e, lane);
-      else get_column<C>(x0, w0, id0, src_e, src_id_e, lane);
+      if (team == 0) get_column<C>(c1, id1, src_e, src_id_e, lane);
+      else get_column<C>(c0, id0, src_e, src_id_e, lane);
       if (++rr == Cn && sweep_end()) break;
       // odd round: every team moves array 1
-      if (pair_step<C>(x0, x1, w0, w1, tol2)) { rotated = 1; ++nrot; }
-      put_column<C>(x1, w1, id1, dst_o, dst_id_o, lane);
+      if (pair_step<C>(c0, c1, tol2)) { rotated = 1; ++nrot; }
+      put_column<C>(c1, id1, dst_o, dst_id_o, lane);
       sym_sync<C>();
-      get_column<C>(x1, w1, id1, src_o, src_id_o, lane);
+      get_column<C>(c1, id1, src_o, src_id_o, lane);
       if (++rr == Cn && sweep_end()) break;
     }
     if (!converged && st == 0 && crank == 0 && active) {
@@ -414,10 +486,22 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
 
     // ---------------------------------------------------------------- singular values, order
     const int ca = id0, cb = id1;
-    float2 (&xa)[MR] = x0;
-    float2 (&xb)[MR] = x1;
-    float2 (&wa)[WN] = w0;
-    float2 (&wb)[WN] = w1;
+    float2 xa[MR], xb[MR], wa[WN], wb[WN];
+#pragma unroll
+    for (int i = 0; i < MR; ++i) {
+      xa[i] = x_at<C>(c0, i);
+      xb[i] = x_at<C>(c1, i);
+    }
+#pragma unroll
+    for (int i = 0; i < WN; ++i) {
+      if constexpr (C::VEC) {
+        wa[i] = w_at<C>(c0, i);
+        wb[i] = w_at<C>(c1, i);
+      } else {
+        wa[i] = make_float2(0.f, 0.f);
+        wb[i] = make_float2(0.f, 0.f);
+      }
+    }
     float al = 0.f, be = 0.f;
 #pragma unroll
     for (int i = 0; i < MR; ++i) {
