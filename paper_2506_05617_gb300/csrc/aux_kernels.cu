@@ -55,7 +55,8 @@ cudaError_t launch_symbols(const LayerArgs& La, float2* out, cudaStream_t s) {
 // ----------------------------------------------------------------------------- expansion
 // u_hat[q][c][x1][x2] = U_f[c][s] exp(2 pi i (j x1/n + l x2/m)) / sqrt(nm), q = f*r + s
 // (U^_k = F_k U_k, Sec. III). U_f = U[h] on the half grid, conj(U[h(fc)]) otherwise.
-// One CTA per vector q; threads stride over the c*n*m outputs (x2 fastest: coalesced).
+// Grid (element chunk, vector q); threads stride over the chunk's c*n*m outputs (x2 fastest:
+// coalesced writes).
 __device__ int half_index(const int32_t* half, int F_h, int f) {
   int lo = 0, hi = F_h - 1;
   while (lo < hi) {
@@ -67,7 +68,7 @@ __device__ int half_index(const int32_t* half, int F_h, int f) {
 
 __global__ void __launch_bounds__(256) expand_kernel(LayerArgs La, const float2* U, const float2* V,
                                                      int64_t first, float2* u_hat, float2* v_hat) {
-  const int64_t q = first + blockIdx.x;
+  const int64_t q = first + blockIdx.y;
   const int r = La.r;
   const int f = (int)(q / r), s = (int)(q - (int64_t)f * r);
   const int j = f / La.m, l = f - j * La.m;
@@ -82,9 +83,12 @@ __global__ void __launch_bounds__(256) expand_kernel(LayerArgs La, const float2*
     const int C = pass == 0 ? La.c_out : La.c_in;
     if (dst == nullptr || Src == nullptr) continue;
     const float2* col = Src + (size_t)h * C * r + s;
-    float2* d = dst + (size_t)blockIdx.x * C * nm;
-    for (int e = threadIdx.x; e < C * nm; e += blockDim.x) {
-      const int c = e / nm, x = e - c * nm;
+    float2* d = dst + (size_t)blockIdx.y * C * nm;
+    const int64_t total = (int64_t)C * nm;
+    const int64_t per = (total + gridDim.x - 1) / gridDim.x;
+    const int64_t e0 = (int64_t)blockIdx.x * per, e1 = e0 + per < total ? e0 + per : total;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const int c = (int)(e / nm), x = (int)(e - (int64_t)c * nm);
       const int x1 = x / La.m, x2 = x - x1 * La.m;
       float2 u = __ldg(col + (size_t)c * r);
       if (conj) u.y = -u.y;
@@ -99,8 +103,24 @@ __global__ void __launch_bounds__(256) expand_kernel(LayerArgs La, const float2*
 cudaError_t launch_expand(const LayerArgs& La, const float2* U, const float2* V, int64_t first,
                           int64_t count, float2* u_hat, float2* v_hat, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  if (count > 0x7fffffff) return cudaErrorInvalidValue;
-  expand_kernel<<<(unsigned)count, 256, 0, s>>>(La, U, V, first, u_hat, v_hat);
+  if (count > 65535) {
+    // more vectors than one grid dimension holds: split the range
+    for (int64_t q0 = 0; q0 < count; q0 += 65535) {
+      const int64_t cnt = count - q0 < 65535 ? count - q0 : 65535;
+      cudaError_t e = launch_expand(La, U, V, first + q0, cnt,
+                                    u_hat ? u_hat + (size_t)q0 * La.c_out * La.n * La.m : nullptr,
+                                    v_hat ? v_hat + (size_t)q0 * La.c_in * La.n * La.m : nullptr, s);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  const int64_t per_vec = (int64_t)(La.c_out > La.c_in ? La.c_out : La.c_in) * La.n * La.m;
+  int64_t chunks = (per_vec + 8191) / 8192;                 // ~32 elements per thread
+  const int64_t want = 4 * 152 * 4;                          // enough CTAs to fill the GPU
+  if (chunks * count > want) chunks = (want + count - 1) / count;
+  if (chunks < 1) chunks = 1;
+  dim3 grid((unsigned)chunks, (unsigned)count);
+  expand_kernel<<<grid, 256, 0, s>>>(La, U, V, first, u_hat, v_hat);
   return cudaGetLastError();
 }
 
@@ -163,36 +183,41 @@ __global__ void __launch_bounds__(256) backward_g_kernel(LayerArgs La, const flo
 }
 
 // Stage 2: partial[c][o][i][a][b] = sum_{h in chunk c} Re(G_h[o,i] exp(-2 pi i <k_h, y_ab>)),
-// the phase split into its row and column factors. Thread per (o, i); the chunk's
-// frequencies in a fixed order (deterministic).
+// the phase split into its row factor (per thread) and column factor (per tap). One thread per
+// (o, i, a) keeps the kw column taps in registers; the chunk's frequencies are summed in a
+// fixed order (deterministic).
+template <int KW>
 __global__ void __launch_bounds__(128) backward_dw_kernel(LayerArgs La, const float2* G, int g_begin,
                                                           int chunk, int c_begin, float* partial) {
   const int CC = La.c_out * La.c_in;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  const int c = c_begin + blockIdx.y;
-  if (e >= CC) return;
   const int kh = La.kh, kw = La.kw;
-  float acc[kMaxTaps];
-#pragma unroll 1
-  for (int t = 0; t < kh * kw; ++t) acc[t] = 0.f;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = c_begin + blockIdx.y;
+  if (tid >= CC * kh) return;
+  const int e = tid / kh, a = tid - e * kh;
+  float acc[KW];
+#pragma unroll
+  for (int b = 0; b < KW; ++b) acc[b] = 0.f;
   const int h0 = c * chunk, h1 = min(La.F_h, h0 + chunk);
   for (int h = h0; h < h1; ++h) {
     const int f = La.half[h];
     const int j = f / La.m, l = f - j * La.m;
     const float2 g = G[(size_t)(h - g_begin) * CC + e];
-    for (int a = 0; a < kh; ++a) {
-      const float2 pa = La.tw_n[mod_pos(j * (a - La.ph), La.n)];
-      // G * conj(pa)
-      const float2 ga = make_float2(g.x * pa.x + g.y * pa.y, g.y * pa.x - g.x * pa.y);
-      for (int b = 0; b < kw; ++b) {
+    const float2 pa = La.tw_n[mod_pos(j * (a - La.ph), La.n)];
+    // G * conj(pa)
+    const float2 ga = make_float2(g.x * pa.x + g.y * pa.y, g.y * pa.x - g.x * pa.y);
+#pragma unroll
+    for (int b = 0; b < KW; ++b) {
+      if (b < kw) {
         const float2 pb = La.tw_m[mod_pos(l * (b - La.pw), La.m)];
-        // Re(ga * conj(pb))
-        acc[a * kw + b] += ga.x * pb.x + ga.y * pb.y;
+        acc[b] = fmaf(ga.x, pb.x, fmaf(ga.y, pb.y, acc[b]));   // Re(ga * conj(pb))
       }
     }
   }
-  float* p = partial + ((size_t)c * CC + e) * (kh * kw);
-  for (int t = 0; t < kh * kw; ++t) p[t] = acc[t];
+  float* p = partial + ((size_t)c * CC + e) * (kh * kw) + (size_t)a * kw;
+#pragma unroll
+  for (int b = 0; b < KW; ++b)
+    if (b < kw) p[b] = acc[b];
 }
 
 // Stage 3: dw = sum over chunks in order.
@@ -228,8 +253,10 @@ cudaError_t launch_backward(const LayerArgs& La, const float* dsigma, int half_o
     ++*nkernels;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    dim3 gd((CC + 127) / 128, c1 - c0);
-    backward_dw_kernel<<<gd, 128, 0, s>>>(La, G, h0, chunk, c0, partial);
+    dim3 gd((CC * La.kh + 127) / 128, c1 - c0);
+    if (La.kw <= 3) backward_dw_kernel<3><<<gd, 128, 0, s>>>(La, G, h0, chunk, c0, partial);
+    else if (La.kw <= 7) backward_dw_kernel<7><<<gd, 128, 0, s>>>(La, G, h0, chunk, c0, partial);
+    else backward_dw_kernel<15><<<gd, 128, 0, s>>>(La, G, h0, chunk, c0, partial);
     ++*nkernels;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -39,7 +39,7 @@ namespace lfa {
 
 namespace cg = cooperative_groups;
 
-template <int NP_, int L_, int MR_, int WR_, bool VEC_, int CS_>
+template <int NP_, int L_, int MR_, int WR_, bool VEC_, int CS_, int MINB_ = 1>
 struct JCfg {
   static constexpr int NP = NP_, L = L_, MR = MR_, WR = WR_, CS = CS_;
   static constexpr bool VEC = VEC_;
@@ -62,6 +62,7 @@ struct JCfg {
   static constexpr size_t SYM_BYTES = (size_t)(MBOX + kMaxTaps) * 8 + NC * 4 + 2 * TPC * 4 + 64;
   static constexpr size_t UNIT_BYTES = SPU * SYM_BYTES + 64;
   static constexpr size_t SMEM = UPB * UNIT_BYTES;
+  static constexpr int MINB = MINB_;   // resident CTAs per SM the register allocation aims for
   static_assert((size_t)NC * (XR + WRC) <= (size_t)MBOX || CS > 1, "staging must fit the mailbox");
 };
 
@@ -167,7 +168,7 @@ __device__ __forceinline__ float rsqrt_nr(float x) {
 // One Jacobi round on the team's pair (a, b) (symmetric in the two columns): dots, butterfly,
 // rotation of X and W. Returns whether a rotation was applied.
 template <class C>
-__device__ __forceinline__ bool pair_step(Planes<C>& a, Planes<C>& b, float tol2) {
+__device__ __forceinline__ bool pair_step(Planes<C>& a, Planes<C>& b, float tol2, float4& prm) {
   constexpr int MH = C::MH, WH = C::WH, L = C::L;
   // real and imaginary planes accumulate separately: eight independent chains
   float2 alr = f2(0.f), ali = f2(0.f), ber = f2(0.f), bei = f2(0.f);
@@ -212,6 +213,7 @@ __device__ __forceinline__ bool pair_step(Planes<C>& a, Planes<C>& b, float tol2
   // a' = a + (c-1) a - conj(e s) b ; b' = b + (c-1) b + (e s) a,  e s = sr + i si:
   //   a'r = ar + cm1 ar - sr br - si bi     a'i = ai + cm1 ai - sr bi + si br
   //   b'r = br + cm1 br + sr ar - si ai     b'i = bi + cm1 bi + sr ai + si ar
+  prm = make_float4(cm1, sr, si, 0.f);
   const float2 c2 = f2(cm1), s2 = f2(sr), ns2 = f2(-sr), t2 = f2(si), nt2 = f2(-si);
 #pragma unroll
   for (int k = 0; k < MH; ++k) {
@@ -232,6 +234,20 @@ __device__ __forceinline__ bool pair_step(Planes<C>& a, Planes<C>& b, float tol2
     }
   }
   return true;
+}
+
+// Apply a logged rotation (c-1, Re(e s), Im(e s)) to the X planes of a pair (the replay).
+template <class C>
+__device__ __forceinline__ void apply_rotation(Planes<C>& a, Planes<C>& b, float4 prm) {
+  const float2 c2 = f2(prm.x), s2 = f2(prm.y), ns2 = f2(-prm.y), t2 = f2(prm.z), nt2 = f2(-prm.z);
+#pragma unroll
+  for (int k = 0; k < C::MH; ++k) {
+    const float2 Ar = a.xr[k], Ai = a.xi[k], Br = b.xr[k], Bi = b.xi[k];
+    a.xr[k] = __ffma2_rn(nt2, Bi, __ffma2_rn(ns2, Br, __ffma2_rn(c2, Ar, Ar)));
+    a.xi[k] = __ffma2_rn(t2, Br, __ffma2_rn(ns2, Bi, __ffma2_rn(c2, Ai, Ai)));
+    b.xr[k] = __ffma2_rn(nt2, Ai, __ffma2_rn(s2, Ar, __ffma2_rn(c2, Br, Br)));
+    b.xi[k] = __ffma2_rn(t2, Ar, __ffma2_rn(s2, Ai, __ffma2_rn(c2, Bi, Bi)));
+  }
 }
 
 // Write column `a` (id `ida`) to a mailbox slot, planes lane-interleaved. No barrier inside: the
@@ -286,9 +302,10 @@ __device__ __forceinline__ float2 w_at(const Planes<C>& a, int s) {
   return s < C::WH ? make_float2(a.wr[k].x, a.wi[k].x) : make_float2(a.wr[k].y, a.wi[k].y);
 }
 
-template <class C, bool FUSED>
-__global__ void __launch_bounds__(C::BLOCK)
+template <class C, bool FUSED, bool LOG = false>
+__global__ void __launch_bounds__(C::BLOCK, C::MINB)
 jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
+  static_assert(!LOG || (!C::VEC && C::CS > 1), "the rotation log serves values-mode cluster variants");
   constexpr int NP = C::NP, L = C::L, MR = C::MR, WR = C::WR, TC = C::TC, NC = C::NC;
   constexpr int TPC = C::TPC, CS = C::CS, RS = C::RS;
   constexpr int Cn = NC - 1;      // rounds per sweep
@@ -462,9 +479,23 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
       }
       return !any_unit || sweeps >= P.max_sweeps;
     };
+    float4 prm;
+    int t = 0;   // round counter (rotation log)
+    float4* lg = nullptr;
+    if constexpr (LOG) lg = P.log + (size_t)h * P.log_cap * NP + team;
+    auto log_round = [&](bool rot) {
+      if constexpr (LOG) {
+        if (lane == 0 && active && t < P.log_cap) lg[(size_t)t * NP] = rot ? prm : make_float4(0.f, 0.f, 0.f, 0.f);
+        ++t;
+      }
+    };
     for (;;) {
       // even round: teams move array 0, team 0 moves array 1
-      if (pair_step<C>(c0, c1, tol2)) { rotated = 1; ++nrot; }
+      {
+        const bool rot = pair_step<C>(c0, c1, tol2, prm);
+        if (rot) { rotated = 1; ++nrot; }
+        log_round(rot);
+      }
       if (team == 0) put_column<C>(c1, id1, dst_e, dst_id_e, lane);
       else put_column<C>(c0, id0, dst_e, dst_id_e, lane);
       sym_sync<C>();
@@ -472,7 +503,11 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
       else get_column<C>(c0, id0, src_e, src_id_e, lane);
       if (++rr == Cn && sweep_end()) break;
       // odd round: every team moves array 1
-      if (pair_step<C>(c0, c1, tol2)) { rotated = 1; ++nrot; }
+      {
+        const bool rot = pair_step<C>(c0, c1, tol2, prm);
+        if (rot) { rotated = 1; ++nrot; }
+        log_round(rot);
+      }
       put_column<C>(c1, id1, dst_o, dst_id_o, lane);
       sym_sync<C>();
       get_column<C>(c1, id1, src_o, src_id_o, lane);
@@ -483,6 +518,23 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
       atomicAdd(&ctr->unconverged, 1ull);
     }
     if (lane == 0 && nrot && active) atomicAdd(&ctr->rotations, (unsigned long long)nrot);
+    if constexpr (LOG) {
+      // raw X columns in column order; sigma, order and vectors come from the finalize kernel
+      if (st == 0 && crank == 0 && active) P.rounds[h] = t < P.log_cap ? t : P.log_cap;
+      if (active) {
+        float2* xo = P.xraw + (size_t)h * M * N;
+#pragma unroll
+        for (int i = 0; i < MR; ++i) {
+          const int row = lane + L * i;
+          if (row < M) {
+            if (id0 < N) xo[(size_t)row * N + id0] = x_at<C>(c0, i);
+            if (id1 < N) xo[(size_t)row * N + id1] = x_at<C>(c1, i);
+          }
+        }
+      }
+      sym_sync<C>();
+      continue;
+    }
 
     // ---------------------------------------------------------------- singular values, order
     const int ca = id0, cb = id1;

@@ -6,33 +6,35 @@
 #pragma once
 #include "jacobi.cuh"
 
-// X(id, NP, L, MR, WR, CS, VEC_OK)
+// X(id, NP, L, MR, WR, CS, VEC_OK, MINB)  MINB: CTAs per SM the register allocation targets
 #define LFA_JACOBI_VARIANTS(X)     \
-  X(0, 2, 4, 2, 1, 1, 1)           \
-  X(1, 2, 8, 8, 1, 1, 1)           \
-  X(2, 4, 4, 4, 2, 1, 1)           \
-  X(3, 4, 8, 8, 1, 1, 1)           \
-  X(4, 8, 4, 8, 4, 1, 1)           \
-  X(5, 8, 8, 8, 2, 1, 1)           \
-  X(6, 16, 8, 4, 4, 1, 1)          \
-  X(7, 16, 8, 8, 4, 1, 1)          \
-  X(8, 32, 8, 8, 8, 1, 1)          \
-  X(9, 32, 4, 16, 16, 1, 1)        \
-  X(10, 32, 16, 8, 4, 1, 1)        \
-  X(11, 64, 16, 8, 8, 2, 1)        \
-  X(12, 64, 16, 8, 8, 1, 0)        \
-  X(13, 64, 32, 8, 4, 4, 1)        \
-  X(14, 128, 32, 8, 8, 8, 1)       \
-  X(15, 128, 32, 16, 8, 8, 0)      \
-  X(16, 256, 32, 16, 16, 16, 0)
+  X(0, 2, 4, 2, 1, 1, 1, 1)        \
+  X(1, 2, 8, 8, 1, 1, 1, 1)        \
+  X(2, 4, 4, 4, 2, 1, 1, 1)        \
+  X(3, 4, 8, 8, 1, 1, 1, 1)        \
+  X(4, 8, 4, 8, 4, 1, 1, 1)        \
+  X(5, 8, 8, 8, 2, 1, 1, 1)        \
+  X(6, 16, 8, 4, 4, 1, 1, 1)       \
+  X(7, 16, 8, 8, 4, 1, 1, 1)       \
+  X(8, 32, 8, 8, 8, 1, 1, 1)       \
+  X(9, 32, 4, 16, 16, 1, 1, 1)     \
+  X(10, 32, 16, 8, 4, 1, 1, 1)     \
+  X(11, 64, 16, 8, 8, 2, 1, 1)     \
+  X(12, 64, 16, 8, 8, 1, 0, 1)     \
+  X(13, 64, 32, 8, 4, 4, 1, 1)     \
+  X(14, 128, 32, 8, 8, 8, 1, 1)    \
+  X(15, 128, 32, 16, 8, 8, 0, 1)   \
+  X(16, 256, 32, 16, 16, 16, 0, 1) \
+  X(17, 32, 16, 4, 4, 1, 1, 2)     \
+  X(18, 16, 16, 4, 2, 1, 1, 2)
 
 namespace lfa {
 
-template <int NP, int L, int MR, int WR, int CS, bool VEC, bool FUSED>
+template <int NP, int L, int MR, int WR, int CS, int MB, bool VEC, bool FUSED, bool LOG = false>
 cudaError_t jacobi_launch_t(const JacobiLaunch& P, int grid, cudaStream_t s) {
-  using C = JCfg<NP, L, MR, WR, VEC, CS>;
+  using C = JCfg<NP, L, MR, WR, VEC, CS, MB>;
   if constexpr (CS == 1) {
-    jacobi_kernel<C, FUSED><<<grid, C::BLOCK, C::SMEM, s>>>(P);
+    jacobi_kernel<C, FUSED, LOG><<<grid, C::BLOCK, C::SMEM, s>>>(P);
     return cudaGetLastError();
   } else {
     cudaLaunchConfig_t cfg = {};
@@ -47,27 +49,27 @@ cudaError_t jacobi_launch_t(const JacobiLaunch& P, int grid, cudaStream_t s) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, jacobi_kernel<C, FUSED>, P);
+    return cudaLaunchKernelEx(&cfg, jacobi_kernel<C, FUSED, LOG>, P);
   }
 }
 
-template <int NP, int L, int MR, int WR, int CS, bool VEC, bool FUSED>
+template <int NP, int L, int MR, int WR, int CS, int MB, bool VEC, bool FUSED, bool LOG = false>
 cudaError_t jacobi_prepare_t() {
-  using C = JCfg<NP, L, MR, WR, VEC, CS>;
-  cudaError_t e = cudaFuncSetAttribute(jacobi_kernel<C, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  using C = JCfg<NP, L, MR, WR, VEC, CS, MB>;
+  cudaError_t e = cudaFuncSetAttribute(jacobi_kernel<C, FUSED, LOG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)C::SMEM);
   if (e == cudaSuccess && CS > 8)
-    e = cudaFuncSetAttribute(jacobi_kernel<C, FUSED>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute(jacobi_kernel<C, FUSED, LOG>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   return e;
 }
 
 // Largest grid (in CTAs) that is fully co-resident: blocks per SM x SMs, or clusters x CS.
-template <int NP, int L, int MR, int WR, int CS, bool VEC, bool FUSED>
+template <int NP, int L, int MR, int WR, int CS, int MB, bool VEC, bool FUSED, bool LOG = false>
 cudaError_t jacobi_grid_t(int sms, int* grid) {
-  using C = JCfg<NP, L, MR, WR, VEC, CS>;
+  using C = JCfg<NP, L, MR, WR, VEC, CS, MB>;
   if constexpr (CS == 1) {
     int b = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, jacobi_kernel<C, FUSED>, C::BLOCK, C::SMEM);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, jacobi_kernel<C, FUSED, LOG>, C::BLOCK, C::SMEM);
     *grid = b * sms;
     return e;
   } else {
@@ -83,7 +85,7 @@ cudaError_t jacobi_grid_t(int sms, int* grid) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int nc = 0;
-    cudaError_t e = cudaOccupancyMaxActiveClusters(&nc, jacobi_kernel<C, FUSED>, &cfg);
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&nc, jacobi_kernel<C, FUSED, LOG>, &cfg);
     *grid = nc * CS;
     return e;
   }
@@ -110,31 +112,48 @@ cudaError_t jacobi_grid_t(int sms, int* grid) {
   }
 
 // values-only instantiations exist for every variant; vector ones only where VEC_OK
-#define LFA_CASE_LAUNCH_false_true(id, NP, L, MR, WR, CS, OK) \
-  case id: return jacobi_launch_t<NP, L, MR, WR, CS, false, true>(P, grid, s);
-#define LFA_CASE_LAUNCH_false_false(id, NP, L, MR, WR, CS, OK) \
-  case id: return jacobi_launch_t<NP, L, MR, WR, CS, false, false>(P, grid, s);
-#define LFA_CASE_LAUNCH_true_true(id, NP, L, MR, WR, CS, OK)                              \
+#define LFA_CASE_LAUNCH_false_true(id, NP, L, MR, WR, CS, OK, MB) \
+  case id: return jacobi_launch_t<NP, L, MR, WR, CS, MB, false, true>(P, grid, s);
+#define LFA_CASE_LAUNCH_false_false(id, NP, L, MR, WR, CS, OK, MB) \
+  case id: return jacobi_launch_t<NP, L, MR, WR, CS, MB, false, false>(P, grid, s);
+#define LFA_CASE_LAUNCH_true_true(id, NP, L, MR, WR, CS, OK, MB)                              \
   case id:                                                                                 \
-    if constexpr (OK) return jacobi_launch_t<NP, L, MR, WR, CS, true, true>(P, grid, s); \
+    if constexpr (OK) return jacobi_launch_t<NP, L, MR, WR, CS, MB, true, true>(P, grid, s); \
     else return cudaErrorInvalidValue;
-#define LFA_CASE_PREPARE_false_true(id, NP, L, MR, WR, CS, OK) \
-  case id: return jacobi_prepare_t<NP, L, MR, WR, CS, false, true>();
-#define LFA_CASE_PREPARE_false_false(id, NP, L, MR, WR, CS, OK) \
-  case id: return jacobi_prepare_t<NP, L, MR, WR, CS, false, false>();
-#define LFA_CASE_PREPARE_true_true(id, NP, L, MR, WR, CS, OK)                    \
+#define LFA_CASE_PREPARE_false_true(id, NP, L, MR, WR, CS, OK, MB) \
+  case id: return jacobi_prepare_t<NP, L, MR, WR, CS, MB, false, true>();
+#define LFA_CASE_PREPARE_false_false(id, NP, L, MR, WR, CS, OK, MB) \
+  case id: return jacobi_prepare_t<NP, L, MR, WR, CS, MB, false, false>();
+#define LFA_CASE_PREPARE_true_true(id, NP, L, MR, WR, CS, OK, MB)                    \
   case id:                                                                        \
-    if constexpr (OK) return jacobi_prepare_t<NP, L, MR, WR, CS, true, true>();  \
+    if constexpr (OK) return jacobi_prepare_t<NP, L, MR, WR, CS, MB, true, true>();  \
     else return cudaErrorInvalidValue;
-#define LFA_CASE_GRID_false_true(id, NP, L, MR, WR, CS, OK) \
-  case id: return jacobi_grid_t<NP, L, MR, WR, CS, false, true>(sms, g);
-#define LFA_CASE_GRID_false_false(id, NP, L, MR, WR, CS, OK) \
-  case id: return jacobi_grid_t<NP, L, MR, WR, CS, false, false>(sms, g);
-#define LFA_CASE_GRID_true_true(id, NP, L, MR, WR, CS, OK)                           \
+#define LFA_CASE_GRID_false_true(id, NP, L, MR, WR, CS, OK, MB) \
+  case id: return jacobi_grid_t<NP, L, MR, WR, CS, MB, false, true>(sms, g);
+#define LFA_CASE_GRID_false_false(id, NP, L, MR, WR, CS, OK, MB) \
+  case id: return jacobi_grid_t<NP, L, MR, WR, CS, MB, false, false>(sms, g);
+#define LFA_CASE_GRID_true_true(id, NP, L, MR, WR, CS, OK, MB)                           \
   case id:                                                                            \
-    if constexpr (OK) return jacobi_grid_t<NP, L, MR, WR, CS, true, true>(sms, g);   \
+    if constexpr (OK) return jacobi_grid_t<NP, L, MR, WR, CS, MB, true, true>(sms, g);   \
     else return cudaErrorInvalidValue;
 
+// the rotation-logging forward exists for the values-mode cluster variants only
+#define LFA_CASE_LAUNCH_log_log(id, NP, L, MR, WR, CS, OK, MB)                                         \
+  case id:                                                                                           \
+    if constexpr (CS > 1) return jacobi_launch_t<NP, L, MR, WR, CS, MB, false, true, true>(P, grid, s); \
+    else return cudaErrorInvalidValue;
+#define LFA_CASE_PREPARE_log_log(id, NP, L, MR, WR, CS, OK, MB)                              \
+  case id:                                                                                 \
+    if constexpr (CS > 1) return jacobi_prepare_t<NP, L, MR, WR, CS, MB, false, true, true>(); \
+    else return cudaErrorInvalidValue;
+#define LFA_CASE_GRID_log_log(id, NP, L, MR, WR, CS, OK, MB)                                     \
+  case id:                                                                                     \
+    if constexpr (CS > 1) return jacobi_grid_t<NP, L, MR, WR, CS, MB, false, true, true>(sms, g); \
+    else return cudaErrorInvalidValue;
+
+cudaError_t jacobi_val_log_launch(int id, const JacobiLaunch& P, int grid, cudaStream_t s);
+cudaError_t jacobi_val_log_prepare(int id);
+cudaError_t jacobi_val_log_grid(int id, int sms, int* g);
 cudaError_t jacobi_vec_fused_launch(int id, const JacobiLaunch& P, int grid, cudaStream_t s);
 cudaError_t jacobi_vec_fused_prepare(int id);
 cudaError_t jacobi_vec_fused_grid(int id, int sms, int* g);

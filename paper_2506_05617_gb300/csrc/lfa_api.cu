@@ -89,13 +89,13 @@ bool build_schedule(int NC, std::vector<ushort2>& out) {
 // --------------------------------------------------------------------------- variants
 struct VDesc { int NP, L, MR, WR, CS, vec_ok; };
 const VDesc kVariants[] = {
-#define LFA_VD(id, NP, L, MR, WR, CS, OK) {NP, L, MR, WR, CS, OK},
+#define LFA_VD(id, NP, L, MR, WR, CS, OK, MB) {NP, L, MR, WR, CS, OK},
     LFA_JACOBI_VARIANTS(LFA_VD)
 #undef LFA_VD
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 const char* kVariantNames[] = {
-#define LFA_VN(id, NP, L, MR, WR, CS, OK) "reg_np" #NP "_l" #L "_mr" #MR "_wr" #WR "_cs" #CS,
+#define LFA_VN(id, NP, L, MR, WR, CS, OK, MB) "reg_np" #NP "_l" #L "_mr" #MR "_wr" #WR "_cs" #CS,
     LFA_JACOBI_VARIANTS(LFA_VN)
 #undef LFA_VN
 };
@@ -191,6 +191,13 @@ struct lfa_plan_s {
   struct Group { int variant; std::vector<int> layers; int items; int grid; };
   std::vector<Group> groups;
   std::vector<int> plain_grid;            // per layer (plain path)
+  // layers whose W does not fit registers: values-mode forward with a rotation log + replay
+  struct Logged { int layer; int variant; int grid; int batch; int log_cap; int sweeps_cap; };
+  std::vector<Logged> logged;
+  float4* log_ws = nullptr;
+  int32_t* rounds_ws = nullptr;
+  float2* xraw_ws = nullptr;
+  float2* wraw_ws = nullptr;
   // device memory
   void* dmem = nullptr;
   size_t dbytes = 0;
@@ -289,7 +296,60 @@ lfa_status_t enqueue_forward(lfa_plan_s* p, const float* const* w, float* const*
     P.counters = p->counters;
     LFA_CUDA_TRY(vlaunch(g.variant, p->vec, true, P, g.grid, s));
   }
+  // logged layers: per batch of symbols, the values-mode forward that logs its rotations and
+  // writes sigma and the X-side vectors, then the replay that builds W
+  for (const auto& lg : p->logged) {
+    const LayerArgs& base = p->args[lg.layer];
+    const int NP = kVariants[lg.variant].NP;
+    for (int b0 = 0; b0 < base.F_h; b0 += lg.batch) {
+      const int cnt = std::min(lg.batch, base.F_h - b0);
+      LayerArgs La = base;
+      La.w = w[lg.layer];
+      La.half = base.half + b0;
+      La.F_h = cnt;
+      La.item_begin = 0;
+      La.sigma = sigma[lg.layer] + (p->half_output ? (size_t)b0 * base.r : 0);
+      La.U = reinterpret_cast<float2*>(U[lg.layer]) + (size_t)b0 * base.c_out * base.r;
+      La.V = reinterpret_cast<float2*>(V[lg.layer]) + (size_t)b0 * base.c_in * base.r;
+      JacobiLaunch P{};
+      P.L[0] = La;
+      P.nlayers = 1;
+      P.total_items = cnt;
+      P.max_sweeps = lg.sweeps_cap;
+      P.half_output = p->half_output;
+      P.queue_slot = 15;
+      P.counters = p->counters;
+      P.log = p->log_ws;
+      P.log_cap = lg.log_cap;
+      P.rounds = p->rounds_ws;
+      P.xraw = p->xraw_ws;
+      LFA_CUDA_TRY(cudaMemsetAsync(&p->counters->queue[15], 0, sizeof(unsigned), s));
+      const int cs = kVariants[lg.variant].CS;
+      const int grid = std::max(cs, std::min(cnt * cs, lg.grid) / cs * cs);
+      LFA_CUDA_TRY(jacobi_val_log_launch(lg.variant, P, grid, s));
+      ReplayArgs R;
+      R.log = p->log_ws;
+      R.log_cap = lg.log_cap;
+      R.rounds = p->rounds_ws;
+      R.wraw = p->wraw_ws;
+      R.xraw = p->xraw_ws;
+      R.La = La;
+      R.half_output = p->half_output;
+      R.counters = p->counters;
+      int nk = 0;
+      LFA_CUDA_TRY(launch_replay(NP, R, cnt, s, &nk));
+    }
+  }
   return LFA_OK;
+}
+
+int64_t logged_launches(const lfa_plan_s* p) {
+  int64_t n = 0;
+  for (const auto& lg : p->logged) {
+    const int batches = (p->args[lg.layer].F_h + lg.batch - 1) / lg.batch;
+    n += 3 * (int64_t)batches;
+  }
+  return n;
 }
 
 }  // namespace
@@ -339,7 +399,8 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
   // ---- per-layer host tables and variant choice
   size_t bytes = align256(sizeof(Counters));
   std::vector<size_t> off_half(nlayers), off_twn(nlayers), off_twm(nlayers);
-  size_t sym_bytes = 0, g_need = 0, part_bytes = 0;
+  size_t sym_bytes = 0, g_need = 0, part_bytes = 0, log_bytes = 0, ranks_bytes = 0, rounds_bytes = 0;
+  size_t wraw_bytes = 0;
   for (int l = 0; l < nlayers; ++l) {
     const lfa_layer_desc_t& d = layers[l];
     LayerArgs& La = p->args[l];
@@ -359,8 +420,32 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
     if (opt && opt->variant >= 0 && variant_fits(opt->variant, La.M, La.N, p->vec)) v = opt->variant;
     if (v < 0) v = tuned_variant(opt ? opt->tune_cache : nullptr, La.M, La.N, p->vec);
     if (v < 0) v = choose_variant(La.M, La.N, p->vec);
+    bool logged = false;
+    if (v < 0 && p->vec && !p->plain) {
+      // W does not fit registers next to X: values-mode cluster variant + rotation log + replay
+      v = choose_variant(La.M, La.N, false);
+      if (v >= 0 && kVariants[v].CS > 1 && (kVariants[v].NP == 128 || kVariants[v].NP == 256)) logged = true;
+      else v = -1;
+    }
     if (v < 0) { free_plan(p); return LFA_ERR_UNSUPPORTED; }
     p->variant[l] = v;
+    if (logged) {
+      lfa_plan_s::Logged lg;
+      lg.layer = l;
+      lg.variant = v;
+      lg.grid = 0;
+      lg.sweeps_cap = std::min(p->max_sweeps, 24);
+      lg.log_cap = lg.sweeps_cap * (2 * kVariants[v].NP - 1);
+      const size_t per_symbol = (size_t)lg.log_cap * kVariants[v].NP * sizeof(float4) +
+                                (size_t)(La.M + La.N) * La.N * sizeof(float2);
+      const size_t budget = (size_t)2 << 30;
+      lg.batch = (int)std::max<size_t>(1, std::min<size_t>(budget / per_symbol, (size_t)La.F_h));
+      log_bytes = std::max(log_bytes, (size_t)lg.batch * lg.log_cap * kVariants[v].NP * sizeof(float4));
+      ranks_bytes = std::max(ranks_bytes, (size_t)lg.batch * La.M * La.N * sizeof(float2));    // raw X
+      wraw_bytes = std::max(wraw_bytes, (size_t)lg.batch * La.N * La.N * sizeof(float2));
+      rounds_bytes = std::max(rounds_bytes, (size_t)lg.batch * sizeof(int32_t));
+      p->logged.push_back(lg);
+    }
     off_half[l] = bytes; bytes += align256((size_t)La.F_h * 4);
     off_twn[l] = bytes; bytes += align256((size_t)d.n * 8);
     off_twm[l] = bytes; bytes += align256((size_t)d.m * 8);
@@ -389,6 +474,10 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
   const size_t off_sym = bytes; bytes += align256(sym_bytes);
   const size_t off_g = bytes; bytes += align256(g_bytes);
   const size_t off_part = bytes; bytes += align256(part_bytes);
+  const size_t off_log = bytes; bytes += align256(log_bytes);
+  const size_t off_ranks = bytes; bytes += align256(ranks_bytes);
+  const size_t off_rounds = bytes; bytes += align256(rounds_bytes);
+  const size_t off_wraw = bytes; bytes += align256(wraw_bytes);
 
   cudaError_t e = cudaMalloc(&p->dmem, bytes);
   if (e != cudaSuccess) { free_plan(p); return from_cuda(e); }
@@ -399,6 +488,10 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
   p->g_ws = g_bytes ? reinterpret_cast<float2*>(base + off_g) : nullptr;
   p->g_cap_bytes = (int64_t)g_bytes;
   p->partial_ws = part_bytes ? reinterpret_cast<float*>(base + off_part) : nullptr;
+  p->log_ws = log_bytes ? reinterpret_cast<float4*>(base + off_log) : nullptr;
+  p->xraw_ws = ranks_bytes ? reinterpret_cast<float2*>(base + off_ranks) : nullptr;
+  p->rounds_ws = rounds_bytes ? reinterpret_cast<int32_t*>(base + off_rounds) : nullptr;
+  p->wraw_ws = wraw_bytes ? reinterpret_cast<float2*>(base + off_wraw) : nullptr;
 
   // ---- upload tables (synchronous, plan time only)
   std::vector<float2> tw;
@@ -430,7 +523,8 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
     g.variant = v;
     g.items = 0;
     for (int l = 0; l < nlayers; ++l)
-      if (p->variant[l] == v) {
+      if (p->variant[l] == v && std::none_of(p->logged.begin(), p->logged.end(),
+                                              [l](const lfa_plan_s::Logged& q) { return q.layer == l; })) {
         g.layers.push_back(l);
         g.items += (p->args[l].F_h + variant_spu(v) - 1) / variant_spu(v);
       }
@@ -452,7 +546,14 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
         p->plain_grid[l] = std::max(cs, std::min(items * cs, full) / cs * cs);
       }
   }
-  if (e == cudaSuccess && p->groups.size() > 16) e = cudaErrorInvalidValue;
+  for (auto& lg : p->logged) {
+    if (e != cudaSuccess) break;
+    e = jacobi_val_log_prepare(lg.variant);
+    if (e == cudaSuccess) e = prepare_replay(kVariants[lg.variant].NP);
+    if (e == cudaSuccess) e = jacobi_val_log_grid(lg.variant, p->sms, &lg.grid);
+    if (e == cudaSuccess && lg.grid < 1) e = cudaErrorInvalidConfiguration;
+  }
+  if (e == cudaSuccess && p->groups.size() > 15) e = cudaErrorInvalidValue;   // slot 15: logged layers
   if (e == cudaSuccess && p->use_graph) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) { free_plan(p); return from_cuda(e); }
   *plan = p;
@@ -471,7 +572,7 @@ lfa_status_t lfa_svd(lfa_plan_t p, const float* const* w, float* const* sigma, f
   p->last_stream = s;
   if (!p->use_graph) {
     lfa_status_t st = enqueue_forward(p, w, sigma, U, V, s);
-    if (st == LFA_OK && !p->plain) g_launches += (int64_t)p->groups.size();
+    if (st == LFA_OK && !p->plain) g_launches += (int64_t)p->groups.size() + logged_launches(p);
     return st;
   }
   // graph path: capture once per distinct set of buffers, then replay
@@ -498,7 +599,7 @@ lfa_status_t lfa_svd(lfa_plan_t p, const float* const* w, float* const* sigma, f
     p->graph_key = key;
   }
   lfa_status_t st = from_cuda(cudaGraphLaunch(p->exec, s));
-  if (st == LFA_OK) g_launches += (int64_t)p->groups.size();
+  if (st == LFA_OK) g_launches += (int64_t)p->groups.size() + logged_launches(p);
   return st;
 }
 
@@ -516,9 +617,9 @@ lfa_status_t lfa_expand(lfa_plan_t p, int32_t layer, const float* U, const float
   if (p == nullptr || layer < 0 || layer >= p->nlayers || !p->vec) return LFA_ERR_INVALID_ARG;
   const LayerArgs& La = p->args[layer];
   const int64_t total = (int64_t)La.n * La.m * La.r;
-  if (first < 0 || count < 0 || first + count > total || count > 0x7fffffff) return LFA_ERR_INVALID_ARG;
+  if (first < 0 || count < 0 || first + count > total) return LFA_ERR_INVALID_ARG;
   if ((u_hat && !U) || (v_hat && !V)) return LFA_ERR_INVALID_ARG;
-  if (count > 0) g_launches += 1;
+  if (count > 0) g_launches += (count + 65534) / 65535;
   return from_cuda(launch_expand(La, reinterpret_cast<const float2*>(U), reinterpret_cast<const float2*>(V),
                                  first, count, reinterpret_cast<float2*>(u_hat),
                                  reinterpret_cast<float2*>(v_hat), static_cast<cudaStream_t>(stream)));

@@ -46,7 +46,30 @@ struct JacobiLaunch {
   int32_t half_output;
   int32_t queue_slot;
   Counters* counters;
+  // rotation log (symbols whose W does not fit registers): per symbol h of the launch,
+  // log[(h * log_cap + t) * NP + team] = (c - 1, Re(e s), Im(e s), 0) of round t (zeros: no
+  // rotation), rounds[h] = number of rounds run, xraw[h][row][column] = the final X columns in
+  // column order (sigma, order and normalisation are left to the finalize kernel).
+  float4* log;
+  int32_t log_cap;
+  int32_t* rounds;
+  float2* xraw;
 };
+
+// Replay of logged rotations onto W = I (one CTA per (row block, symbol)), then the finalize
+// step: sigma_c = |x_c| / |w_c|, descending order, normalised X and W columns in that order.
+struct ReplayArgs {
+  const float4* log;
+  int32_t log_cap;
+  const int32_t* rounds;
+  float2* wraw;       // [symbols][N][N] W in column order
+  const float2* xraw; // [symbols][M][N] X in column order
+  LayerArgs La;       // the layer, half-grid list offset to the batch
+  int32_t half_output;
+  Counters* counters;
+};
+cudaError_t launch_replay(int NP, const ReplayArgs& R, int symbols, cudaStream_t s, int* nkernels);
+cudaError_t prepare_replay(int NP);   // kernel attributes, once per plan
 
 // Auxiliary kernels (aux_kernels.cu).
 cudaError_t launch_symbols(const LayerArgs& La, float2* out, cudaStream_t s);

@@ -40,6 +40,10 @@ LARGE = [
     (512, 256, 3, 2, 3, False),   # cluster of 8, 16 rows per lane
     (512, 512, 3, 2, 3, False),   # cluster of 16
     (300, 450, 3, 2, 2, False),
+    (512, 512, 3, 2, 3, True),    # vectors through the rotation log + replay
+    (512, 256, 3, 2, 2, True),
+    (256, 512, 3, 2, 2, True),    # wide: V from the normalised columns, U from the replay
+    (400, 400, 1, 1, 2, True),
 ]
 
 
@@ -133,4 +137,28 @@ def test_conv512_values_sampled():
     plan, (s, _, _), st, info = gpu_svd(w, lay.n, lay.m, vectors=False)
     assert st == C.LFA_OK, info
     sampled_sigma_check(w, lay, s, 6, seed=3)
+    plan.close()
+
+
+def test_conv512_n64_values_and_vectors_sampled():
+    """512->512 3x3 on 64x64 (2050 half-grid symbols): values and vectors, checked on samples."""
+    lay = W.layers("conv512_k3_n64")[0]
+    w = W.weights(lay)
+    plan = LfaPlan([(lay.c_out, lay.c_in, lay.kh, lay.kw, lay.n, lay.m)], vectors=True)
+    sig, U, V = plan.svd([torch.from_numpy(w).cuda()])
+    torch.cuda.synchronize()
+    st, info = plan.info()
+    assert st == C.LFA_OK, info
+    s = sig[0].cpu().numpy()
+    sampled_sigma_check(w, lay, s, 4, seed=8)
+    half = O.half_grid(lay.n, lay.m)
+    pick = np.random.default_rng(1).choice(len(half), 3, replace=False)
+    S = O.symbols(w, lay.n, lay.m, freqs=half[pick])
+    Uu = U[0][torch.from_numpy(pick).cuda()].cpu().numpy().astype(np.complex128)
+    Vv = V[0][torch.from_numpy(pick).cuda()].cpu().numpy().astype(np.complex128)
+    ss = s[half[pick]].astype(np.float64)
+    res = np.einsum("hoi,his->hos", S, Vv) - Uu * ss[:, None, :]
+    assert np.max(np.linalg.norm(res, axis=1)) <= VEC_TOL * s.max()
+    for X in (Uu, Vv):
+        assert np.max(np.abs(np.einsum("hos,hot->hst", np.conj(X), X) - np.eye(lay.r))) <= VEC_TOL
     plan.close()
