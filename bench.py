@@ -81,6 +81,26 @@ def measured_traffic(workload: str):
     return rec.get("bytes_per_launch")
 
 
+def rank_seed(layer: W.Layer, rank: int) -> int:
+    """Seed of a rank's weights: every rank decomposes its own independent layers (weak scaling)."""
+    return layer.seed + 1000 * rank
+
+
+def reduce_max(values, dist=None, device="cpu"):
+    """Element-wise max over ranks (the identity without a process group)."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def aggregate_rate(units_per_rank_step: float, steps: int, world: int, slowest_ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank_step * steps / (slowest_ms / 1e3)
+
+
 def fp32_peak_tflops() -> float:
     return SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
@@ -196,7 +216,7 @@ def run_lfa(args, rank: int, world: int, local_rank: int):
     layers = W.layers(args.workload)
     vectors = not (args.values_only or args.workload in VALUES_ONLY)
     # each rank gets its own seeded weights (independent units)
-    ws = [torch.from_numpy(W.weights(l, seed=l.seed + 1000 * rank)).to(dev) for l in layers]
+    ws = [torch.from_numpy(W.weights(l, seed=rank_seed(l, rank))).to(dev) for l in layers]
     specs = [(l.c_out, l.c_in, l.kh, l.kw, l.n, l.m, l.pad_h, l.pad_w) for l in layers]
     plan = LfaPlan(specs, vectors=vectors, tune_cache=args.tune_cache)
     sig, U, V = plan.alloc(dev)
@@ -270,14 +290,11 @@ def run_lfa(args, rank: int, world: int, local_rank: int):
     fwd_ms = [ev[i][0].elapsed_time(ev[i][1]) for i in range(K)]
     total_ms = float(sum(step_ms))
     fwd_mean = float(sum(fwd_ms) / K)
-    if dist is not None:
-        t = torch.tensor([total_ms, fwd_mean], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms, fwd_mean = float(t[0]), float(t[1])
+    total_ms, fwd_mean = reduce_max([total_ms, fwd_mean], dist, dev)
     st, info = plan.info()
 
     # ---- plain per-layer forward-only path (materialised symbols, per-layer launches, no graph)
-    plain = LfaPlan(specs, vectors=False, plain=True)
+    plain = LfaPlan(specs, vectors=False, plain=True, tune_cache=args.tune_cache)
     psig, _, _ = plain.alloc(dev)
     pw = [w.data_ptr() for w in ws]
     pp = [s.data_ptr() for s in psig]
@@ -315,17 +332,14 @@ def run_lfa(args, rank: int, world: int, local_rank: int):
             eev[i][1].record(stream)
         barrier()
         e2e_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in eev]))
-        if dist is not None:
-            t = torch.tensor([e2e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t[0])
+        (e2e_ms,) = reduce_max([e2e_ms], dist, dev)
         sig_per_step = sum(l.n_sigma for l in layers)
-        e2e = {"value": world * sig_per_step / (e2e_ms / 1e3), "unit": "singular values/s",
+        e2e = {"value": aggregate_rate(sig_per_step, 1, world, e2e_ms), "unit": "singular values/s",
                "ms_per_step": e2e_ms, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     sig_per_step = sum(l.n_sigma for l in layers)
     ms_per_step = total_ms / K
-    value = world * sig_per_step * K / (total_ms / 1e3)
+    value = aggregate_rate(sig_per_step, K, world, total_ms)
     flops = sum(layer_flops(l, vectors) for l in layers)
     peak = fp32_peak_tflops()
     achieved = flops / (fwd_mean / 1e3) / 1e12

@@ -110,7 +110,8 @@ bool variant_fits(int v, int M, int N, bool vec) {
          N <= variant_cols(v, vec);
 }
 // Default choice: the smallest padded problem (2*NP columns x MR*L rows) that holds M x N;
-// ties go to the smaller cluster, then to the larger team (fewer registers per lane).
+// ties go to the smaller cluster, then to fewer threads per symbol (fewer butterfly levels and
+// a cheaper barrier per round). An autotuner cache overrides this per problem.
 int choose_variant(int M, int N, bool vec) {
   int best = -1;
   long best_area = 0;
@@ -121,7 +122,7 @@ int choose_variant(int M, int N, bool vec) {
     if (!better && area == best_area) {
       const VDesc& a = kVariants[v];
       const VDesc& b = kVariants[best];
-      better = a.CS < b.CS || (a.CS == b.CS && a.L > b.L);
+      better = a.CS < b.CS || (a.CS == b.CS && a.NP * a.L < b.NP * b.L);
     }
     if (better) {
       best = v;
