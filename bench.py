@@ -59,6 +59,20 @@ def layer_flops(l: W.Layer, vectors: bool) -> float:
     return F_h * (4.0 * l.c_out * l.c_in * l.kh * l.kw + nominal_svd_flops(M, N, vectors))
 
 
+def executed_flops(layers, info, vectors: bool) -> float:
+    """Flops the Jacobi kernel executed, from its device counters: every pair of every round forms
+    three dot products over M complex rows (16 real flops per row), and every applied rotation
+    updates two columns of X (M rows) and, with vectors, of W (N rows) at 24 flops per row.
+    Per-layer sizes are averaged over symbols (exact for a single layer)."""
+    syms = sum((l.F + (1 + (l.n % 2 == 0)) * (1 + (l.m % 2 == 0))) // 2 for l in layers)
+    M = sum(max(l.c_out, l.c_in) * l.F for l in layers) / max(1, sum(l.F for l in layers))
+    N = sum(min(l.c_out, l.c_in) * l.F for l in layers) / max(1, sum(l.F for l in layers))
+    pairs_per_sweep = N * (N - 1) / 2 + (N / 2 if int(N) % 2 else 0)
+    dots = info["sweeps"] * pairs_per_sweep * 16.0 * M
+    rots = info["rotations"] * 24.0 * (M + (N if vectors else 0))
+    return dots + rots
+
+
 def kernel_sha16() -> str:
     import hashlib
     h = hashlib.sha256()
@@ -391,6 +405,8 @@ def run_lfa(args, rank: int, world: int, local_rank: int):
             "flops_model": "nominal Golub-Van Loan complex SVD counts (x4) + symbol assembly, per half-grid symbol",
             "executed_sweeps_per_symbol": info["sweeps"] / max(1, info["symbols"]),
             "rotations": info["rotations"],
+            "executed_tflops": executed_flops(layers, info, vectors) / (fwd_mean / 1e3) / 1e12,
+            "executed_frac": executed_flops(layers, info, vectors) / (fwd_mean / 1e3) / 1e12 / peak,
         },
         "clocks": clocks,
         "gpu_launches": int(launches),

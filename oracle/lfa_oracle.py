@@ -48,7 +48,8 @@ import numpy as np
 __all__ = [
     "origin", "dense_operator", "dense_svd", "symbols", "fft_symbols", "lfa_svd",
     "lift", "apply_operator", "apply_adjoint", "half_grid", "lfa_backward",
-    "regulariser_loss", "regulariser_grad_sigma", "folded_kernel",
+    "regulariser_loss", "regulariser_grad_sigma", "folded_kernel", "edit_values",
+    "spectral_edit", "dense_spectral_edit",
 ]
 
 
@@ -267,3 +268,63 @@ def regulariser_grad_sigma(sigma, lam: float) -> np.ndarray:
     idx = np.unravel_index(int(np.argmax(s)), s.shape)
     g[idx] += 1.0
     return g
+
+
+# --------------------------------------------------------------------------- spectral editing
+def edit_values(sigma, mode: str, a: float, b: float = 0.0) -> np.ndarray:
+    """The map phi applied to every singular value (applications of Sec. I-II: clipping the
+    spectral norm, hard thresholding / low rank). ``sigma`` is [F, r], descending per row.
+
+    clip: min(s, a); clamp: min(max(s, a), b); threshold: s if s >= a else 0;
+    rank: the first round(a) values of every frequency kept, the rest 0.
+    """
+    s = np.asarray(sigma, np.float64)
+    if mode == "clip":
+        return np.minimum(s, a)
+    if mode == "clamp":
+        return np.minimum(np.maximum(s, a), b)
+    if mode == "threshold":
+        return np.where(s >= a, s, 0.0)
+    if mode == "rank":
+        out = s.copy()
+        out[:, int(round(a)):] = 0.0
+        return out
+    raise ValueError(mode)
+
+
+def spectral_edit(w, n: int, m: int, mode: str, a: float, b: float = 0.0, pad_h: int = -1, pad_w: int = -1):
+    """The kh x kw kernel nearest (Frobenius norm of the operator) to U phi(S) V^*.
+
+    The edited operator B has symbols B_k = U_k phi(S_k) V_k^*. The operators of single taps,
+    T[(o, x), (i, x + y_ab)] = 1, are mutually orthogonal with <T, T> = n m when no taps alias
+    (k <= n, m), so the projection of B onto their span has weights
+        w'[o,i,a,b] = <B, T_oiab> / (n m) = (1/(n m)) sum_k Re(B_k[o,i] exp(-2 pi i <k, y_ab>)).
+    """
+    s, U, V = lfa_svd(w, n, m, pad_h, pad_w)
+    g = edit_values(s, mode, a, b) / (n * m)
+    return lfa_backward(w, n, m, g, U, V, pad_h, pad_w)
+
+
+def dense_spectral_edit(w, n: int, m: int, mode: str, a: float, b: float = 0.0, pad_h: int = -1, pad_w: int = -1):
+    """The same projection from the dense operator: full LAPACK SVD, phi on the values grouped
+    by frequency through the lifted vectors, then <B, T_oiab> / <T, T> with the tap operators
+    built entry by entry (small sizes only). Independent of the symbol formula."""
+    w = np.asarray(w, dtype=np.float64)
+    c_out, c_in, kh, kw = w.shape
+    s, U, V = lfa_svd(w, n, m, pad_h, pad_w)
+    sp = edit_values(s, mode, a, b)
+    B = np.zeros((c_out * n * m, c_in * n * m), dtype=np.complex128)
+    for f in range(n * m):
+        j, l = divmod(f, m)
+        uh, vh = lift(U[f], V[f], j, l, n, m)
+        Uf = uh.reshape(uh.shape[0], -1).T          # [c_out n m, r]
+        Vf = vh.reshape(vh.shape[0], -1).T
+        B += (Uf * sp[f][None, :]) @ Vf.conj().T
+    out = np.zeros_like(w)
+    basis = np.zeros_like(w)
+    for idx in np.ndindex(w.shape):
+        basis[idx] = 1.0
+        T = dense_operator(basis, n, m, pad_h, pad_w)
+        out[idx] = np.real(np.sum(B * T)) / np.sum(T * T)
+        basis[idx] = 0.0
+    return out

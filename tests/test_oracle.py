@@ -306,3 +306,28 @@ def test_backward_of_frobenius_norm_closed_form():
     s, U, V = O.lfa_svd(w, n, m)
     dW = O.lfa_backward(w, n, m, 2 * s, U, V)
     np.testing.assert_allclose(dW, 2 * n * m * w, rtol=1e-11, atol=1e-12)
+
+
+# ----------------------------------------------------------------- spectral editing
+@pytest.mark.parametrize("mode,a,b", [("clip", 0.8, 0), ("clamp", 0.3, 0.9), ("threshold", 0.5, 0), ("rank", 2, 0)])
+def test_spectral_edit_matches_dense_projection(mode, a, b):
+    """The symbol-side projection equals the projection of the dense edited operator onto taps."""
+    w = rand_w(3, 3, 3, 3, 31)
+    n, m = 4, 5
+    np.testing.assert_allclose(O.spectral_edit(w, n, m, mode, a, b), O.dense_spectral_edit(w, n, m, mode, a, b),
+                               atol=1e-12)
+
+
+def test_spectral_edit_identity_and_full_support():
+    w = rand_w(3, 2, 3, 3, 32)
+    n, m = 5, 4
+    # phi = identity (clip far above sigma_max) returns the kernel itself
+    np.testing.assert_allclose(O.spectral_edit(w, n, m, "clip", 1e9), w, atol=1e-12)
+    # a kernel covering the whole torus represents every operator: the edit is exact
+    wf = rand_w(3, 3, 4, 4, 33)
+    n = m = 4
+    s = O.lfa_svd(wf, n, m, compute_uv=False)
+    c = 0.6 * s.max()
+    we = O.spectral_edit(wf, n, m, "clip", c)
+    np.testing.assert_allclose(np.sort(O.lfa_svd(we, n, m, compute_uv=False).ravel()),
+                               np.sort(np.minimum(s, c).ravel()), atol=1e-12)
