@@ -166,6 +166,27 @@ lfa_status_t lfa_expand(lfa_plan_t plan, int32_t layer, const float* U, const fl
 lfa_status_t lfa_svd_backward(lfa_plan_t plan, const float* const* dsigma, const float* const* U,
                               const float* const* V, float* const* dw, void* stream);
 
+/* Spectral editing modes (see lfa_spectral_edit). */
+#define LFA_EDIT_CLIP       0  /* phi(s) = min(s, a): clip the spectral norm to a */
+#define LFA_EDIT_CLAMP      1  /* phi(s) = min(max(s, a), b) */
+#define LFA_EDIT_THRESHOLD  2  /* phi(s) = s if s >= a else 0 (hard threshold; a global low rank) */
+#define LFA_EDIT_RANK       3  /* keep the first round(a) singular values of every frequency */
+
+/* Spectral editing: the applications the paper motivates (Sec. I-II: spectral-norm
+ * regularisation, low-rank compression) edit the singular values of the operator. This
+ * returns, per layer, the kh x kw kernel nearest in Frobenius norm to the edited operator
+ * B = U phi(S) V^* (phi applied to every singular value of every frequency):
+ *   w_out[o,i,a,b] = <B, T_oiab> / (n m) = (1/(n m)) sum_k Re( B_k[o,i] exp(-2 pi i <k, y_ab>) ),
+ * T_oiab the operator of one tap (these are orthogonal, <T, T> = n m, when no taps alias,
+ * kh <= n and kw <= m). When the kernel covers the torus (kh = n, kw = m) the edit is exact.
+ *  sigma[l], U[l], V[l]  the layer's lfa_svd outputs (plan with LFA_VECTORS)
+ *  mode, a, b            LFA_EDIT_* and its parameters
+ *  w_out[l]              device float32 [c_out][c_in][kh][kw], overwritten
+ * Uses the plan's backward workspace; deterministic; asynchronous. Errors: LFA_ERR_INVALID_ARG. */
+lfa_status_t lfa_spectral_edit(lfa_plan_t plan, const float* const* sigma, const float* const* U,
+                               const float* const* V, int32_t mode, float a, float b,
+                               float* const* w_out, void* stream);
+
 /* dL/dsigma of the spectral regulariser L = sum_layers max(sigma) + lam * sum (sigma - 1)^2
  * (a spectral-norm term plus an orthogonality term) for each layer's sigma in the plan's
  * sigma layout: dsigma = 2 lam (sigma - 1), plus 1 at the first maximiser (row-major).

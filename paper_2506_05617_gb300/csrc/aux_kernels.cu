@@ -314,3 +314,42 @@ cudaError_t launch_regulariser(const LayerArgs& La, int half_output, const float
 }
 
 }  // namespace lfa
+
+namespace lfa {
+
+// ----------------------------------------------------------------------------- spectral editing
+// g = mult(k) phi(sigma) / (n m): the upstream "gradient" whose backward is the projection of the
+// edited operator onto the kernel taps. With the full-grid layout the backward folds k and -k;
+// with the half-grid layout each row stands for mult(k) = 2 (conjugate pair) or 1 frequencies.
+__global__ void __launch_bounds__(256) edit_values_kernel(LayerArgs La, int half_output, const float* sigma,
+                                                           int mode, float a, float b, float* g) {
+  const int rows = half_output ? La.F_h : La.n * La.m;
+  const int r = La.r;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)rows * r) return;
+  const int row = (int)(e / r), s = (int)(e - (int64_t)row * r);
+  const float v = sigma[e];
+  float p;
+  if (mode == 0) p = fminf(v, a);
+  else if (mode == 1) p = fminf(fmaxf(v, a), b);
+  else if (mode == 2) p = v >= a ? v : 0.f;
+  else p = (float)s < rintf(a) ? v : 0.f;
+  float mult = 1.f;
+  if (half_output) {
+    const int f = La.half[row];
+    const int j = f / La.m, l = f - j * La.m;
+    const int fc = ((La.n - j) % La.n) * La.m + (La.m - l) % La.m;
+    mult = fc != f ? 2.f : 1.f;
+  }
+  g[e] = mult * p / (float)(La.n * La.m);
+}
+
+cudaError_t launch_edit_values(const LayerArgs& La, int half_output, const float* sigma, int mode, float a,
+                               float b, float* g, cudaStream_t s) {
+  const int64_t total = (int64_t)(half_output ? La.F_h : La.n * La.m) * La.r;
+  if (total <= 0) return cudaSuccess;
+  edit_values_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(La, half_output, sigma, mode, a, b, g);
+  return cudaGetLastError();
+}
+
+}  // namespace lfa

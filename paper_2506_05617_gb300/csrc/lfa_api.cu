@@ -207,6 +207,7 @@ struct lfa_plan_s {
   float2* g_ws = nullptr;    // backward G workspace
   int64_t g_cap_bytes = 0;
   float* partial_ws = nullptr;
+  float* edit_ws = nullptr;                 // phi(sigma) / (n m) of one layer (spectral editing)
   std::vector<int> bw_chunks;      // per layer
   // graph cache
   cudaStream_t cap_stream = nullptr;
@@ -475,6 +476,12 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
   const size_t off_sym = bytes; bytes += align256(sym_bytes);
   const size_t off_g = bytes; bytes += align256(g_bytes);
   const size_t off_part = bytes; bytes += align256(part_bytes);
+  size_t edit_bytes = 0;
+  if (p->vec)
+    for (int l = 0; l < nlayers; ++l)
+      edit_bytes = std::max(edit_bytes, (size_t)(p->half_output ? p->args[l].F_h : p->args[l].n * p->args[l].m) *
+                                            p->args[l].r * sizeof(float));
+  const size_t off_edit = bytes; bytes += align256(edit_bytes);
   const size_t off_log = bytes; bytes += align256(log_bytes);
   const size_t off_ranks = bytes; bytes += align256(ranks_bytes);
   const size_t off_rounds = bytes; bytes += align256(rounds_bytes);
@@ -489,6 +496,7 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
   p->g_ws = g_bytes ? reinterpret_cast<float2*>(base + off_g) : nullptr;
   p->g_cap_bytes = (int64_t)g_bytes;
   p->partial_ws = part_bytes ? reinterpret_cast<float*>(base + off_part) : nullptr;
+  p->edit_ws = edit_bytes ? reinterpret_cast<float*>(base + off_edit) : nullptr;
   p->log_ws = log_bytes ? reinterpret_cast<float4*>(base + off_log) : nullptr;
   p->xraw_ws = ranks_bytes ? reinterpret_cast<float2*>(base + off_ranks) : nullptr;
   p->rounds_ws = rounds_bytes ? reinterpret_cast<int32_t*>(base + off_rounds) : nullptr;
@@ -642,6 +650,29 @@ lfa_status_t lfa_svd_backward(lfa_plan_t p, const float* const* dsigma, const fl
                                  reinterpret_cast<const float2*>(V[l]), p->g_ws, g_cap, p->partial_ws,
                                  p->bw_chunks[l], dw[l], s, &nk));
     g_launches += nk;
+  }
+  return LFA_OK;
+}
+
+lfa_status_t lfa_spectral_edit(lfa_plan_t p, const float* const* sigma, const float* const* U,
+                               const float* const* V, int32_t mode, float a, float b, float* const* w_out,
+                               void* stream) {
+  if (p == nullptr || !p->vec || sigma == nullptr || U == nullptr || V == nullptr || w_out == nullptr)
+    return LFA_ERR_INVALID_ARG;
+  if (mode < LFA_EDIT_CLIP || mode > LFA_EDIT_RANK || !std::isfinite(a) || !std::isfinite(b)) return LFA_ERR_INVALID_ARG;
+  for (int l = 0; l < p->nlayers; ++l)
+    if (!sigma[l] || !U[l] || !V[l] || !w_out[l]) return LFA_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int l = 0; l < p->nlayers; ++l) {
+    const LayerArgs& La = p->args[l];
+    LFA_CUDA_TRY(launch_edit_values(La, p->half_output, sigma[l], mode, a, b, p->edit_ws, s));
+    const int64_t CC = (int64_t)La.c_out * La.c_in;
+    const int64_t g_cap = p->g_cap_bytes / (CC * 8);
+    int nk = 0;
+    LFA_CUDA_TRY(launch_backward(La, p->edit_ws, p->half_output, reinterpret_cast<const float2*>(U[l]),
+                                 reinterpret_cast<const float2*>(V[l]), p->g_ws, g_cap, p->partial_ws,
+                                 p->bw_chunks[l], w_out[l], s, &nk));
+    g_launches += 1 + nk;
   }
   return LFA_OK;
 }

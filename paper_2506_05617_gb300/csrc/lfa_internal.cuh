@@ -78,6 +78,8 @@ cudaError_t launch_expand(const LayerArgs& La, const float2* U, const float2* V,
 cudaError_t launch_backward(const LayerArgs& La, const float* dsigma, int half_output,
                             const float2* U, const float2* V, float2* G, int64_t g_cap,
                             float* partial, int chunks, float* dw, cudaStream_t s, int* nkernels);
+cudaError_t launch_edit_values(const LayerArgs& La, int half_output, const float* sigma, int mode, float a,
+                               float b, float* g, cudaStream_t s);
 cudaError_t launch_regulariser(const LayerArgs& La, int half_output, const float* sigma, float lam,
                                float* dsigma, float* loss, cudaStream_t s);
 

@@ -25,6 +25,12 @@ LFA_VECTORS = 0x2
 LFA_HALF_OUTPUT = 0x4
 LFA_PLAIN = 0x8
 
+# spectral editing modes
+LFA_EDIT_CLIP = 0
+LFA_EDIT_CLAMP = 1
+LFA_EDIT_THRESHOLD = 2
+LFA_EDIT_RANK = 3
+
 # status codes
 LFA_OK = 0
 LFA_ERR_INVALID_ARG = 1
@@ -38,7 +44,7 @@ LFA_ERR_TIMEOUT = 7
 # every symbol include/lfa.h and include/lfa_debug.h declare
 EXPORTS = [
     "lfa_plan", "lfa_svd", "lfa_symbols", "lfa_expand", "lfa_svd_backward", "lfa_svd_backward_noalloc",
-    "lfa_regulariser_grad",
+    "lfa_regulariser_grad", "lfa_spectral_edit",
     "lfa_destroy", "lfa_get_info", "lfa_layer_query", "lfa_status_string", "lfa_variant_name",
     "lfa_last_cuda_error", "lfa_kernel_launches", "lfa_version",
     "lfa_debug_schedule", "lfa_debug_half_grid", "lfa_debug_choose_variant", "lfa_debug_variant_count",
@@ -96,6 +102,7 @@ def lib():
         "lfa_svd_backward": (c_int32, [P, PP, PP, PP, PP, P]),
         "lfa_svd_backward_noalloc": (c_int32, [POINTER(LayerDesc), c_uint32, P, P, P, P, P]),
         "lfa_regulariser_grad": (c_int32, [P, PP, c_float, PP, PP, P]),
+        "lfa_spectral_edit": (c_int32, [P, PP, PP, PP, c_int32, c_float, c_float, PP, P]),
         "lfa_destroy": (c_int32, [P]),
         "lfa_get_info": (c_int32, [P, POINTER(Info)]),
         "lfa_layer_query": (c_int32, [P, c_int32, POINTER(c_int64), POINTER(c_int32), POINTER(c_int32),
@@ -197,6 +204,13 @@ def lfa_regulariser_grad(plan: int, sigma: Sequence[int], lam: float, dsigma: Se
     n = len(sigma)
     _check(lib().lfa_regulariser_grad(c_void_p(plan), _ptrs(sigma, n), float(lam), _ptrs(dsigma, n),
                                       _ptrs(loss, n), _stream(stream)), "lfa_regulariser_grad")
+
+
+def lfa_spectral_edit(plan: int, sigma: Sequence[int], U: Sequence[int], V: Sequence[int], mode: int, a: float,
+                      b: float, w_out: Sequence[int], stream=None) -> None:
+    n = len(sigma)
+    _check(lib().lfa_spectral_edit(c_void_p(plan), _ptrs(sigma, n), _ptrs(U, n), _ptrs(V, n), int(mode), float(a),
+                                   float(b), _ptrs(w_out, n), _stream(stream)), "lfa_spectral_edit")
 
 
 def lfa_destroy(plan: int) -> None:

@@ -87,6 +87,16 @@ class LfaPlan:
                                [l.data_ptr() for l in loss], stream)
         return dsigma, loss
 
+    def spectral_edit(self, sigma, U, V, mode: str, a: float, b: float = 0.0, stream=None):
+        """Kernels nearest to the operators with edited singular values (see lfa_spectral_edit)."""
+        modes = {"clip": C.LFA_EDIT_CLIP, "clamp": C.LFA_EDIT_CLAMP, "threshold": C.LFA_EDIT_THRESHOLD,
+                 "rank": C.LFA_EDIT_RANK}
+        out = [torch.empty(self.layers[i][:4], dtype=torch.float32, device=U[0].device) for i in range(len(self.layers))]
+        stream = stream if stream is not None else torch.cuda.current_stream(U[0].device)
+        C.lfa_spectral_edit(self.handle, [s.data_ptr() for s in sigma], [u.data_ptr() for u in U],
+                            [v.data_ptr() for v in V], modes[mode], a, b, [o.data_ptr() for o in out], stream)
+        return out
+
     def symbols(self, layer: int, w: torch.Tensor, stream=None):
         c_out, c_in = self.layers[layer][:2]
         out = torch.empty((self.meta[layer]["F_h"], c_out, c_in), dtype=torch.complex64, device=w.device)

@@ -1,0 +1,72 @@
+"""Spectral editing on the GPU (lfa_spectral_edit) against the FP64 oracle's projection of the
+edited operator onto the kernel taps. Tolerance: the backward's, relative 1e-4 in norm; the
+exact full-support case by its spectrum, 1e-5 * sigma_max."""
+import numpy as np
+import pytest
+import torch
+
+import lfa_workloads as W
+import oracle as O
+from paper_2506_05617_gb300.torch_api import LfaPlan
+
+from test_gpu_parity import rand_w
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_05617_gb300 import build as B
+    B.build()
+
+
+def safe_threshold(s):
+    """A threshold in the widest gap of the spectrum's middle, so fp32 and fp64 agree on each side."""
+    v = np.sort(s.ravel())
+    lo, hi = len(v) // 4, 3 * len(v) // 4
+    k = lo + int(np.argmax(np.diff(v[lo:hi])))
+    return 0.5 * (v[k] + v[k + 1])
+
+
+@pytest.mark.parametrize("half", [False, True])
+@pytest.mark.parametrize("shape", [(4, 4, 3, 3, 8, 8), (6, 3, 3, 3, 5, 7), (3, 5, 5, 3, 6, 6), (64, 64, 3, 3, 6, 6)])
+@pytest.mark.parametrize("mode", ["clip", "clamp", "threshold", "rank"])
+def test_spectral_edit_matches_oracle(shape, mode, half):
+    c_out, c_in, kh, kw, n, m = shape
+    w = rand_w(c_out, c_in, kh, kw, seed=51)
+    s_ref = O.lfa_svd(w, n, m, compute_uv=False)
+    smax = float(s_ref.max())
+    a, b = {"clip": (0.7 * smax, 0.0), "clamp": (0.3 * smax, 0.8 * smax),
+            "threshold": (safe_threshold(s_ref), 0.0), "rank": (max(1, min(c_out, c_in) // 2), 0.0)}[mode]
+    plan = LfaPlan([shape], vectors=True, half_output=half)
+    sig, U, V = plan.svd([torch.from_numpy(w).cuda()])
+    got = plan.spectral_edit(sig, U, V, mode, a, b)[0].cpu().numpy()
+    ref = O.spectral_edit(w, n, m, mode, a, b)
+    assert np.linalg.norm(got - ref) <= 1e-4 * max(np.linalg.norm(ref), 1e-30) + 1e-7
+    plan.close()
+
+
+def test_full_support_clip_is_exact():
+    c, k = 8, 6
+    w = rand_w(c, c, k, k, seed=52)
+    s = O.lfa_svd(w, k, k, compute_uv=False)
+    cap = 0.6 * float(s.max())
+    plan = LfaPlan([(c, c, k, k, k, k)], vectors=True)
+    sig, U, V = plan.svd([torch.from_numpy(w).cuda()])
+    we = plan.spectral_edit(sig, U, V, "clip", cap)[0].cpu().numpy()
+    s2 = O.lfa_svd(we, k, k, compute_uv=False)
+    assert np.max(np.abs(np.sort(s2.ravel()) - np.sort(np.minimum(s, cap).ravel()))) <= 1e-5 * s.max()
+    plan.close()
+
+
+def test_conv64_n32_clip_full_size():
+    lay = W.layers("conv64_k3_n32")[0]
+    w = W.weights(lay)
+    plan = LfaPlan([(lay.c_out, lay.c_in, lay.kh, lay.kw, lay.n, lay.m)], vectors=True)
+    sig, U, V = plan.svd([torch.from_numpy(w).cuda()])
+    got = plan.spectral_edit(sig, U, V, "clip", 1.0)[0].cpu().numpy()
+    ref = O.spectral_edit(w, lay.n, lay.m, "clip", 1.0)
+    assert np.linalg.norm(got - ref) <= 1e-4 * np.linalg.norm(ref)
+    plan.close()
