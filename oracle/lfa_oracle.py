@@ -49,7 +49,8 @@ __all__ = [
     "origin", "dense_operator", "dense_svd", "symbols", "fft_symbols", "lfa_svd",
     "lift", "apply_operator", "apply_adjoint", "half_grid", "lfa_backward",
     "regulariser_loss", "regulariser_grad_sigma", "folded_kernel", "edit_values",
-    "spectral_edit", "dense_spectral_edit",
+    "spectral_edit", "dense_spectral_edit", "dense_operator_strided", "symbols_strided",
+    "lfa_svd_strided", "lfa_backward_strided", "lift_strided",
 ]
 
 
@@ -328,3 +329,93 @@ def dense_spectral_edit(w, n: int, m: int, mode: str, a: float, b: float = 0.0, 
         out[idx] = np.real(np.sum(B * T)) / np.sum(T * T)
         basis[idx] = 0.0
     return out
+
+
+# --------------------------------------------------------------------------- strided convolutions
+# A stride-(s_h, s_w) convolution maps an input on the fine (s_h n) x (s_w m) torus to an output on
+# the coarse n x m torus, (A f)(o, x) = sum_{i,a,b} w[o,i,a,b] f(i, s x + y_ab). Seen as a crystal
+# (Sec. III "Introduction to Lattices and Crystals"), the input has s_h s_w points per coarse unit
+# cell: the polyphase components f(i, s x + u), u in [0, s_h) x [0, s_w). A tap at offset
+# y = s q + u (q = floor(y / s) componentwise) couples component u at coarse offset q, so the
+# Fourier modes of the coarse torus are again invariant and the symbol is the c_out x (c_in s_h s_w)
+# matrix  A_k[o, (i, u)] = sum_{taps with y mod s = u} w[o,i,a,b] exp(2 pi i <k, q>).
+# Columns are ordered (i, u_h, u_w) -> i s_h s_w + u_h s_w + u_w.
+
+def dense_operator_strided(w, n: int, m: int, s_h: int, s_w: int, pad_h: int = -1, pad_w: int = -1) -> np.ndarray:
+    """Dense strided periodic operator: row (o, x1, x2) of the coarse grid, column (i, z1, z2) of the
+    fine grid, entry [(o, x), (i, s x + y_ab mod (s_h n, s_w m))] += w[o, i, a, b]."""
+    w = np.asarray(w, dtype=np.float64)
+    c_out, c_in, kh, kw = w.shape
+    ph, pw = origin(kh, kw, pad_h, pad_w)
+    N1, N2 = s_h * n, s_w * m
+    A = np.zeros((c_out * n * m, c_in * N1 * N2), dtype=np.float64)
+    x1, x2 = np.meshgrid(np.arange(n), np.arange(m), indexing="ij")
+    pix = (x1 * m + x2).ravel()
+    for a in range(kh):
+        for b in range(kw):
+            src = (((s_h * x1 + a - ph) % N1) * N2 + ((s_w * x2 + b - pw) % N2)).ravel()
+            for o in range(c_out):
+                for i in range(c_in):
+                    np.add.at(A, (o * n * m + pix, i * N1 * N2 + src), w[o, i, a, b])
+    return A
+
+
+def symbols_strided(w, n: int, m: int, s_h: int, s_w: int, pad_h: int = -1, pad_w: int = -1, freqs=None):
+    """Strided symbols [n m (or len(freqs)), c_out, c_in s_h s_w] (see the block comment above)."""
+    w = np.asarray(w, dtype=np.float64)
+    c_out, c_in, kh, kw = w.shape
+    ph, pw = origin(kh, kw, pad_h, pad_w)
+    S = s_h * s_w
+    sel = np.arange(n * m) if freqs is None else np.asarray(freqs)
+    out = np.zeros((len(sel), c_out, c_in * S), dtype=np.complex128)
+    for a in range(kh):
+        for b in range(kw):
+            qh, uh = divmod(a - ph, s_h)      # python floor division: y = s q + u, 0 <= u < s
+            qw, uw = divmod(b - pw, s_w)
+            phase = _phase(n, m, qh, qw).reshape(n * m)[sel]
+            cols = np.arange(c_in) * S + uh * s_w + uw
+            out[:, :, cols] += phase[:, None, None] * w[None, :, :, a, b]
+    return out
+
+
+def lfa_svd_strided(w, n: int, m: int, s_h: int, s_w: int, pad_h: int = -1, pad_w: int = -1,
+                    compute_uv: bool = True, freqs=None):
+    """Per-frequency LAPACK SVD of the strided symbols (Algorithm 1 on the crystal)."""
+    S = symbols_strided(w, n, m, s_h, s_w, pad_h, pad_w, freqs)
+    if not compute_uv:
+        return np.linalg.svd(S, compute_uv=False)
+    U, sv, Vh = np.linalg.svd(S, full_matrices=False)
+    return sv, U, np.conj(np.swapaxes(Vh, 1, 2))
+
+
+def lfa_backward_strided(w, n: int, m: int, s_h: int, s_w: int, g, U, V, pad_h: int = -1, pad_w: int = -1):
+    """dL/dw for the strided operator: dW[o,i,a,b] = sum_k Re(sum_s g conj(U[o,s]) V[(i,u_ab),s] exp(2 pi i <k,q_ab>))."""
+    w = np.asarray(w, dtype=np.float64)
+    c_out, c_in, kh, kw = w.shape
+    ph, pw = origin(kh, kw, pad_h, pad_w)
+    S = s_h * s_w
+    H = np.einsum("fs,fos,fcs->foc", np.asarray(g, np.float64), np.conj(U), V)   # [F, c_out, c_in S]
+    dW = np.zeros_like(w)
+    for a in range(kh):
+        for b in range(kw):
+            qh, uh = divmod(a - ph, s_h)
+            qw, uw = divmod(b - pw, s_w)
+            phase = _phase(n, m, qh, qw).reshape(n * m)
+            cols = np.arange(c_in) * S + uh * s_w + uw
+            dW[:, :, a, b] = np.real(np.einsum("f,foi->oi", phase, H[:, :, cols]))
+    return dW
+
+
+def lift_strided(U_k, V_k, j: int, l: int, n: int, m: int, s_h: int, s_w: int):
+    """Global singular vectors of a strided operator: u_hat on the coarse grid [q, c_out, n, m] as in
+    ``lift``; v_hat on the fine grid [q, c_in, s_h n, s_w m] with v_hat[i, s x + u] = V[(i,u)] f_k(x)."""
+    c_in_s = np.asarray(V_k).shape[0]
+    S = s_h * s_w
+    c_in = c_in_s // S
+    t = ((j * np.arange(n))[:, None] % n) / n + ((l * np.arange(m))[None, :] % m) / m
+    mode = np.exp(2j * np.pi * t) / np.sqrt(n * m)
+    u_hat = np.einsum("cq,xy->qcxy", np.asarray(U_k), mode)
+    Vr = np.asarray(V_k).reshape(c_in, s_h, s_w, -1)                 # [i, u_h, u_w, q]
+    v = np.einsum("iabq,xy->qixayb", Vr, mode)                        # [q, i, x1, u_h, x2, u_w]
+    v_hat = v.reshape(v.shape[0], c_in, n * s_h, m * s_w)
+    return u_hat, v_hat

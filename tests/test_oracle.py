@@ -331,3 +331,70 @@ def test_spectral_edit_identity_and_full_support():
     we = O.spectral_edit(wf, n, m, "clip", c)
     np.testing.assert_allclose(np.sort(O.lfa_svd(we, n, m, compute_uv=False).ravel()),
                                np.sort(np.minimum(s, c).ravel()), atol=1e-12)
+
+
+# ----------------------------------------------------------------- strided convolutions (crystals)
+@pytest.mark.parametrize("c_out,c_in,kh,kw,n,m,sh,sw", [
+    (3, 2, 3, 3, 4, 3, 2, 2), (2, 3, 3, 5, 3, 4, 2, 1), (4, 2, 1, 1, 3, 3, 2, 2), (2, 2, 4, 4, 3, 2, 2, 3)])
+def test_strided_dense_operator_is_torch_strided_circular_conv(c_out, c_in, kh, kw, n, m, sh, sw):
+    w = rand_w(c_out, c_in, kh, kw, 41)
+    ph, pw = kh // 2, kw // 2
+    A = O.dense_operator_strided(w, n, m, sh, sw)
+    f = RNG.standard_normal((c_in, sh * n, sw * m))
+    ft = Fnn.pad(torch.as_tensor(f)[None], (pw, kw - 1 - pw, ph, kh - 1 - ph), mode="circular")
+    ref = Fnn.conv2d(ft, torch.as_tensor(w), stride=(sh, sw))[0].numpy()
+    assert ref.shape == (c_out, n, m)
+    np.testing.assert_allclose(A @ f.ravel(), ref.ravel(), rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("c_out,c_in,kh,kw,n,m,sh,sw", [
+    (3, 2, 3, 3, 4, 3, 2, 2), (8, 2, 3, 3, 3, 3, 2, 2), (2, 3, 3, 5, 3, 4, 2, 1), (5, 1, 5, 5, 3, 3, 3, 3)])
+def test_strided_dense_svd_is_union_of_crystal_symbol_svds(c_out, c_in, kh, kw, n, m, sh, sw):
+    w = rand_w(c_out, c_in, kh, kw, 42)
+    dense = np.sort(np.linalg.svd(O.dense_operator_strided(w, n, m, sh, sw), compute_uv=False))[::-1]
+    s = O.lfa_svd_strided(w, n, m, sh, sw, compute_uv=False)
+    r = min(c_out, c_in * sh * sw)
+    assert s.shape == (n * m, r)
+    np.testing.assert_allclose(dense[: n * m * r], np.sort(s.ravel())[::-1], atol=1e-12 * dense[0])
+    # Parseval: when no two taps alias on the fine torus, every tap appears once per coarse site
+    if kh <= sh * n and kw <= sw * m:
+        np.testing.assert_allclose(np.sum(s ** 2), n * m * np.sum(w ** 2), rtol=1e-12)
+
+
+def test_stride_one_reduces_to_the_plain_symbols():
+    w = rand_w(3, 4, 3, 5, 43)
+    np.testing.assert_allclose(O.symbols_strided(w, 5, 4, 1, 1), O.symbols(w, 5, 4), atol=1e-14)
+
+
+def test_strided_single_tap_is_a_subsampling():
+    """One tap: each output samples one input entry, so every singular value is |w| (closed form)."""
+    w = np.zeros((2, 2, 3, 3))
+    w[:, :, 1, 2] = 1.5 * np.eye(2)
+    s = O.lfa_svd_strided(w, 3, 4, 2, 2, compute_uv=False)
+    np.testing.assert_allclose(s, 1.5, atol=1e-14)
+
+
+def test_strided_lifted_vectors_and_backward():
+    c_out, c_in, k, n, m, sh, sw = 3, 2, 3, 3, 4, 2, 2
+    w = rand_w(c_out, c_in, k, k, 44)
+    A = O.dense_operator_strided(w, n, m, sh, sw)
+    s, U, V = O.lfa_svd_strided(w, n, m, sh, sw)
+    for f in (0, 5, 7):
+        j, l = divmod(f, m)
+        uh, vh = O.lift_strided(U[f], V[f], j, l, n, m, sh, sw)
+        for q in range(s.shape[1]):
+            np.testing.assert_allclose(A @ vh[q].ravel(), s[f, q] * uh[q].ravel(), atol=1e-12)
+            assert abs(np.linalg.norm(vh[q]) - 1) < 1e-12
+    g = W.upstream_gradient(s.shape, seed=45).astype(np.float64)
+
+    def L(wv):
+        return float(np.sum(g * O.lfa_svd_strided(wv, n, m, sh, sw, compute_uv=False)))
+
+    dW = O.lfa_backward_strided(w, n, m, sh, sw, g, U, V)
+    h = 1e-6
+    fd = np.zeros_like(w)
+    for idx in np.ndindex(w.shape):
+        wp = w.copy(); wp[idx] += h
+        wm = w.copy(); wm[idx] -= h
+        fd[idx] = (L(wp) - L(wm)) / (2 * h)
+    np.testing.assert_allclose(dW, fd, rtol=1e-6, atol=1e-8)
