@@ -54,7 +54,7 @@ def nominal_svd_flops(M: int, N: int, vectors: bool) -> float:
 
 def layer_flops(l: W.Layer, vectors: bool) -> float:
     """Nominal flops of one forward over a layer: assembly + SVD per half-grid symbol."""
-    M, N = max(l.c_out, l.c_in), min(l.c_out, l.c_in)
+    M, N = max(l.c_out, l.cols), min(l.c_out, l.cols)
     F_h = (l.n * l.m + (1 + (l.n % 2 == 0)) * (1 + (l.m % 2 == 0))) // 2
     return F_h * (4.0 * l.c_out * l.c_in * l.kh * l.kw + nominal_svd_flops(M, N, vectors))
 
@@ -65,8 +65,8 @@ def executed_flops(layers, info, vectors: bool) -> float:
     updates two columns of X (M rows) and, with vectors, of W (N rows) at 24 flops per row.
     Per-layer sizes are averaged over symbols (exact for a single layer)."""
     syms = sum((l.F + (1 + (l.n % 2 == 0)) * (1 + (l.m % 2 == 0))) // 2 for l in layers)
-    M = sum(max(l.c_out, l.c_in) * l.F for l in layers) / max(1, sum(l.F for l in layers))
-    N = sum(min(l.c_out, l.c_in) * l.F for l in layers) / max(1, sum(l.F for l in layers))
+    M = sum(max(l.c_out, l.cols) * l.F for l in layers) / max(1, sum(l.F for l in layers))
+    N = sum(min(l.c_out, l.cols) * l.F for l in layers) / max(1, sum(l.F for l in layers))
     pairs_per_sweep = N * (N - 1) / 2 + (N / 2 if int(N) % 2 else 0)
     dots = info["sweeps"] * pairs_per_sweep * 16.0 * M
     rots = info["rotations"] * 24.0 * (M + (N if vectors else 0))
@@ -170,15 +170,36 @@ def oracle_sample_step(w, lay: W.Layer, freqs, g_seed: int, vectors: bool = True
     sampled frequencies, regulariser gradient, their dL/dw contribution, lifted vectors
     (values only: symbols + SVD values)."""
     import oracle as O
+    st = (lay.sh, lay.sw) != (1, 1)
     if not vectors:
-        return O.lfa_svd(w, lay.n, lay.m, compute_uv=False, freqs=freqs), None, None, None
-    s, U, V = O.lfa_svd(w, lay.n, lay.m, compute_uv=True, freqs=freqs)
+        return oracle_values(w, lay, freqs), None, None, None
+    if st:
+        s, U, V = O.lfa_svd_strided(w, lay.n, lay.m, lay.sh, lay.sw, lay.pad_h, lay.pad_w, freqs=freqs)
+    else:
+        s, U, V = O.lfa_svd(w, lay.n, lay.m, compute_uv=True, freqs=freqs)
     g = O.regulariser_grad_sigma(s, LAM)
-    dw = O.lfa_backward(w, lay.n, lay.m, g, U, V, freqs=freqs)
     f0 = int(freqs[0])
     j, l = divmod(f0, lay.m)
-    uh, vh = O.lift(U[0], V[0], j, l, lay.n, lay.m)
+    if st:
+        dw = O.lfa_backward_strided(w, lay.n, lay.m, lay.sh, lay.sw, g, U, V, lay.pad_h, lay.pad_w, freqs=freqs)
+        uh, vh = O.lift_strided(U[0], V[0], j, l, lay.n, lay.m, lay.sh, lay.sw)
+    else:
+        dw = O.lfa_backward(w, lay.n, lay.m, g, U, V, freqs=freqs)
+        uh, vh = O.lift(U[0], V[0], j, l, lay.n, lay.m)
     return s, dw, uh, vh
+
+
+def oracle_values(w, lay: W.Layer, freqs):
+    """FP64 oracle singular values of the sampled frequencies (any stride)."""
+    import oracle as O
+    if (lay.sh, lay.sw) != (1, 1):
+        return O.lfa_svd_strided(w, lay.n, lay.m, lay.sh, lay.sw, lay.pad_h, lay.pad_w, compute_uv=False,
+                                 freqs=freqs)
+    return O.lfa_svd(w, lay.n, lay.m, compute_uv=False, freqs=freqs)
+
+
+def layer_name(l: W.Layer) -> str:
+    return f"{l.c_out}x{l.c_in}x{l.kh}x{l.kw}@{l.n}x{l.m}" + (f"/s{l.sh}x{l.sw}" if (l.sh, l.sw) != (1, 1) else "")
 
 
 def run_oracle(lay: W.Layer, seconds: float, nfreq: int, steps: int | None = None, vectors: bool = True):
@@ -231,7 +252,7 @@ def run_lfa(args, rank: int, world: int, local_rank: int):
     vectors = not (args.values_only or args.workload in VALUES_ONLY)
     # each rank gets its own seeded weights (independent units)
     ws = [torch.from_numpy(W.weights(l, seed=rank_seed(l, rank))).to(dev) for l in layers]
-    specs = [(l.c_out, l.c_in, l.kh, l.kw, l.n, l.m, l.pad_h, l.pad_w) for l in layers]
+    specs = [l.desc() for l in layers]
     plan = LfaPlan(specs, vectors=vectors, tune_cache=args.tune_cache)
     sig, U, V = plan.alloc(dev)
     stream = torch.cuda.current_stream(dev)
@@ -247,7 +268,7 @@ def run_lfa(args, rank: int, world: int, local_rank: int):
         f_exp = 1 if l0.F > 1 else 0
         cnt = l0.r
         uh = torch.empty((cnt, l0.c_out, l0.n, l0.m), dtype=torch.complex64, device=dev)
-        vh = torch.empty((cnt, l0.c_in, l0.n, l0.m), dtype=torch.complex64, device=dev)
+        vh = torch.empty((cnt, l0.c_in, l0.sh * l0.n, l0.sw * l0.m), dtype=torch.complex64, device=dev)
         u_ptrs = [u.data_ptr() for u in U]
         v_ptrs = [v.data_ptr() for v in V]
         ds_ptrs = [d.data_ptr() for d in dsig]
@@ -380,7 +401,7 @@ def run_lfa(args, rank: int, world: int, local_rank: int):
         "data": "synthetic (seeded He-normal weights; the paper's weights are unstated)",
         "config": {
             "workload": args.workload,
-            "layers": [f"{l.c_out}x{l.c_in}x{l.kh}x{l.kw}@{l.n}x{l.m}" for l in layers],
+            "layers": [layer_name(l) for l in layers],
             "outputs": "values+vectors (U, V per half-grid frequency)" if vectors else "values only",
             "step": ("fwd(assembly+Jacobi, graph) + regulariser dL/dsigma + bwd dL/dw + lift r vector pairs"
                      if vectors else "fwd(assembly+Jacobi, all layers in one graph-replayed launch per variant)"),
@@ -418,11 +439,9 @@ def run_lfa(args, rank: int, world: int, local_rank: int):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = run_oracle(layers[0], args.cpu_seconds, args.cpu_freqs, vectors=vectors)
         # the sampled oracle frequencies also give an accuracy check of this run's sigma
-        import oracle as O
         rng = np.random.default_rng(5)
         fr = np.sort(rng.choice(layers[0].F, min(64, layers[0].F), replace=False))
-        s_ref = O.lfa_svd(W.weights(layers[0], seed=layers[0].seed), layers[0].n, layers[0].m,
-                          compute_uv=False, freqs=fr)
+        s_ref = oracle_values(W.weights(layers[0], seed=layers[0].seed), layers[0], fr)
         s_gpu = sig[0].cpu().numpy()[fr]
         cb["sigma_err_vs_oracle_rel_sigma_max"] = float(np.max(np.abs(s_gpu - s_ref)) / s_ref.max())
         cb.pop("step_s", None)
@@ -470,7 +489,7 @@ def run_reference(args):
         "dtype": "f64",
         "data": "synthetic (seeded He-normal weights)",
         "config": {"workload": args.workload,
-                   "layers": [f"{l.c_out}x{l.c_in}x{l.kh}x{l.kw}@{l.n}x{l.m}" for l in layers],
+                   "layers": [layer_name(l) for l in layers],
                    "sample": sample},
         "cpu_baseline": {"value": value, "unit": "singular values/s", "cores": round(cpu / wall, 2),
                          "cores_available": os.cpu_count(), "kind": "oracle", "sample": sample},

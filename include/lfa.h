@@ -65,12 +65,27 @@ typedef enum lfa_status {
   LFA_ERR_TIMEOUT = 7        /* reserved: a bounded device wait ran out */
 } lfa_status_t;
 
-/* One stride-1 periodic convolution layer (Sec. III "Convolutional Mappings"):
- * weights [c_out][c_in][kh][kw] on an n x m torus, tap origin (pad_h, pad_w),
- * -1 = floor(k/2). Limits: 1 <= c_out, c_in <= 512; 1 <= kh, kw <= 15;
- * 1 <= n, m <= 65536; n*m <= 2^31 - 1; 0 <= pad < k or -1. */
+/* One periodic convolution layer (Sec. III "Convolutional Mappings"):
+ * weights [c_out][c_in][kh][kw], tap origin (pad_h, pad_w), -1 = floor(k/2).
+ *
+ * Stride 1 (stride_h = stride_w = 0 or 1): the layer maps an n x m torus to itself and
+ * its symbol A_k is c_out x c_in.
+ *
+ * Stride (s_h, s_w): the output is (A f)(o, x) = sum_{i,a,b} w[o,i,a,b] f(i, s x + y_ab) on
+ * the coarse n x m torus and the input lives on the fine (s_h n) x (s_w m) torus. Viewed as
+ * a crystal (Sec. III "Introduction to Lattices and Crystals") the input has s_h s_w points
+ * per coarse cell, the polyphase components u = (u_h, u_w) in [0, s_h) x [0, s_w), and the
+ * symbol is the c_out x (c_in s_h s_w) matrix
+ *   A_k[o][(i, u)] = sum_{taps with y_ab = s q + u} w[o,i,a,b] exp(2 pi i <k, q>),
+ * q = floor(y_ab / s) componentwise, column (i, u_h, u_w) at i s_h s_w + u_h s_w + u_w.
+ * Everywhere below "c_in" of a symbol, of V and of v_hat then means c_in s_h s_w; the
+ * weights keep c_in.
+ *
+ * Limits: 1 <= c_out <= 512; 1 <= c_in * s_h * s_w <= 512; 1 <= kh, kw <= 15;
+ * 1 <= s_h, s_w <= 8; 1 <= n, m <= 65536; n*m <= 2^31 - 1; 0 <= pad < k or -1. */
 typedef struct lfa_layer_desc {
   int32_t c_out, c_in, kh, kw, n, m, pad_h, pad_w;
+  int32_t stride_h, stride_w;   /* 0 or 1: stride 1 */
 } lfa_layer_desc_t;
 
 /* Plan flags. */
@@ -84,7 +99,8 @@ typedef struct lfa_layer_desc {
 /* Options (nullable pointer: defaults). */
 typedef struct lfa_options {
   float tol;            /* one-sided Jacobi threshold: a pair (p, q) is rotated while
-                           |x_p^H x_q| > tol * ||x_p|| ||x_q||. <= 0: default 2^-22 */
+                           |x_p^H x_q| > tol * ||x_p|| ||x_q||. <= 0: default
+                           max(2^-22, 4 sqrt(M) 2^-24), M = max(c_out, c_in) */
   int32_t max_sweeps;   /* sweep cap per symbol; <= 0: default 30 */
   int32_t variant;      /* -1: built-in / autotuned choice; >= 0 forces a kernel variant
                            (see lfa_variant_name) for every layer it can run */
@@ -147,6 +163,8 @@ lfa_status_t lfa_symbols(lfa_plan_t plan, int32_t layer, const float* w, float* 
  * where U_f = U[h] for a half-grid frequency f (h its position in the half grid) and
  * U_f = conj(U[h(fc)]) otherwise. U, V: the layer's lfa_svd outputs. u_hat is complex64
  * [count][c_out][n][m], v_hat complex64 [count][c_in][n][m]; either may be NULL.
+ * Strided layer: v_hat is complex64 [count][c_in][s_h n][s_w m] on the fine torus, with
+ *   v_hat[q - first][i][s_h x1 + u_h][s_w x2 + u_w] = V_f[(i, u)][s] exp(2 pi i (j x1/n + l x2/m)) / sqrt(n m).
  * Errors: LFA_ERR_INVALID_ARG (range outside [0, n*m*r), plan without LFA_VECTORS). */
 lfa_status_t lfa_expand(lfa_plan_t plan, int32_t layer, const float* U, const float* V,
                         int64_t first, int64_t count, float* u_hat, float* v_hat, void* stream);
@@ -155,6 +173,7 @@ lfa_status_t lfa_expand(lfa_plan_t plan, int32_t layer, const float* U, const fl
  * d(sigma_s) = Re(u_s^* dA_k v_s) and, from the symbol definition,
  * dA_k/dw[o,i,a,b] = exp(2 pi i <k, y_ab>) e_o e_i^T. Summed over frequencies:
  *   dw[o,i,a,b] = sum_k Re( G_k[o,i] exp(-2 pi i <k, y_ab>) ),  G_k = U_k diag(g~_k) V_k^*,
+ * (strided layer: G_k[o,(i,u_ab)] and exp(-2 pi i <k, q_ab>), y_ab = s q_ab + u_ab)
  * over the half grid, with g~_k = g_k + g_{-k} for a conjugate pair and g~_k = g_k for a
  * self-conjugate k (full-grid dsigma), or g~_k = dsigma_half[k] with LFA_HALF_OUTPUT.
  * Symbols are not needed (only U, V, dsigma).

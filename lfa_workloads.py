@@ -26,10 +26,11 @@ import numpy as np
 
 @dataclass(frozen=True)
 class Layer:
-    """One stride-1 periodic convolution: weight [c_out, c_in, kh, kw] on an n x m torus.
+    """One periodic convolution: weight [c_out, c_in, kh, kw], output on an n x m torus.
 
     ``pad_h``/``pad_w`` is the tap origin p: tap (a, b) acts at offset
     (a - pad_h, b - pad_w). -1 means floor(k/2) (the centred stencil).
+    ``sh``/``sw`` is the stride: the input lives on the (sh n) x (sw m) torus.
     """
     c_out: int
     c_in: int
@@ -42,10 +43,21 @@ class Layer:
     seed: int = 0
     pad_h: int = -1
     pad_w: int = -1
+    sh: int = 1
+    sw: int = 1
+
+    @property
+    def cols(self) -> int:
+        """Columns of a symbol: the input channels times the polyphase components per cell."""
+        return self.c_in * self.sh * self.sw
 
     @property
     def r(self) -> int:
-        return min(self.c_out, self.c_in)
+        return min(self.c_out, self.cols)
+
+    def desc(self):
+        """(c_out, c_in, kh, kw, n, m, pad_h, pad_w, stride_h, stride_w)."""
+        return (self.c_out, self.c_in, self.kh, self.kw, self.n, self.m, self.pad_h, self.pad_w, self.sh, self.sw)
 
     @property
     def F(self) -> int:
@@ -92,6 +104,14 @@ def _resnet18_body() -> List[Layer]:
             for i, (ci, co, n) in enumerate(spec)]
 
 
+def _resnet18_strided() -> List[Layer]:
+    # the stride-2 layers of a ResNet-18 whose symbols have at most 512 columns: the 7x7 stem on a
+    # 224 input (112 output) and the first 3x3 conv and 1x1 shortcut of stages 2 and 3
+    spec = [(3, 64, 7, 112), (64, 128, 3, 28), (64, 128, 1, 28), (128, 256, 3, 14), (128, 256, 1, 14)]
+    return [Layer(c_out=co, c_in=ci, kh=k, kw=k, n=n, m=n, init="normal", gain=2.0, seed=500 + i, sh=2, sw=2)
+            for i, (ci, co, k, n) in enumerate(spec)]
+
+
 # Named workloads. Sizes are the paper-shaped synthetic stand-ins.
 WORKLOADS = {
     # single 4->4 3x3 conv on 8x8: 256 singular values; the dense 256x256 operator is the cross-check
@@ -107,6 +127,8 @@ WORKLOADS = {
     "conv512_k3_n64": [Layer(512, 512, 3, 3, 64, 64, "uniform", 0.0, 51)],
     # stem: 3->64 7x7 on 224x224 (tall 64x3 symbols)
     "stem3to64_k7_n224": [Layer(64, 3, 7, 7, 224, 224, "uniform", 0.0, 52)],
+    # stride-2 layers (crystals with 4 polyphase components per coarse cell)
+    "resnet18_strided": _resnet18_strided(),
     # the paper's runtime shape: 16->16 3x3 (Table II uses n = 256 ... 16384)
     "paper_c16_k3_n256": [Layer(16, 16, 3, 3, 256, 256, "normal", 2.0, 6)],
 }

@@ -388,8 +388,10 @@ def lfa_svd_strided(w, n: int, m: int, s_h: int, s_w: int, pad_h: int = -1, pad_
     return sv, U, np.conj(np.swapaxes(Vh, 1, 2))
 
 
-def lfa_backward_strided(w, n: int, m: int, s_h: int, s_w: int, g, U, V, pad_h: int = -1, pad_w: int = -1):
-    """dL/dw for the strided operator: dW[o,i,a,b] = sum_k Re(sum_s g conj(U[o,s]) V[(i,u_ab),s] exp(2 pi i <k,q_ab>))."""
+def lfa_backward_strided(w, n: int, m: int, s_h: int, s_w: int, g, U, V, pad_h: int = -1, pad_w: int = -1,
+                         freqs=None):
+    """dL/dw for the strided operator: dW[o,i,a,b] = sum_k Re(sum_s g conj(U[o,s]) V[(i,u_ab),s] exp(2 pi i <k,q_ab>)),
+    the sum over all n m frequencies, or over ``freqs`` (then g, U, V hold those rows only)."""
     w = np.asarray(w, dtype=np.float64)
     c_out, c_in, kh, kw = w.shape
     ph, pw = origin(kh, kw, pad_h, pad_w)
@@ -401,6 +403,8 @@ def lfa_backward_strided(w, n: int, m: int, s_h: int, s_w: int, g, U, V, pad_h: 
             qh, uh = divmod(a - ph, s_h)
             qw, uw = divmod(b - pw, s_w)
             phase = _phase(n, m, qh, qw).reshape(n * m)
+            if freqs is not None:
+                phase = phase[np.asarray(freqs)]
             cols = np.arange(c_in) * S + uh * s_w + uw
             dW[:, :, a, b] = np.real(np.einsum("f,foi->oi", phase, H[:, :, cols]))
     return dW

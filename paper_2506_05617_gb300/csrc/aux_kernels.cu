@@ -1,4 +1,5 @@
-// Auxiliary kernels of the LFA SVD library (arXiv 2506.05617, Sec. III):
+// Auxiliary kernels of the LFA SVD library (arXiv 2506.05617, Sec. III; strided layers as
+// crystals):
 //  * symbol assembly into memory (the plain path and lfa_symbols),
 //  * lifting of symbol singular vectors to global singular vectors,
 //  * the backward pass dL/dw,
@@ -17,10 +18,10 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 }
 
 // ----------------------------------------------------------------------------- symbols
-// A_k[o][i] = sum_{a,b} w[o,i,a,b] T_n[j(a-p_h) mod n] T_m[l(b-p_w) mod m] for the
-// half-grid frequencies (symbol definition, Sec. III). One CTA per frequency; the
-// kh x kw phase grid is built once in shared memory; threads stride over (o, i),
-// reading the contiguous kh*kw taps of one (o, i).
+// A_k[o][i] = sum_{a,b} w[o,i,a,b] exp(2 pi i <k, q_ab>) for the half-grid frequencies (symbol
+// definition, Sec. III; for a stride, column i = (ci, u) sums the taps congruent to u). One CTA
+// per frequency; the kh x kw phase grid is built once in shared memory; threads stride over
+// the symbol's (o, i) entries.
 __global__ void __launch_bounds__(256) symbols_kernel(LayerArgs La, float2* out) {
   __shared__ float2 phs[kMaxTaps];
   const int h = blockIdx.x;
@@ -29,20 +30,14 @@ __global__ void __launch_bounds__(256) symbols_kernel(LayerArgs La, float2* out)
   const int kk = La.kh * La.kw;
   for (int t = threadIdx.x; t < kk; t += blockDim.x) {
     const int a = t / La.kw, b = t - a * La.kw;
-    phs[t] = cmul(La.tw_n[mod_pos(j * (a - La.ph), La.n)], La.tw_m[mod_pos(l * (b - La.pw), La.m)]);
+    phs[t] = tap_phase(La, j, l, a, b);
   }
   __syncthreads();
   const int CC = La.c_out * La.c_in;
   float2* o = out + (size_t)h * CC;
   for (int e = threadIdx.x; e < CC; e += blockDim.x) {
-    const float* wp = La.w + (size_t)e * kk;
-    float re = 0.f, im = 0.f;
-    for (int t = 0; t < kk; ++t) {
-      const float wv = __ldg(wp + t);
-      re = fmaf(wv, phs[t].x, re);
-      im = fmaf(wv, phs[t].y, im);
-    }
-    o[e] = make_float2(re, im);
+    const int oo = e / La.c_in, i = e - oo * La.c_in;
+    o[e] = symbol_entry(La, oo, i, phs);
   }
 }
 
@@ -55,8 +50,10 @@ cudaError_t launch_symbols(const LayerArgs& La, float2* out, cudaStream_t s) {
 // ----------------------------------------------------------------------------- expansion
 // u_hat[q][c][x1][x2] = U_f[c][s] exp(2 pi i (j x1/n + l x2/m)) / sqrt(nm), q = f*r + s
 // (U^_k = F_k U_k, Sec. III). U_f = U[h] on the half grid, conj(U[h(fc)]) otherwise.
-// Grid (element chunk, vector q); threads stride over the chunk's c*n*m outputs (x2 fastest:
-// coalesced writes).
+// For a stride, v_hat lives on the fine torus: v_hat[q][ci][sh x1 + uh][sw x2 + uw] takes
+// row (ci, uh, uw) of V_f with the coarse mode of (x1, x2).
+// Grid (element chunk, vector q); threads stride over the chunk's outputs (the last grid
+// coordinate fastest: coalesced writes).
 __device__ int half_index(const int32_t* half, int F_h, int f) {
   int lo = 0, hi = F_h - 1;
   while (lo < hi) {
@@ -80,17 +77,22 @@ __global__ void __launch_bounds__(256) expand_kernel(LayerArgs La, const float2*
   for (int pass = 0; pass < 2; ++pass) {
     const float2* Src = pass == 0 ? U : V;
     float2* dst = pass == 0 ? u_hat : v_hat;
-    const int C = pass == 0 ? La.c_out : La.c_in;
+    const int C = pass == 0 ? La.c_out : La.c_in;               // rows of the factor
+    const int sh = pass == 0 ? 1 : La.sh, sw = pass == 0 ? 1 : La.sw;
     if (dst == nullptr || Src == nullptr) continue;
+    const int G2 = La.m * sw;                                     // output grid sh n x sw m
+    const int64_t G = (int64_t)La.n * sh * G2;
     const float2* col = Src + (size_t)h * C * r + s;
     float2* d = dst + (size_t)blockIdx.y * C * nm;
-    const int64_t total = (int64_t)C * nm;
+    const int64_t total = (int64_t)C * nm;                        // = (C / (sh sw)) * G
     const int64_t per = (total + gridDim.x - 1) / gridDim.x;
     const int64_t e0 = (int64_t)blockIdx.x * per, e1 = e0 + per < total ? e0 + per : total;
     for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      const int c = (int)(e / nm), x = (int)(e - (int64_t)c * nm);
-      const int x1 = x / La.m, x2 = x - x1 * La.m;
-      float2 u = __ldg(col + (size_t)c * r);
+      const int c = (int)(e / G);
+      const int64_t z = e - (int64_t)c * G;
+      const int z1 = (int)(z / G2), z2 = (int)(z - (int64_t)z1 * G2);
+      const int x1 = z1 / sh, uh = z1 - x1 * sh, x2 = z2 / sw, uw = z2 - x2 * sw;
+      float2 u = __ldg(col + (size_t)((c * sh + uh) * sw + uw) * r);
       if (conj) u.y = -u.y;
       const float2 ph = cmul(La.tw_n[(int)(((int64_t)j * x1) % La.n)],
                              La.tw_m[(int)(((int64_t)l * x2) % La.m)]);
@@ -182,19 +184,24 @@ __global__ void __launch_bounds__(256) backward_g_kernel(LayerArgs La, const flo
   }
 }
 
-// Stage 2: partial[c][o][i][a][b] = sum_{h in chunk c} Re(G_h[o,i] exp(-2 pi i <k_h, y_ab>)),
-// the phase split into its row factor (per thread) and column factor (per tap). One thread per
-// (o, i, a) keeps the kw column taps in registers; the chunk's frequencies are summed in a
-// fixed order (deterministic).
+// Stage 2: partial[c][o][i][a][b] = sum_{h in chunk c} Re(G_h[o,(i,u_ab)] exp(-2 pi i <k_h, q_ab>)),
+// the phase split into its row factor (per thread) and column factor (per tap); at stride 1
+// (i, u_ab) = i and q_ab = y_ab. One thread per (o, i, a) keeps the kw column taps in registers;
+// the chunk's frequencies are summed in a fixed order (deterministic).
 template <int KW>
 __global__ void __launch_bounds__(128) backward_dw_kernel(LayerArgs La, const float2* G, int g_begin,
                                                           int chunk, int c_begin, float* partial) {
-  const int CC = La.c_out * La.c_in;
+  const int CW = La.c_out * La.c_w;     // weight (o, i) pairs
+  const int CC = La.c_out * La.c_in;    // symbol entries per G_h
   const int kh = La.kh, kw = La.kw;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int c = c_begin + blockIdx.y;
-  if (tid >= CC * kh) return;
+  if (tid >= CW * kh) return;
   const int e = tid / kh, a = tid - e * kh;
+  const int o = e / La.c_w, ci = e - o * La.c_w;
+  const int sh = La.sh, sw = La.sw;
+  const int qa = floor_div(a - La.ph, sh), uh = (a - La.ph) - qa * sh;
+  const int gcol = o * La.c_in + (ci * sh + uh) * sw;      // + u_w of the tap's column
   float acc[KW];
 #pragma unroll
   for (int b = 0; b < KW; ++b) acc[b] = 0.f;
@@ -202,19 +209,32 @@ __global__ void __launch_bounds__(128) backward_dw_kernel(LayerArgs La, const fl
   for (int h = h0; h < h1; ++h) {
     const int f = La.half[h];
     const int j = f / La.m, l = f - j * La.m;
-    const float2 g = G[(size_t)(h - g_begin) * CC + e];
-    const float2 pa = La.tw_n[mod_pos(j * (a - La.ph), La.n)];
-    // G * conj(pa)
-    const float2 ga = make_float2(g.x * pa.x + g.y * pa.y, g.y * pa.x - g.x * pa.y);
+    const float2* Gh = G + (size_t)(h - g_begin) * CC + gcol;
+    const float2 pa = La.tw_n[mod_pos(j * qa, La.n)];
+    if (sw == 1) {
+      const float2 g = Gh[0];
+      const float2 ga = make_float2(g.x * pa.x + g.y * pa.y, g.y * pa.x - g.x * pa.y);   // G conj(pa)
 #pragma unroll
-    for (int b = 0; b < KW; ++b) {
-      if (b < kw) {
-        const float2 pb = La.tw_m[mod_pos(l * (b - La.pw), La.m)];
-        acc[b] = fmaf(ga.x, pb.x, fmaf(ga.y, pb.y, acc[b]));   // Re(ga * conj(pb))
+      for (int b = 0; b < KW; ++b) {
+        if (b < kw) {
+          const float2 pb = La.tw_m[mod_pos(l * (b - La.pw), La.m)];
+          acc[b] = fmaf(ga.x, pb.x, fmaf(ga.y, pb.y, acc[b]));   // Re(ga conj(pb))
+        }
+      }
+    } else {
+#pragma unroll
+      for (int b = 0; b < KW; ++b) {
+        if (b < kw) {
+          const int qb = floor_div(b - La.pw, sw), uw = (b - La.pw) - qb * sw;
+          const float2 g = Gh[uw];
+          const float2 ga = make_float2(g.x * pa.x + g.y * pa.y, g.y * pa.x - g.x * pa.y);
+          const float2 pb = La.tw_m[mod_pos(l * qb, La.m)];
+          acc[b] = fmaf(ga.x, pb.x, fmaf(ga.y, pb.y, acc[b]));
+        }
       }
     }
   }
-  float* p = partial + ((size_t)c * CC + e) * (kh * kw) + (size_t)a * kw;
+  float* p = partial + ((size_t)c * CW + e) * (kh * kw) + (size_t)a * kw;
 #pragma unroll
   for (int b = 0; b < KW; ++b)
     if (b < kw) p[b] = acc[b];
@@ -236,7 +256,7 @@ cudaError_t launch_backward(const LayerArgs& La, const float* dsigma, int half_o
                             int chunks, float* dw, cudaStream_t s, int* nkernels) {
   *nkernels = 0;
   if (La.F_h <= 0) return cudaSuccess;
-  const int CC = La.c_out * La.c_in;
+  const int CW = La.c_out * La.c_w;
   const int chunk = (La.F_h + chunks - 1) / chunks;
   chunks = (La.F_h + chunk - 1) / chunk;
   int per_block = (int)(g_cap / chunk) < 1 ? 1 : (int)(g_cap / chunk);
@@ -253,7 +273,7 @@ cudaError_t launch_backward(const LayerArgs& La, const float* dsigma, int half_o
     ++*nkernels;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    dim3 gd((CC * La.kh + 127) / 128, c1 - c0);
+    dim3 gd((CW * La.kh + 127) / 128, c1 - c0);
     if (La.kw <= 3) backward_dw_kernel<3><<<gd, 128, 0, s>>>(La, G, h0, chunk, c0, partial);
     else if (La.kw <= 7) backward_dw_kernel<7><<<gd, 128, 0, s>>>(La, G, h0, chunk, c0, partial);
     else backward_dw_kernel<15><<<gd, 128, 0, s>>>(La, G, h0, chunk, c0, partial);
@@ -261,7 +281,7 @@ cudaError_t launch_backward(const LayerArgs& La, const float* dsigma, int half_o
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  const int64_t total = (int64_t)CC * La.kh * La.kw;
+  const int64_t total = (int64_t)CW * La.kh * La.kw;
   backward_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(partial, chunks, total, dw);
   ++*nkernels;
   return cudaGetLastError();

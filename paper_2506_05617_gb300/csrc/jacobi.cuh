@@ -123,25 +123,14 @@ __device__ __forceinline__ int pi_pos(int p) {
 // Entry X[row][col] of the symbol (phases in `phs`), or 0 outside M x N.
 template <bool FUSED>
 __device__ __forceinline__ float2 x_entry(const LayerArgs& La, int h, int row, int col,
-                                          const float2* phs, int kk) {
+                                          const float2* phs) {
   if (row >= La.M || col >= La.N) return make_float2(0.f, 0.f);
   const int o = La.wide ? col : row;
   const int i = La.wide ? row : col;
-  float re = 0.f, im = 0.f;
-  if constexpr (FUSED) {
-    const float* wp = La.w + ((size_t)o * La.c_in + i) * kk;
-    for (int t = 0; t < kk; ++t) {
-      const float wv = __ldg(wp + t);
-      const float2 p = phs[t];
-      re = fmaf(wv, p.x, re);
-      im = fmaf(wv, p.y, im);
-    }
-  } else {
-    const float2 v = La.symbols[((size_t)h * La.c_out + o) * La.c_in + i];
-    re = v.x;
-    im = v.y;
-  }
-  return make_float2(re, La.wide ? -im : im);
+  float2 v;
+  if constexpr (FUSED) v = symbol_entry(La, o, i, phs);
+  else v = La.symbols[((size_t)h * La.c_out + o) * La.c_in + i];
+  return make_float2(v.x, La.wide ? -v.y : v.y);
 }
 
 // A column of X (and of W) held by one lane as real/imaginary planes over row pairs: pair k
@@ -395,16 +384,12 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
     const int ll = f - jj * La.m;
     const int N = La.N, M = La.M;
 
-    // ---------------------------------------------------------------- phases exp(2 pi i <k, y_ab>)
+    // ---------------------------------------------------------------- phases exp(2 pi i <k, q_ab>)
+    // q_ab = floor(y_ab / s): the tap's coarse offset (q = y at stride 1)
     if constexpr (FUSED) {
       for (int t = st; t < kk; t += TC) {
         const int a = t / La.kw, b = t - a * La.kw;
-        int ia = (jj * (a - La.ph)) % La.n;
-        if (ia < 0) ia += La.n;
-        int ib = (ll * (b - La.pw)) % La.m;
-        if (ib < 0) ib += La.m;
-        const float2 p = La.tw_n[ia], q = La.tw_m[ib];
-        phs[t] = make_float2(p.x * q.x - p.y * q.y, p.x * q.y + p.y * q.x);
+        phs[t] = tap_phase(La, jj, ll, a, b);
       }
       unit_sync<C>();
     }
@@ -424,10 +409,10 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
 #pragma unroll
     for (int k = 0; k < C::MH; ++k) {
       const int r0 = lane + L * k, r1 = lane + L * (k + C::MH);
-      const float2 a0 = active ? x_entry<FUSED>(La, h, r0, id0, phs, kk) : make_float2(0.f, 0.f);
-      const float2 a1 = active ? x_entry<FUSED>(La, h, r1, id0, phs, kk) : make_float2(0.f, 0.f);
-      const float2 b0 = active ? x_entry<FUSED>(La, h, r0, id1, phs, kk) : make_float2(0.f, 0.f);
-      const float2 b1 = active ? x_entry<FUSED>(La, h, r1, id1, phs, kk) : make_float2(0.f, 0.f);
+      const float2 a0 = active ? x_entry<FUSED>(La, h, r0, id0, phs) : make_float2(0.f, 0.f);
+      const float2 a1 = active ? x_entry<FUSED>(La, h, r1, id0, phs) : make_float2(0.f, 0.f);
+      const float2 b0 = active ? x_entry<FUSED>(La, h, r0, id1, phs) : make_float2(0.f, 0.f);
+      const float2 b1 = active ? x_entry<FUSED>(La, h, r1, id1, phs) : make_float2(0.f, 0.f);
       c0.xr[k] = make_float2(a0.x, a1.x);
       c0.xi[k] = make_float2(a0.y, a1.y);
       c1.xr[k] = make_float2(b0.x, b1.x);

@@ -221,13 +221,13 @@ namespace {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+bool layer_geometry(const lfa_layer_desc_t& d, LayerArgs& La) {
+  return set_geometry(La, d.c_out, d.c_in, d.kh, d.kw, d.n, d.m, d.pad_h, d.pad_w, d.stride_h, d.stride_w);
+}
+
 lfa_status_t validate_layer(const lfa_layer_desc_t& d) {
-  if (d.c_out < 1 || d.c_in < 1 || d.c_out > 512 || d.c_in > 512) return LFA_ERR_INVALID_ARG;
-  if (d.kh < 1 || d.kw < 1 || d.kh > 15 || d.kw > 15) return LFA_ERR_INVALID_ARG;
-  if (d.n < 1 || d.m < 1 || d.n > 65536 || d.m > 65536) return LFA_ERR_INVALID_ARG;
-  if ((int64_t)d.n * d.m > 0x7fffffffLL) return LFA_ERR_INVALID_ARG;
-  if (d.pad_h < -1 || d.pad_h >= d.kh || d.pad_w < -1 || d.pad_w >= d.kw) return LFA_ERR_INVALID_ARG;
-  return LFA_OK;
+  LayerArgs La;
+  return layer_geometry(d, La) ? LFA_OK : LFA_ERR_INVALID_ARG;
 }
 
 float default_tol(int M) {
@@ -407,13 +407,7 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
     const lfa_layer_desc_t& d = layers[l];
     LayerArgs& La = p->args[l];
     std::memset(&La, 0, sizeof La);
-    La.c_out = d.c_out; La.c_in = d.c_in; La.kh = d.kh; La.kw = d.kw; La.n = d.n; La.m = d.m;
-    La.ph = d.pad_h < 0 ? d.kh / 2 : d.pad_h;
-    La.pw = d.pad_w < 0 ? d.kw / 2 : d.pad_w;
-    La.r = std::min(d.c_out, d.c_in);
-    La.wide = d.c_in > d.c_out ? 1 : 0;
-    La.M = std::max(d.c_out, d.c_in);
-    La.N = La.r;
+    layer_geometry(d, La);   // validated above
     build_half_grid(d.n, d.m, p->half_host[l]);
     La.F_h = (int)p->half_host[l].size();
     const float tol = p->tol_opt > 0.f ? p->tol_opt : default_tol(La.M);
@@ -451,7 +445,7 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
     off_half[l] = bytes; bytes += align256((size_t)La.F_h * 4);
     off_twn[l] = bytes; bytes += align256((size_t)d.n * 8);
     off_twm[l] = bytes; bytes += align256((size_t)d.m * 8);
-    const size_t CC = (size_t)d.c_out * d.c_in;
+    const size_t CC = (size_t)La.c_out * La.c_in;   // symbol entries
     if (p->plain) sym_bytes = std::max(sym_bytes, (size_t)La.F_h * CC * 8);
     if (p->vec) g_need = std::max(g_need, (size_t)La.F_h * CC * 8);
   }
@@ -683,10 +677,11 @@ lfa_status_t lfa_regulariser_grad(lfa_plan_t p, const float* const* sigma, float
   for (int l = 0; l < p->nlayers; ++l)
     if (!sigma[l] || !dsigma[l]) return LFA_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  for (int l = 0; l < p->nlayers; ++l)
+  for (int l = 0; l < p->nlayers; ++l) {
     LFA_CUDA_TRY(launch_regulariser(p->args[l], p->half_output, sigma[l], lam, dsigma[l],
                                     loss ? loss[l] : nullptr, s));
     g_launches += 1;
+  }
   return LFA_OK;
 }
 

@@ -34,8 +34,75 @@ struct LayerArgs {
   int32_t c_out, c_in, kh, kw, n, m, ph, pw;
   int32_t F_h, r, M, N, wide;
   int32_t item_begin;       // first work item of this layer in its launch
+  // Stride (sh, sw) >= 1 and the weights' input channels c_w. The symbol has c_in = c_w sh sw
+  // columns (i, u_h, u_w) -> i sh sw + u_h sw + u_w: the polyphase components of the fine input.
+  int32_t c_w, sh, sw;
   float tol2;               // squared Jacobi threshold
 };
+
+// floor(a / s) for s >= 1: the coarse offset q of a tap y = s q + u, 0 <= u < s.
+__host__ __device__ __forceinline__ int floor_div(int a, int s) { return a >= 0 ? a / s : -((s - 1 - a) / s); }
+
+// Fills the geometry of La from a layer description (stride 0 reads as 1) after checking the
+// limits that every entry point shares; false when one is violated.
+inline bool set_geometry(LayerArgs& La, int c_out, int c_in, int kh, int kw, int n, int m, int pad_h,
+                         int pad_w, int stride_h, int stride_w) {
+  const int sh = stride_h == 0 ? 1 : stride_h, sw = stride_w == 0 ? 1 : stride_w;
+  if (sh < 1 || sw < 1 || sh > 8 || sw > 8) return false;
+  if (c_out < 1 || c_in < 1 || c_out > 512 || c_in > 512 || c_in * sh * sw > 512) return false;
+  if (kh < 1 || kw < 1 || kh > 15 || kw > 15) return false;
+  if (n < 1 || m < 1 || n > 65536 || m > 65536 || (int64_t)n * m > 0x7fffffffLL) return false;
+  if (pad_h < -1 || pad_h >= kh || pad_w < -1 || pad_w >= kw) return false;
+  La.c_out = c_out; La.c_w = c_in; La.sh = sh; La.sw = sw; La.c_in = c_in * sh * sw;
+  La.kh = kh; La.kw = kw; La.n = n; La.m = m;
+  La.ph = pad_h < 0 ? kh / 2 : pad_h;
+  La.pw = pad_w < 0 ? kw / 2 : pad_w;
+  La.r = c_out < La.c_in ? c_out : La.c_in;
+  La.wide = La.c_in > c_out ? 1 : 0;
+  La.M = c_out > La.c_in ? c_out : La.c_in;
+  La.N = La.r;
+  return true;
+}
+
+// exp(2 pi i <k, q_ab>) for the frequency k = (j/n, l/m) and the tap (a, b), q_ab = floor(y_ab / s)
+// its coarse offset (q = y at stride 1); products below 2^31 since j < n <= 65536 and |q| < 15.
+__device__ __forceinline__ float2 tap_phase(const LayerArgs& La, int j, int l, int a, int b) {
+  int ia = (j * floor_div(a - La.ph, La.sh)) % La.n;
+  if (ia < 0) ia += La.n;
+  int ib = (l * floor_div(b - La.pw, La.sw)) % La.m;
+  if (ib < 0) ib += La.m;
+  const float2 p = La.tw_n[ia], q = La.tw_m[ib];
+  return make_float2(p.x * q.x - p.y * q.y, p.x * q.y + p.y * q.x);
+}
+
+// Symbol entry A_k[o][i] from the taps and their phases phs[a kw + b] (symbol definition, Sec. III;
+// for a stride, the taps of column i = (ci, u) are those whose offset is congruent to u).
+__device__ __forceinline__ float2 symbol_entry(const LayerArgs& La, int o, int i, const float2* phs) {
+  const int kk = La.kh * La.kw;
+  float re = 0.f, im = 0.f;
+  if (La.sh == 1 && La.sw == 1) {
+    const float* wp = La.w + ((size_t)o * La.c_w + i) * kk;
+    for (int t = 0; t < kk; ++t) {
+      const float wv = __ldg(wp + t);
+      const float2 p = phs[t];
+      re = fmaf(wv, p.x, re);
+      im = fmaf(wv, p.y, im);
+    }
+  } else {
+    const int S = La.sh * La.sw;
+    const int ci = i / S, u = i - ci * S, uh = u / La.sw, uw = u - uh * La.sw;
+    const float* wp = La.w + ((size_t)o * La.c_w + ci) * kk;
+    for (int a = (uh + La.ph) % La.sh; a < La.kh; a += La.sh)
+      for (int b = (uw + La.pw) % La.sw; b < La.kw; b += La.sw) {
+        const int t = a * La.kw + b;
+        const float wv = __ldg(wp + t);
+        const float2 p = phs[t];
+        re = fmaf(wv, p.x, re);
+        im = fmaf(wv, p.y, im);
+      }
+  }
+  return make_float2(re, im);
+}
 
 // One launch of a Jacobi variant over some layers (a persistent grid pulling items).
 struct JacobiLaunch {

@@ -100,24 +100,14 @@ extern "C" lfa_status_t lfa_svd_backward_noalloc(const lfa_layer_desc_t* layer, 
     return LFA_ERR_INVALID_ARG;
   if (flags & ~(uint32_t)LFA_HALF_OUTPUT) return LFA_ERR_INVALID_ARG;
   const lfa_layer_desc_t& d = *layer;
-  if (d.c_out < 1 || d.c_in < 1 || d.c_out > 512 || d.c_in > 512 || d.kh < 1 || d.kw < 1 || d.kh > 15 ||
-      d.kw > 15 || d.n < 1 || d.m < 1 || d.n > 65536 || d.m > 65536 || (int64_t)d.n * d.m > 0x7fffffffLL ||
-      d.pad_h < -1 || d.pad_h >= d.kh || d.pad_w < -1 || d.pad_w >= d.kw)
-    return LFA_ERR_INVALID_ARG;
-
   LayerArgs La;
+  if (!set_geometry(La, d.c_out, d.c_in, d.kh, d.kw, d.n, d.m, d.pad_h, d.pad_w, d.stride_h, d.stride_w))
+    return LFA_ERR_INVALID_ARG;
   La.w = nullptr;
   La.sigma = nullptr;
   La.U = nullptr;
   La.V = nullptr;
   La.symbols = nullptr;
-  La.c_out = d.c_out; La.c_in = d.c_in; La.kh = d.kh; La.kw = d.kw; La.n = d.n; La.m = d.m;
-  La.ph = d.pad_h < 0 ? d.kh / 2 : d.pad_h;
-  La.pw = d.pad_w < 0 ? d.kw / 2 : d.pad_w;
-  La.r = d.c_out < d.c_in ? d.c_out : d.c_in;
-  La.M = d.c_out > d.c_in ? d.c_out : d.c_in;
-  La.N = La.r;
-  La.wide = d.c_in > d.c_out ? 1 : 0;
   const int s_self = (1 + (d.n % 2 == 0)) * (1 + (d.m % 2 == 0));
   La.F_h = (int)(((int64_t)d.n * d.m + s_self) / 2);
   La.item_begin = 0;
@@ -125,7 +115,7 @@ extern "C" lfa_status_t lfa_svd_backward_noalloc(const lfa_layer_desc_t* layer, 
 
   // scratch layout: half-grid list | twiddles n | twiddles m | partial sums | G workspace.
   // The partial sums get at most half the array; G gets the rest and must hold one chunk.
-  const int64_t CC = (int64_t)d.c_out * d.c_in;
+  const int64_t CC = (int64_t)La.c_out * La.c_in;   // symbol entries (>= weight pairs)
   const int64_t kk = (int64_t)d.kh * d.kw;
   const size_t fixed = align256((size_t)La.F_h * 4) + align256((size_t)d.n * 8) + align256((size_t)d.m * 8);
   if (fixed >= kScratchBytes / 2) return LFA_ERR_UNSUPPORTED;

@@ -53,7 +53,19 @@ EXPORTS = [
 
 class LayerDesc(ctypes.Structure):
     _fields_ = [("c_out", c_int32), ("c_in", c_int32), ("kh", c_int32), ("kw", c_int32),
-                ("n", c_int32), ("m", c_int32), ("pad_h", c_int32), ("pad_w", c_int32)]
+                ("n", c_int32), ("m", c_int32), ("pad_h", c_int32), ("pad_w", c_int32),
+                ("stride_h", c_int32), ("stride_w", c_int32)]
+
+
+def layer_desc(d) -> "LayerDesc":
+    """LayerDesc from a LayerDesc or (c_out, c_in, kh, kw, n, m[, pad_h, pad_w[, stride_h, stride_w]])."""
+    if isinstance(d, LayerDesc):
+        return d
+    d = tuple(int(x) for x in d)
+    if len(d) not in (6, 8, 10):
+        raise ValueError(f"layer description needs 6, 8 or 10 integers, got {len(d)}")
+    d = d + (-1, -1, 1, 1)[len(d) - 6:]
+    return LayerDesc(*d)
 
 
 class Options(ctypes.Structure):
@@ -148,16 +160,9 @@ def _stream(s) -> Optional[int]:
 # ----------------------------------------------------------------------------- entry points
 def lfa_plan(layers: Iterable, flags: int = LFA_VALUES, tol: float = 0.0, max_sweeps: int = 0,
              variant: int = -1, use_graph: int = -1, tune_cache: Optional[str] = None) -> int:
-    """Creates a plan; ``layers`` holds LayerDesc or (c_out, c_in, kh, kw, n, m[, pad_h, pad_w])."""
-    descs = []
-    for d in layers:
-        if isinstance(d, LayerDesc):
-            descs.append(d)
-        else:
-            d = tuple(d)
-            if len(d) == 6:
-                d = d + (-1, -1)
-            descs.append(LayerDesc(*[int(x) for x in d]))
+    """Creates a plan; ``layers`` holds LayerDesc or
+    (c_out, c_in, kh, kw, n, m[, pad_h, pad_w[, stride_h, stride_w]])."""
+    descs = [layer_desc(d) for d in layers]
     arr = (LayerDesc * max(1, len(descs)))(*descs)
     opt = Options(float(tol), int(max_sweeps), int(variant), int(use_graph),
                   tune_cache.encode() if tune_cache else None)
@@ -192,9 +197,7 @@ def lfa_svd_backward(plan: int, dsigma: Sequence[int], U: Sequence[int], V: Sequ
 
 def lfa_svd_backward_noalloc(layer, flags: int, dsigma: int, U: int, V: int, dw: int, stream=None) -> None:
     """Backward of one layer without any device allocation (no plan); see include/lfa.h."""
-    d = tuple(int(x) for x in layer)
-    d = d if len(d) == 8 else d + (-1, -1)
-    desc = LayerDesc(*d)
+    desc = layer_desc(layer)
     _check(lib().lfa_svd_backward_noalloc(ctypes.byref(desc), int(flags), c_void_p(dsigma), c_void_p(U),
                                           c_void_p(V), c_void_p(dw), _stream(stream)), "lfa_svd_backward_noalloc")
 

@@ -15,12 +15,17 @@ from . import lfa as C
 
 
 def _layer_tuple(d):
-    d = tuple(int(x) for x in d)
-    return d if len(d) == 8 else d + (-1, -1)
+    L = C.layer_desc(d)
+    t = tuple(getattr(L, k) for k, _ in L._fields_)
+    return t[:8] + tuple(max(1, v) for v in t[8:])
 
 
 class LfaPlan:
-    """A plan over ``layers``: each (c_out, c_in, kh, kw, n, m[, pad_h, pad_w])."""
+    """A plan over ``layers``: each (c_out, c_in, kh, kw, n, m[, pad_h, pad_w[, stride_h, stride_w]]).
+
+    A strided layer's symbol has c_in * stride_h * stride_w columns (the input's polyphase
+    components); its V has that many rows and its v_hat lives on the (stride_h n) x (stride_w m)
+    input torus."""
 
     def __init__(self, layers: Sequence, vectors: bool = False, half_output: bool = False,
                  plain: bool = False, tol: float = 0.0, max_sweeps: int = 0, variant: int = -1,
@@ -34,18 +39,22 @@ class LfaPlan:
         self.meta = [C.lfa_layer_query(self.handle, i) for i in range(len(self.layers))]
 
     # ------------------------------------------------------------------ shapes
+    def symbol_cols(self, i):
+        c_in, sh, sw = self.layers[i][1], self.layers[i][8], self.layers[i][9]
+        return c_in * sh * sw
+
     def sigma_shape(self, i):
-        c_out, c_in, kh, kw, n, m = self.layers[i][:6]
-        r = min(c_out, c_in)
+        c_out, n, m = self.layers[i][0], self.layers[i][4], self.layers[i][5]
+        r = min(c_out, self.symbol_cols(i))
         return (self.meta[i]["F_h"], r) if self.half_output else (n * m, r)
 
     def u_shape(self, i):
-        c_out, c_in = self.layers[i][:2]
-        return (self.meta[i]["F_h"], c_out, min(c_out, c_in))
+        c_out = self.layers[i][0]
+        return (self.meta[i]["F_h"], c_out, min(c_out, self.symbol_cols(i)))
 
     def v_shape(self, i):
-        c_out, c_in = self.layers[i][:2]
-        return (self.meta[i]["F_h"], c_in, min(c_out, c_in))
+        c_out, ci = self.layers[i][0], self.symbol_cols(i)
+        return (self.meta[i]["F_h"], ci, min(c_out, ci))
 
     def alloc(self, device="cuda"):
         sig = [torch.empty(self.sigma_shape(i), dtype=torch.float32, device=device) for i in range(len(self.layers))]
@@ -98,17 +107,19 @@ class LfaPlan:
         return out
 
     def symbols(self, layer: int, w: torch.Tensor, stream=None):
-        c_out, c_in = self.layers[layer][:2]
-        out = torch.empty((self.meta[layer]["F_h"], c_out, c_in), dtype=torch.complex64, device=w.device)
+        c_out = self.layers[layer][0]
+        out = torch.empty((self.meta[layer]["F_h"], c_out, self.symbol_cols(layer)), dtype=torch.complex64,
+                          device=w.device)
         stream = stream if stream is not None else torch.cuda.current_stream(w.device)
         C.lfa_symbols(self.handle, layer, w.contiguous().data_ptr(), out.data_ptr(), stream)
         return out
 
     def expand(self, layer: int, U, V, first: int, count: int, stream=None):
-        c_out, c_in, kh, kw, n, m = self.layers[layer][:6]
+        c_out, c_in, kh, kw, n, m, _, _, sh, sw = self.layers[layer]
         dev = (U if U is not None else V).device
         u_hat = torch.empty((count, c_out, n, m), dtype=torch.complex64, device=dev) if U is not None else None
-        v_hat = torch.empty((count, c_in, n, m), dtype=torch.complex64, device=dev) if V is not None else None
+        v_hat = torch.empty((count, c_in, sh * n, sw * m), dtype=torch.complex64, device=dev) \
+            if V is not None else None
         stream = stream if stream is not None else torch.cuda.current_stream(dev)
         C.lfa_expand(self.handle, layer, U.data_ptr() if U is not None else 0, V.data_ptr() if V is not None else 0,
                      first, count, u_hat.data_ptr() if u_hat is not None else 0,
@@ -153,9 +164,12 @@ class LfaSvd(torch.autograd.Function):
         return (None, *dw)
 
 
-def svd(weights: Sequence[torch.Tensor], n: int, m: Optional[int] = None, vectors: bool = True, **kw):
-    """Convenience: singular values (and U, V) of each conv layer on an n x m torus."""
+def svd(weights: Sequence[torch.Tensor], n: int, m: Optional[int] = None, vectors: bool = True,
+        stride=1, **kw):
+    """Convenience: singular values (and U, V) of each conv layer with an n x m output torus
+    (stride (s_h, s_w), or one int for both: the input torus is s_h n x s_w m)."""
     m = n if m is None else m
-    plan = LfaPlan([tuple(w.shape) + (n, m) for w in weights], vectors=vectors, **kw)
+    sh, sw = (stride, stride) if isinstance(stride, int) else tuple(stride)
+    plan = LfaPlan([tuple(w.shape) + (n, m, -1, -1, sh, sw) for w in weights], vectors=vectors, **kw)
     sig, U, V = plan.svd(weights)
     return plan, sig, U, V

@@ -69,8 +69,12 @@ def check_sigma(w, n, m, s_gpu, pad=(-1, -1), half=None):
 
 def check_vectors(w, n, m, s_full, U, V, pad=(-1, -1)):
     half = O.half_grid(n, m)
-    S = O.symbols(w, n, m, *pad)[half]
-    s = s_full[half].astype(np.float64)
+    check_factors(O.symbols(w, n, m, *pad)[half], s_full[half], U, V)
+
+
+def check_factors(S, s, U, V):
+    """Singular triplets (s, U, V) of the half-grid symbols S [F_h, c_out, c_in] (see the header)."""
+    s = s.astype(np.float64)
     smax = max(float(np.max(s)), 1e-30)
     U = U.astype(np.complex128)
     V = V.astype(np.complex128)

@@ -88,11 +88,22 @@ def test_status_strings_and_version():
 @pytest.mark.parametrize("bad", [
     (0, 4, 3, 3, 8, 8), (4, 4, 0, 3, 8, 8), (4, 4, 3, 3, 0, 8), (4, 600, 3, 3, 8, 8),
     (4, 4, 3, 3, 8, 8, 3, 1), (4, 4, 16, 3, 8, 8), (4, 4, 3, 3, 8, 8, -2, 0),
+    # strides: at most 8, not negative, and c_in * s_h * s_w symbol columns at most 512
+    (4, 4, 3, 3, 8, 8, -1, -1, 9, 1), (4, 4, 3, 3, 8, 8, -1, -1, 2, -1), (4, 129, 3, 3, 8, 8, -1, -1, 2, 2),
 ])
 def test_plan_rejects_invalid_layers_without_touching_the_gpu(bad):
     with pytest.raises(C.LfaError) as ei:
         C.lfa_plan([bad], C.LFA_VALUES)
     assert ei.value.status == C.LFA_ERR_INVALID_ARG
+
+
+def test_layer_descriptions_accept_6_8_or_10_integers():
+    assert tuple(getattr(C.layer_desc((4, 5, 3, 3, 8, 9)), k) for k, _ in C.LayerDesc._fields_) == \
+        (4, 5, 3, 3, 8, 9, -1, -1, 1, 1)
+    assert C.layer_desc((4, 5, 3, 3, 8, 9, 0, 2)).pad_w == 2
+    assert C.layer_desc((4, 5, 3, 3, 8, 9, -1, -1, 2, 3)).stride_w == 3
+    with pytest.raises(ValueError):
+        C.layer_desc((4, 5, 3, 3, 8, 9, 0))
 
 
 def test_plan_rejects_bad_flags_and_counts():

@@ -26,10 +26,11 @@ def _built():
 
 
 @pytest.mark.parametrize("half_output", [False, True])
-@pytest.mark.parametrize("spec", [(64, 64, 3, 3, 32, 32), (5, 3, 3, 3, 6, 5), (3, 7, 5, 3, 7, 4)])
+@pytest.mark.parametrize("spec", [(64, 64, 3, 3, 32, 32), (5, 3, 3, 3, 6, 5), (3, 7, 5, 3, 7, 4),
+                                  (12, 4, 3, 3, 5, 6, -1, -1, 2, 2)])
 def test_noalloc_backward_matches_planned_backward_twice(spec, half_output):
     from paper_2506_05617_gb300.torch_api import LfaPlan
-    c_out, c_in, kh, kw, n, m = spec
+    c_out, c_in, kh, kw, n, m = spec[:6]
     w = np.random.default_rng(1).standard_normal((c_out, c_in, kh, kw)) / np.sqrt(c_in * kh * kw)
     w = torch.from_numpy(w.astype(np.float32)).cuda()
     plan = LfaPlan([spec], vectors=True, half_output=half_output)
