@@ -126,6 +126,131 @@ cudaError_t launch_expand(const LayerArgs& La, const float2* U, const float2* V,
   return cudaGetLastError();
 }
 
+// ----------------------------------------------------------------------------- completion
+// The X-side factor of a symbol (U for tall, V for wide; [M][N], column s = rank s) holds an
+// exactly zero column where the forward found a negligible singular value (the cluster and
+// rotation-log paths write them so). Its singular vector is any unit vector orthogonal to the
+// other columns: start from the canonical vector e_k whose residual 1 - |row k|^2 (its squared
+// distance from the span of the columns) is largest, which is at least (M - rank) / M, and
+// orthogonalise it twice by classical Gram-Schmidt ("twice is enough"). Zero columns are
+// completed in increasing order. One CTA per symbol; fixed-order sums (deterministic).
+__global__ void __launch_bounds__(256) complete_kernel(float2* X, int M, int N) {
+  __shared__ float res[512];
+  __shared__ float2 v[512];
+  __shared__ float2 cq[512];
+  __shared__ unsigned char zero[512];
+  __shared__ float rbest[8];
+  __shared__ int kbest[8];
+  __shared__ int nzero;
+  float2* P = X + (size_t)blockIdx.x * M * N;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) nzero = 0;
+  __syncthreads();
+  for (int c = tid; c < N; c += blockDim.x) {
+    float q = 0.f;
+    for (int m = 0; m < M; ++m) {
+      const float2 x = P[(size_t)m * N + c];
+      q = fmaf(x.x, x.x, fmaf(x.y, x.y, q));
+    }
+    zero[c] = q == 0.f;
+    if (q == 0.f) atomicAdd(&nzero, 1);
+  }
+  __syncthreads();
+  if (nzero == 0) return;
+  // squared distance of e_k from the span of the columns, one warp per row
+  for (int k = wid; k < M; k += 8) {
+    float q = 0.f;
+    for (int c = lane; c < N; c += 32) {
+      const float2 x = P[(size_t)k * N + c];
+      q = fmaf(x.x, x.x, fmaf(x.y, x.y, q));
+    }
+    for (int off = 16; off > 0; off >>= 1) q += __shfl_xor_sync(0xffffffffu, q, off);
+    if (lane == 0) res[k] = 1.f - q;
+  }
+  __syncthreads();
+  for (int d = 0; d < N; ++d) {
+    if (!zero[d]) continue;                      // uniform: zero[] is shared
+    // k* = argmax res (ties: smallest k)
+    float rb = -1.f;
+    int kb = 0;
+    for (int k = tid; k < M; k += blockDim.x)
+      if (res[k] > rb) { rb = res[k]; kb = k; }
+    for (int off = 16; off > 0; off >>= 1) {
+      const float orb = __shfl_xor_sync(0xffffffffu, rb, off);
+      const int okb = __shfl_xor_sync(0xffffffffu, kb, off);
+      if (orb > rb || (orb == rb && okb < kb)) { rb = orb; kb = okb; }
+    }
+    if (lane == 0) { rbest[wid] = rb; kbest[wid] = kb; }
+    __syncthreads();
+    if (tid == 0) {
+      for (int w = 1; w < 8; ++w)
+        if (rbest[w] > rbest[0] || (rbest[w] == rbest[0] && kbest[w] < kbest[0])) {
+          rbest[0] = rbest[w];
+          kbest[0] = kbest[w];
+        }
+    }
+    __syncthreads();
+    const int ks = kbest[0];
+    for (int m = tid; m < M; m += blockDim.x) v[m] = make_float2(m == ks ? 1.f : 0.f, 0.f);
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+      // c = P^* v (one thread per column: coalesced rows)
+      for (int c = tid; c < N; c += blockDim.x) {
+        float cr = 0.f, ci = 0.f;
+        for (int m = 0; m < M; ++m) {
+          const float2 x = P[(size_t)m * N + c], y = v[m];
+          cr = fmaf(x.x, y.x, fmaf(x.y, y.y, cr));       // Re(conj(x) y)
+          ci = fmaf(x.x, y.y, fmaf(-x.y, y.x, ci));      // Im(conj(x) y)
+        }
+        cq[c] = make_float2(cr, ci);
+      }
+      __syncthreads();
+      // v -= P c (one warp per row)
+      for (int m = wid; m < M; m += 8) {
+        float sr = 0.f, si = 0.f;
+        for (int c = lane; c < N; c += 32) {
+          const float2 x = P[(size_t)m * N + c], y = cq[c];
+          sr = fmaf(x.x, y.x, fmaf(-x.y, y.y, sr));
+          si = fmaf(x.x, y.y, fmaf(x.y, y.x, si));
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+          sr += __shfl_xor_sync(0xffffffffu, sr, off);
+          si += __shfl_xor_sync(0xffffffffu, si, off);
+        }
+        if (lane == 0) v[m] = make_float2(v[m].x - sr, v[m].y - si);
+      }
+      __syncthreads();
+    }
+    // normalise, write column d, update the residuals
+    float q = 0.f;
+    for (int m = tid; m < M; m += blockDim.x) q = fmaf(v[m].x, v[m].x, fmaf(v[m].y, v[m].y, q));
+    for (int off = 16; off > 0; off >>= 1) q += __shfl_xor_sync(0xffffffffu, q, off);
+    if (lane == 0) rbest[wid] = q;
+    __syncthreads();
+    float nrm = 0.f;
+    for (int w = 0; w < 8; ++w) nrm += rbest[w];
+    const float inv = nrm > 0.f ? rsqrtf(nrm) : 0.f;
+    for (int m = tid; m < M; m += blockDim.x) {
+      const float2 u = make_float2(v[m].x * inv, v[m].y * inv);
+      P[(size_t)m * N + d] = u;
+      res[m] -= u.x * u.x + u.y * u.y;
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_complete(const LayerArgs& La, float2* X, int symbols, cudaStream_t s) {
+  if (symbols <= 0) return cudaSuccess;
+  if (La.M > 512 || La.N > 512) return cudaErrorInvalidValue;
+  for (int h0 = 0; h0 < symbols; h0 += 65535) {
+    const int cnt = symbols - h0 < 65535 ? symbols - h0 : 65535;
+    complete_kernel<<<cnt, 256, 0, s>>>(X + (size_t)h0 * La.M * La.N, La.M, La.N);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 // ----------------------------------------------------------------------------- backward
 // Stage 1: G_h = U_h diag(g~_h) V_h^* (c_out x c_in complex) for every half-grid h, with
 // g~ = g_f + g_fc for a conjugate pair, g_f for a self-conjugate f (full-grid dsigma), or the

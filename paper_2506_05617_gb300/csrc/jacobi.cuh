@@ -180,8 +180,23 @@ __device__ __forceinline__ bool pair_step(Planes<C>& a, Planes<C>& b, float tol2
   be = team_sum<L>(be);
   gr = team_sum<L>(gr);
   gi = team_sum<L>(gi);
+  // The rotation depends only on ratios, so scale the pair by a power of two that brings the
+  // larger squared norm into [1, 4): |gamma|^2 then stays a normal float down to column-norm
+  // ratios of ~1e-19. Without it, columns of a rank-deficient symbol shrink by ~eps every sweep
+  // (they are re-projected against the others), |gamma|^2 goes denormal, e = gamma/|gamma| loses
+  // its unit modulus and the rotations stop being unitary.
+  const float mx = fmaxf(al, be);
+  if (!(mx >= 1.17549435e-38f)) return false;        // both columns below ~1e-19: zero
+  const int ex = (__float_as_int(mx) >> 23) & 0xff;  // biased exponent of mx, in [1, 254]
+  const float sc = __int_as_float(max(254 - ex, 1) << 23);
+  al *= sc;
+  be *= sc;
+  gr *= sc;
+  gi *= sc;
   const float g2 = fmaf(gr, gr, gi * gi);
   if (!(g2 > tol2 * (al * be))) return false;
+  // a denormal |gamma|^2 that passes the test has be < 2e-25 al: the angle is below 1e-19
+  if (!(g2 >= 1.17549435e-38f)) return false;
   // J = [[c, s e], [-s conj(e), c]], e = gamma/|gamma|, t = tan solves t^2 + 2 zeta t - 1 = 0
   // with zeta = (beta - alpha)/(2|gamma|), |t| <= 1. The angle may be approximate; unitarity
   // rests on e, s and c-1, which are formed with correctly rounded reciprocals / reciprocal

@@ -297,6 +297,10 @@ lfa_status_t enqueue_forward(lfa_plan_s* p, const float* const* w, float* const*
     P.queue_slot = slot++;
     P.counters = p->counters;
     LFA_CUDA_TRY(vlaunch(g.variant, p->vec, true, P, g.grid, s));
+    // cluster variants write zero vectors for negligible singular values: complete them
+    if (p->vec && kVariants[g.variant].CS > 1)
+      for (int k = 0; k < P.nlayers; ++k)
+        LFA_CUDA_TRY(launch_complete(P.L[k], P.L[k].wide ? P.L[k].V : P.L[k].U, P.L[k].F_h, s));
   }
   // logged layers: per batch of symbols, the values-mode forward that logs its rotations and
   // writes sigma and the X-side vectors, then the replay that builds W
@@ -340,17 +344,25 @@ lfa_status_t enqueue_forward(lfa_plan_s* p, const float* const* w, float* const*
       R.counters = p->counters;
       int nk = 0;
       LFA_CUDA_TRY(launch_replay(NP, R, cnt, s, &nk));
+      LFA_CUDA_TRY(launch_complete(La, La.wide ? La.V : La.U, cnt, s));
     }
   }
   return LFA_OK;
 }
 
+// Kernels of one forward beyond one per group: per logged batch the logging forward, the
+// replay, the finalize and the completion; per layer of a cluster group with vectors, the
+// completion (one launch per 65535 symbols).
 int64_t logged_launches(const lfa_plan_s* p) {
   int64_t n = 0;
   for (const auto& lg : p->logged) {
     const int batches = (p->args[lg.layer].F_h + lg.batch - 1) / lg.batch;
-    n += 3 * (int64_t)batches;
+    n += 4 * (int64_t)batches;
   }
+  if (p->vec)
+    for (const auto& g : p->groups)
+      if (kVariants[g.variant].CS > 1)
+        for (int l : g.layers) n += (p->args[l].F_h + 65534) / 65535;
   return n;
 }
 

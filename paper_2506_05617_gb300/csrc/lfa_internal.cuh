@@ -140,6 +140,8 @@ cudaError_t prepare_replay(int NP);   // kernel attributes, once per plan
 
 // Auxiliary kernels (aux_kernels.cu).
 cudaError_t launch_symbols(const LayerArgs& La, float2* out, cudaStream_t s);
+// unit vectors for the exactly zero columns of the X-side factors [symbols][M][N] of a layer
+cudaError_t launch_complete(const LayerArgs& La, float2* X, int symbols, cudaStream_t s);
 cudaError_t launch_expand(const LayerArgs& La, const float2* U, const float2* V, int64_t first,
                           int64_t count, float2* u_hat, float2* v_hat, cudaStream_t s);
 cudaError_t launch_backward(const LayerArgs& La, const float* dsigma, int half_output,

@@ -117,13 +117,17 @@ __global__ void __launch_bounds__(512) finalize_kernel(const __grid_constant__ R
   __syncthreads();
   int rank = 0;
   bool finite = true;
+  float smax = 0.f;
   if (c < N) {
     for (int q = 0; q < N; ++q) {
       const float v = sg[q];
       finite = finite && isfinite(v);
+      smax = fmaxf(smax, v);
       rank += (v > sc) || (v == sc && q < c);
     }
   }
+  // a column far below sigma_max carries no direction: write it as zero (completed afterwards)
+  const float ixz = sc > 1e-12f * smax ? ixn : 0.f;
   if (__syncthreads_or(c < N && !finite) && c == 0) atomicAdd(&R.counters->nonfinite, 1ull);
   if (c >= N) return;
   const int h = slot;
@@ -140,7 +144,7 @@ __global__ void __launch_bounds__(512) finalize_kernel(const __grid_constant__ R
   float2* Wo = (La.wide ? La.U : La.V) + (size_t)h * N * N;
   for (int rw = 0; rw < M; ++rw) {
     const float2 v = X[(size_t)rw * N + c];
-    Xo[(size_t)rw * N + rank] = make_float2(v.x * ixn, v.y * ixn);
+    Xo[(size_t)rw * N + rank] = make_float2(v.x * ixz, v.y * ixz);
   }
   for (int rw = 0; rw < N; ++rw) {
     const float2 v = Wr[(size_t)rw * N + c];

@@ -60,6 +60,23 @@ def test_large_channels_match_oracle(spec):
     plan.close()
 
 
+@pytest.mark.parametrize("shape", [(128, 128, 4), (200, 160, 7), (512, 256, 16), (256, 512, 3)],
+                         ids=lambda s: "x".join(map(str, s)))
+def test_rank_deficient_symbols_get_complete_orthonormal_factors(shape):
+    """1x1 kernels of rank q: every symbol has rank q, so the factor built from X has N - q exactly
+    zero columns that must be completed to an orthonormal basis (cluster and rotation-log paths)."""
+    c_out, c_in, q = shape
+    rng = np.random.default_rng(q)
+    w = (rng.standard_normal((c_out, q)) @ rng.standard_normal((q, c_in)) / np.sqrt(q * c_in))
+    w = w.astype(np.float32).reshape(c_out, c_in, 1, 1)
+    plan, (s, U, V), st, info = gpu_svd(w, 2, 2, vectors=True)
+    assert st == C.LFA_OK, info
+    check_sigma(w, 2, 2, s)
+    assert np.all(s[:, q:] <= SIG_TOL * s.max())
+    check_vectors(w, 2, 2, s, U, V)
+    plan.close()
+
+
 def test_large_backward_matches_oracle():
     c_out, c_in, k, n, m = 128, 96, 3, 3, 4
     w = rand_w(c_out, c_in, k, k, seed=5)

@@ -39,6 +39,8 @@ STRIDED = [
     (128, 64, 3, 3, 3, 4, 2, 2, True),    # 128 x 256: cluster kernel
     (256, 128, 3, 3, 2, 3, 2, 2, False),  # 256 x 512 values
     (256, 128, 3, 3, 2, 2, 2, 2, True),   # 256 x 512 vectors: rotation log + replay
+    (128, 64, 1, 1, 3, 3, 2, 2, True),    # 128 x 256 of rank 64: cluster kernel + completion
+    (256, 128, 1, 1, 2, 2, 2, 2, True),   # 256 x 512 of rank 128: rotation log + completion
 ]
 
 
