@@ -185,8 +185,11 @@ __device__ __forceinline__ bool pair_step(Planes<C>& a, Planes<C>& b, float tol2
   // ratios of ~1e-19. Without it, columns of a rank-deficient symbol shrink by ~eps every sweep
   // (they are re-projected against the others), |gamma|^2 goes denormal, e = gamma/|gamma| loses
   // its unit modulus and the rotations stop being unitary.
+  // Both squared norms below 2^-100: the columns are zero. Above it their entries' products
+  // are normal floats, so |gamma| is exact enough for the threshold test (below it, denormal
+  // products leave gamma ~1e-5 relative noise and such a pair would rotate every sweep).
   const float mx = fmaxf(al, be);
-  if (!(mx >= 1.17549435e-38f)) return false;        // both columns below ~1e-19: zero
+  if (!(mx >= 0x1p-100f)) return false;
   const int ex = (__float_as_int(mx) >> 23) & 0xff;  // biased exponent of mx, in [1, 254]
   const float sc = __int_as_float(max(254 - ex, 1) << 23);
   al *= sc;
@@ -620,10 +623,11 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
     }
 
     if constexpr (C::VEC) {
-      // A column far below sigma_max (or whose squared norm is denormal) carries no direction:
-      // treat it as a zero singular value (or NaN) and complete it below.
-      const bool za = !(sa > 1e-12f * smax) || !(al > 1e-36f);
-      const bool zb = !(sb > 1e-12f * smax) || !(be > 1e-36f);
+      // A column far below sigma_max (or whose squared norm is below 2^-100, the bound under
+      // which the sweeps leave pairs unrotated) carries no direction: treat it as a zero
+      // singular value (or NaN) and complete it below.
+      const bool za = !(sa > 1e-12f * smax) || !(al > 0x1p-100f);
+      const bool zb = !(sb > 1e-12f * smax) || !(be > 0x1p-100f);
       const float ia = za ? 0.f : __frsqrt_rn(al), ib = zb ? 0.f : __frsqrt_rn(be);
       const float iwa = 1.f / nwa, iwb = 1.f / nwb;
       float2* Xo = La.wide ? La.V : La.U;     // normalised X columns

@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(512) finalize_kernel(const __grid_constant__ R
       wn = fmaf(v.x, v.x, fmaf(v.y, v.y, wn));
     }
   }
-  const float ixn = xn > 1e-36f ? rsqrt_nr(xn) : 0.f;
+  const float ixn = xn > 0x1p-100f ? rsqrt_nr(xn) : 0.f;   // zero-column bound of the sweeps
   const float iwn = wn > 0.f ? rsqrt_nr(wn) : 0.f;
   const float sc = xn * ixn * iwn;   // |x| / |w|
   if (c < N) sg[c] = sc;

@@ -129,28 +129,48 @@ def test_strided_lifted_vectors_are_singular_pairs_of_the_dense_operator():
     plan.close()
 
 
+def full_grid(X, n, m):
+    """Factors of every frequency from the half-grid ones: X_{-k} = conj(X_k)."""
+    half = list(O.half_grid(n, m))
+    pos = {f: i for i, f in enumerate(half)}
+    out = []
+    for f in range(n * m):
+        fc = ((-(f // m)) % n) * m + (-(f % m)) % m
+        out.append(X[pos[f]] if f in pos else np.conj(X[pos[fc]]))
+    return np.stack(out)
+
+
+def half_dsigma(g, n, m):
+    """Half-grid dL/dsigma: a half-grid row stands for its conjugate pair, g~ = g_f + g_fc."""
+    half = O.half_grid(n, m)
+    fc = [((-(f // m)) % n) * m + (-(f % m)) % m for f in half]
+    return np.stack([g[f] + (g[c] if c != f else 0) for f, c in zip(half, fc)]).astype(np.float32)
+
+
 @pytest.mark.parametrize("half_output", [False, True])
 @pytest.mark.parametrize("shape", [(8, 4, 3, 3, 5, 4, 2, 2), (24, 6, 5, 5, 3, 3, 3, 3), (64, 3, 7, 7, 6, 5, 2, 2),
                                    (16, 8, 1, 1, 4, 4, 2, 2), (128, 64, 3, 3, 3, 3, 2, 2)],
                          ids=lambda s: "x".join(map(str, s)))
 def test_strided_backward_matches_oracle(shape, half_output):
+    """The kernel's dL/dw against the oracle's formula on the same (GPU) factors, tightly; and the
+    whole forward + backward against the oracle's own SVD where r is small. (With many singular
+    values a random per-index dL/dsigma makes dL/dw depend on the basis chosen inside nearly
+    degenerate singular subspaces, so only the first comparison is well posed there.)"""
     c_out, c_in, kh, kw, n, m, sh, sw = shape
     w = rand_w(c_out, c_in, kh, kw, seed=17)
     plan, s, U, V = run(w, n, m, sh, sw, vectors=True, half_output=half_output)
     r = min(c_out, c_in * sh * sw)
-    s_ref, U_ref, V_ref = O.lfa_svd_strided(w, n, m, sh, sw)
     g = W.upstream_gradient((n * m, r), seed=19)
-    if half_output:
-        half = O.half_grid(n, m)
-        # a half-grid row stands for its conjugate pair: g~ = g_f + g_fc
-        fc = [((-(f // m)) % n) * m + (-(f % m)) % m for f in half]
-        gh = np.stack([g[f] + (g[c] if c != f else 0) for f, c in zip(half, fc)]).astype(np.float32)
-        ds = torch.from_numpy(gh).cuda()
-    else:
-        ds = torch.from_numpy(g).cuda()
+    ds = torch.from_numpy(half_dsigma(g, n, m) if half_output else g).cuda()
     dw = plan.backward([ds], [U], [V])[0].cpu().numpy()
-    dw_ref = O.lfa_backward_strided(w, n, m, sh, sw, g, U_ref, V_ref)
-    assert np.linalg.norm(dw - dw_ref) / np.linalg.norm(dw_ref) <= 1e-4
+    Uf = full_grid(U.cpu().numpy().astype(np.complex128), n, m)
+    Vf = full_grid(V.cpu().numpy().astype(np.complex128), n, m)
+    dw_same = O.lfa_backward_strided(w, n, m, sh, sw, g, Uf, Vf)
+    assert np.linalg.norm(dw - dw_same) / np.linalg.norm(dw_same) <= 1e-5
+    if r <= 32:
+        s_ref, U_ref, V_ref = O.lfa_svd_strided(w, n, m, sh, sw)
+        dw_ref = O.lfa_backward_strided(w, n, m, sh, sw, g, U_ref, V_ref)
+        assert np.linalg.norm(dw - dw_ref) / np.linalg.norm(dw_ref) <= 1e-4
     plan.close()
 
 
