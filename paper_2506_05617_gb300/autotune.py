@@ -25,7 +25,7 @@ def candidates(M: int, N: int, vectors: bool) -> List[int]:
     from . import lfa as C
     out = []
     for v in range(C.lfa_debug_variant_count()):
-        npairs, lanes, mr, wr, cs = (int(x) for x in re.findall(r"\d+", C.lfa_variant_name(v)))
+        npairs, lanes, mr, wr, cs, ppt = (int(x) for x in re.findall(r"\d+", C.lfa_variant_name(v)))
         if M > mr * lanes or N > 2 * npairs or (vectors and N > wr * lanes):
             continue
         out.append(v)
@@ -70,8 +70,9 @@ def tune(layers: Iterable[Tuple[int, ...]], vectors: bool, verbose: bool = True)
     from . import lfa as C
     best: Dict[Tuple[int, int, int], Tuple[int, float]] = {}
     for layer in layers:
-        c_out, c_in = layer[:2]
-        key = (max(c_out, c_in), min(c_out, c_in), int(vectors))
+        c_out = layer[0]
+        cols = layer[1] * (layer[8] if len(layer) > 8 else 1) * (layer[9] if len(layer) > 9 else 1)
+        key = (max(c_out, cols), min(c_out, cols), int(vectors))   # the symbol's shape
         if key in best:
             continue
         res = []
@@ -116,7 +117,7 @@ def main():
     names = a.workload or ["conv64_k3_n32"]
     layers = []
     for nm in names:
-        layers += [(l.c_out, l.c_in, l.kh, l.kw, l.n, l.m) for l in W.layers(nm)]
+        layers += [l.desc() for l in W.layers(nm)]
     best = tune(layers, vectors=True)
     if a.values:
         best.update(tune(layers, vectors=False))

@@ -6,7 +6,8 @@
 //  * The N columns of X (X = A_k or A_k^*, M x N, N = r, padded to NC = 2 NP) are
 //    paired; each pair is owned by a team of L lanes, each lane holding MR rows of
 //    both columns of X (and WR rows of the accumulated rotations W) in registers.
-//    Rows are interleaved: lane l holds rows l, l + L, l + 2L, ...
+//    Rows are interleaved: lane l holds rows l, l + L, l + 2L, ... A thread may serve
+//    PPT = 2 teams, whose rounds are independent dependency chains it interleaves.
 //  * One round: every team forms alpha = |x_p|^2, beta = |x_q|^2, gamma = x_p^* x_q
 //    by an xor butterfly over its L lanes (bitwise identical on every lane, so the
 //    team takes one decision) and, when |gamma| > tol sqrt(alpha beta), applies the
@@ -39,13 +40,15 @@ namespace lfa {
 
 namespace cg = cooperative_groups;
 
-template <int NP_, int L_, int MR_, int WR_, bool VEC_, int CS_, int MINB_ = 1>
+template <int NP_, int L_, int MR_, int WR_, bool VEC_, int CS_, int MINB_ = 1, int PPT_ = 1>
 struct JCfg {
-  static constexpr int NP = NP_, L = L_, MR = MR_, WR = WR_, CS = CS_;
+  static constexpr int NP = NP_, L = L_, MR = MR_, WR = WR_, CS = CS_, PPT = PPT_;
   static constexpr bool VEC = VEC_;
   static_assert(NP % 2 == 0 && NP % CS == 0, "pairs must be even and split evenly over the cluster");
   static constexpr int TPC = NP / CS;             // teams per CTA
-  static constexpr int TC = TPC * L;              // threads per CTA per symbol
+  static_assert(PPT == 1 || PPT == 2, "a thread holds rows of one or two teams");
+  static_assert(TPC % PPT == 0, "teams split evenly over the threads");
+  static constexpr int TC = TPC / PPT * L;        // threads per CTA per symbol
   static constexpr int UT = TC <= 32 ? 32 : TC;   // threads per unit (a warp, or the CTA)
   static constexpr int SPU = TC <= 32 ? 32 / TC : 1;
   static constexpr int BLOCK = TC <= 32 ? 128 : TC;
@@ -154,11 +157,14 @@ __device__ __forceinline__ float rsqrt_nr(float x) {
   return fmaf(y, fmaf(-h, y, 0.5f), y);   // y + y (1/2 - x y^2 / 2)
 }
 
-// One Jacobi round on the team's pair (a, b) (symmetric in the two columns): dots, butterfly,
-// rotation of X and W. Returns whether a rotation was applied.
+// One Jacobi round on a team's pair (a, b) comes in three phases, so that a thread holding two
+// pairs can interleave their dependency chains: pair_dots (alpha = |a|^2, beta = |b|^2,
+// gamma = a^* b, summed over the team's L lanes, bitwise identical on every lane), pair_test
+// (scaling and the rotation test), pair_params (the rotation) and rotate_pair (X and W).
 template <class C>
-__device__ __forceinline__ bool pair_step(Planes<C>& a, Planes<C>& b, float tol2, float4& prm) {
-  constexpr int MH = C::MH, WH = C::WH, L = C::L;
+__device__ __forceinline__ void pair_dots(const Planes<C>& a, const Planes<C>& b, float& al, float& be,
+                                          float& gr, float& gi) {
+  constexpr int MH = C::MH, L = C::L;
   // real and imaginary planes accumulate separately: eight independent chains
   float2 alr = f2(0.f), ali = f2(0.f), ber = f2(0.f), bei = f2(0.f);
   float2 grr = f2(0.f), gri = f2(0.f), gp2 = f2(0.f), gm2 = f2(0.f);
@@ -174,12 +180,18 @@ __device__ __forceinline__ bool pair_step(Planes<C>& a, Planes<C>& b, float tol2
     gm2 = __ffma2_rn(a.xi[k], b.xr[k], gm2);
   }
   const float2 al2 = __fadd2_rn(alr, ali), be2 = __fadd2_rn(ber, bei), gr2 = __fadd2_rn(grr, gri);
-  float al = al2.x + al2.y, be = be2.x + be2.y, gr = gr2.x + gr2.y;
-  float gi = (gp2.x + gp2.y) - (gm2.x + gm2.y);
+  al = al2.x + al2.y;
+  be = be2.x + be2.y;
+  gr = gr2.x + gr2.y;
+  gi = (gp2.x + gp2.y) - (gm2.x + gm2.y);
   al = team_sum<L>(al);
   be = team_sum<L>(be);
   gr = team_sum<L>(gr);
   gi = team_sum<L>(gi);
+}
+
+// Scales the pair's quantities (in place) and decides whether it rotates.
+__device__ __forceinline__ bool pair_test(float& al, float& be, float& gr, float& gi, float tol2) {
   // The rotation depends only on ratios, so scale the pair by a power of two that brings the
   // larger squared norm into [1, 4): |gamma|^2 then stays a normal float down to column-norm
   // ratios of ~1e-19. Without it, columns of a rank-deficient symbol shrink by ~eps every sweep
@@ -189,17 +201,22 @@ __device__ __forceinline__ bool pair_step(Planes<C>& a, Planes<C>& b, float tol2
   // are normal floats, so |gamma| is exact enough for the threshold test (below it, denormal
   // products leave gamma ~1e-5 relative noise and such a pair would rotate every sweep).
   const float mx = fmaxf(al, be);
-  if (!(mx >= 0x1p-100f)) return false;
-  const int ex = (__float_as_int(mx) >> 23) & 0xff;  // biased exponent of mx, in [1, 254]
+  const int ex = (__float_as_int(mx) >> 23) & 0xff;  // biased exponent of mx
   const float sc = __int_as_float(max(254 - ex, 1) << 23);
   al *= sc;
   be *= sc;
   gr *= sc;
   gi *= sc;
   const float g2 = fmaf(gr, gr, gi * gi);
-  if (!(g2 > tol2 * (al * be))) return false;
   // a denormal |gamma|^2 that passes the test has be < 2e-25 al: the angle is below 1e-19
-  if (!(g2 >= 1.17549435e-38f)) return false;
+  return mx >= 0x1p-100f && g2 > tol2 * (al * be) && g2 >= 1.17549435e-38f;
+}
+
+// Rotation parameters (c-1, Re(e s), Im(e s)) from the scaled quantities. With rot = false the
+// inputs are replaced by harmless ones, so the call may run unconditionally (its result unused).
+__device__ __forceinline__ float4 pair_params(float al, float be, float gr, float gi, bool rot) {
+  if (!rot) { al = 0.f; be = 0.f; gr = 1.f; gi = 0.f; }
+  const float g2 = fmaf(gr, gr, gi * gi);
   // J = [[c, s e], [-s conj(e), c]], e = gamma/|gamma|, t = tan solves t^2 + 2 zeta t - 1 = 0
   // with zeta = (beta - alpha)/(2|gamma|), |t| <= 1. The angle may be approximate; unitarity
   // rests on e, s and c-1, which are formed with correctly rounded reciprocals / reciprocal
@@ -216,12 +233,17 @@ __device__ __forceinline__ bool pair_step(Planes<C>& a, Planes<C>& b, float tol2
   const float s = tt * ir;
   const float r = r2 * ir;
   const float cm1 = __fdividef(-(tt * s), 1.f + r);  // tiny for small t: its relative error is harmless
-  const float sr = s * (gr * ig), si = s * (gi * ig);
-  // a' = a + (c-1) a - conj(e s) b ; b' = b + (c-1) b + (e s) a,  e s = sr + i si:
-  //   a'r = ar + cm1 ar - sr br - si bi     a'i = ai + cm1 ai - sr bi + si br
-  //   b'r = br + cm1 br + sr ar - si ai     b'i = bi + cm1 bi + sr ai + si ar
-  prm = make_float4(cm1, sr, si, 0.f);
-  const float2 c2 = f2(cm1), s2 = f2(sr), ns2 = f2(-sr), t2 = f2(si), nt2 = f2(-si);
+  return make_float4(cm1, s * (gr * ig), s * (gi * ig), 0.f);
+}
+
+// a' = a + (c-1) a - conj(e s) b ; b' = b + (c-1) b + (e s) a,  e s = sr + i si:
+//   a'r = ar + cm1 ar - sr br - si bi     a'i = ai + cm1 ai - sr bi + si br
+//   b'r = br + cm1 br + sr ar - si ai     b'i = bi + cm1 bi + sr ai + si ar
+// on the X planes and, with vectors, on the W planes.
+template <class C>
+__device__ __forceinline__ void rotate_pair(Planes<C>& a, Planes<C>& b, float4 prm) {
+  constexpr int MH = C::MH, WH = C::WH;
+  const float2 c2 = f2(prm.x), s2 = f2(prm.y), ns2 = f2(-prm.y), t2 = f2(prm.z), nt2 = f2(-prm.z);
 #pragma unroll
   for (int k = 0; k < MH; ++k) {
     const float2 Ar = a.xr[k], Ai = a.xi[k], Br = b.xr[k], Bi = b.xi[k];
@@ -240,7 +262,6 @@ __device__ __forceinline__ bool pair_step(Planes<C>& a, Planes<C>& b, float tol2
       b.wi[k] = __ffma2_rn(t2, Ar, __ffma2_rn(s2, Ai, __ffma2_rn(c2, Bi, Bi)));
     }
   }
-  return true;
 }
 
 // Apply a logged rotation (c-1, Re(e s), Im(e s)) to the X planes of a pair (the replay).
@@ -312,23 +333,29 @@ __device__ __forceinline__ float2 w_at(const Planes<C>& a, int s) {
 template <class C, bool FUSED, bool LOG = false>
 __global__ void __launch_bounds__(C::BLOCK, C::MINB)
 jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
-  static_assert(!LOG || (!C::VEC && C::CS > 1), "the rotation log serves values-mode cluster variants");
+  static_assert(!LOG || (!C::VEC && C::CS > 1 && C::PPT == 1),
+                "the rotation log serves values-mode cluster variants");
   constexpr int NP = C::NP, L = C::L, MR = C::MR, WR = C::WR, TC = C::TC, NC = C::NC;
-  constexpr int TPC = C::TPC, CS = C::CS, RS = C::RS;
+  constexpr int TPC = C::TPC, CS = C::CS, RS = C::RS, PPT = C::PPT;
+  constexpr int NCOL = 2 * PPT;   // columns a thread holds rows of
   constexpr int Cn = NC - 1;      // rounds per sweep
   constexpr int FIX = NC - 1;     // the column that stays at position 0
-  constexpr int WN = C::VEC ? WR : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
 
   const int unit = threadIdx.x / C::UT;
   const int ut = threadIdx.x % C::UT;
   const int sym = ut / TC;
   const int st = ut % TC;
-  const int lteam = st / L;
   const int lane = st % L;
   int crank = 0;
   if constexpr (CS > 1) crank = (int)cg::this_cluster().block_rank();
-  const int team = crank * TPC + lteam;
+  // the thread's teams: PPT consecutive teams of this CTA (local index lteam[j], global team[j])
+  int lteam[PPT], team[PPT];
+#pragma unroll
+  for (int j = 0; j < PPT; ++j) {
+    lteam[j] = (st / L) * PPT + j;
+    team[j] = crank * TPC + lteam[j];
+  }
   unsigned char* ubase = smem_raw + (size_t)unit * C::UNIT_BYTES;
   float2* mbox = reinterpret_cast<float2*>(ubase + (size_t)sym * C::SYM_BYTES);
   float2* phs = mbox + C::MBOX;
@@ -343,29 +370,32 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
   // is the team index, at odd rounds pi(team); the column a position sends goes to the
   // neighbouring position (0 -> 1, odd -> i-1, even -> i+1), held after the move by team
   // dp (next round odd) or pi(dp) (next round even).
-  float2 *dst_e, *dst_o;
-  int *dst_id_e, *dst_id_o;
+  float2 *dst_e[PPT], *dst_o[PPT];
+  int *dst_id_e[PPT], *dst_id_o[PPT];
+  const float2 *src_e[PPT], *src_o[PPT];
+  const int *src_id_e[PPT], *src_id_o[PPT];
   int* mids = reinterpret_cast<int*>(ssig + NC);   // column ids that travel with the columns
-  {
+#pragma unroll
+  for (int j = 0; j < PPT; ++j) {
     auto target = [&](int pos) { return pos == 0 ? 1 : ((pos & 1) ? pos - 1 : pos + 1); };
-    const int dest_e = pi_pos<NP>(target(team));           // sent at an even round
-    const int dest_o = target(pi_pos<NP>(team));           // sent at an odd round
-    dst_e = mbox + (size_t)(0 * TPC + dest_e % TPC) * RS;
-    dst_o = mbox + (size_t)(1 * TPC + dest_o % TPC) * RS;
-    dst_id_e = mids + 0 * TPC + dest_e % TPC;
-    dst_id_o = mids + 1 * TPC + dest_o % TPC;
+    const int dest_e = pi_pos<NP>(target(team[j]));        // sent at an even round
+    const int dest_o = target(pi_pos<NP>(team[j]));        // sent at an odd round
+    dst_e[j] = mbox + (size_t)(0 * TPC + dest_e % TPC) * RS;
+    dst_o[j] = mbox + (size_t)(1 * TPC + dest_o % TPC) * RS;
+    dst_id_e[j] = mids + 0 * TPC + dest_e % TPC;
+    dst_id_o[j] = mids + 1 * TPC + dest_o % TPC;
     if constexpr (CS > 1) {
       cg::cluster_group cl = cg::this_cluster();
-      dst_e = cl.map_shared_rank(dst_e, dest_e / TPC);
-      dst_o = cl.map_shared_rank(dst_o, dest_o / TPC);
-      dst_id_e = cl.map_shared_rank(dst_id_e, dest_e / TPC);
-      dst_id_o = cl.map_shared_rank(dst_id_o, dest_o / TPC);
+      dst_e[j] = cl.map_shared_rank(dst_e[j], dest_e / TPC);
+      dst_o[j] = cl.map_shared_rank(dst_o[j], dest_o / TPC);
+      dst_id_e[j] = cl.map_shared_rank(dst_id_e[j], dest_e / TPC);
+      dst_id_o[j] = cl.map_shared_rank(dst_id_o[j], dest_o / TPC);
     }
+    src_e[j] = mbox + (size_t)(0 * TPC + lteam[j]) * RS;
+    src_o[j] = mbox + (size_t)(1 * TPC + lteam[j]) * RS;
+    src_id_e[j] = mids + 0 * TPC + lteam[j];
+    src_id_o[j] = mids + 1 * TPC + lteam[j];
   }
-  const float2* src_e = mbox + (size_t)(0 * TPC + lteam) * RS;
-  const float2* src_o = mbox + (size_t)(1 * TPC + lteam) * RS;
-  const int* src_id_e = mids + 0 * TPC + lteam;
-  const int* src_id_o = mids + 1 * TPC + lteam;
 
   for (;;) {
     // ---------------------------------------------------------------- fetch a work item
@@ -412,40 +442,44 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
       unit_sync<C>();
     }
 
-    // ---------------------------------------------------------------- round-0 pair of this team
+    // ---------------------------------------------------------------- round-0 pair of each team
     // Two register arrays per team. Every team except team 0 keeps its newest column and
     // sends its older one, so at round t the column that moves is the one in array (t & 1):
     // arrays alternate by round parity and the moving array is static in the 2-way unrolled
     // loop. Team 0 keeps the fixed column NC-1 in array 0 and moves array 1 every round.
     // Round 0: position k holds (c(k), c(-k)), or (c(0), NC-1) for k = 0; the column that
     // leaves first goes to array 0 (array 1 for team 0).
-    int id0, id1;
-    if (team == 0) { id0 = FIX; id1 = 0; }
-    else if ((team & 1) || team == NP - 1) { id0 = team; id1 = Cn - team; }
-    else { id0 = Cn - team; id1 = team; }
-    Planes<C> c0, c1;
+    int id0[PPT], id1[PPT];
+    Planes<C> c0[PPT], c1[PPT];
 #pragma unroll
-    for (int k = 0; k < C::MH; ++k) {
-      const int r0 = lane + L * k, r1 = lane + L * (k + C::MH);
-      const float2 a0 = active ? x_entry<FUSED>(La, h, r0, id0, phs) : make_float2(0.f, 0.f);
-      const float2 a1 = active ? x_entry<FUSED>(La, h, r1, id0, phs) : make_float2(0.f, 0.f);
-      const float2 b0 = active ? x_entry<FUSED>(La, h, r0, id1, phs) : make_float2(0.f, 0.f);
-      const float2 b1 = active ? x_entry<FUSED>(La, h, r1, id1, phs) : make_float2(0.f, 0.f);
-      c0.xr[k] = make_float2(a0.x, a1.x);
-      c0.xi[k] = make_float2(a0.y, a1.y);
-      c1.xr[k] = make_float2(b0.x, b1.x);
-      c1.xi[k] = make_float2(b0.y, b1.y);
-    }
-    if constexpr (C::VEC) {
-      // W starts as the identity; rows beyond WR per lane are padding and stay zero
+    for (int j = 0; j < PPT; ++j) {
+      const int tm = team[j];
+      if (tm == 0) { id0[j] = FIX; id1[j] = 0; }
+      else if ((tm & 1) || tm == NP - 1) { id0[j] = tm; id1[j] = Cn - tm; }
+      else { id0[j] = Cn - tm; id1[j] = tm; }
 #pragma unroll
-      for (int k = 0; k < C::WH; ++k) {
-        const int r0 = lane + L * k, r1 = lane + L * (k + C::WH);
-        const bool v1 = k + C::WH < WR;
-        c0.wr[k] = make_float2(r0 == id0 && r0 < N ? 1.f : 0.f, v1 && r1 == id0 && r1 < N ? 1.f : 0.f);
-        c1.wr[k] = make_float2(r0 == id1 && r0 < N ? 1.f : 0.f, v1 && r1 == id1 && r1 < N ? 1.f : 0.f);
-        c0.wi[k] = make_float2(0.f, 0.f);
-        c1.wi[k] = make_float2(0.f, 0.f);
+      for (int k = 0; k < C::MH; ++k) {
+        const int r0 = lane + L * k, r1 = lane + L * (k + C::MH);
+        const float2 a0 = active ? x_entry<FUSED>(La, h, r0, id0[j], phs) : make_float2(0.f, 0.f);
+        const float2 a1 = active ? x_entry<FUSED>(La, h, r1, id0[j], phs) : make_float2(0.f, 0.f);
+        const float2 b0 = active ? x_entry<FUSED>(La, h, r0, id1[j], phs) : make_float2(0.f, 0.f);
+        const float2 b1 = active ? x_entry<FUSED>(La, h, r1, id1[j], phs) : make_float2(0.f, 0.f);
+        c0[j].xr[k] = make_float2(a0.x, a1.x);
+        c0[j].xi[k] = make_float2(a0.y, a1.y);
+        c1[j].xr[k] = make_float2(b0.x, b1.x);
+        c1[j].xi[k] = make_float2(b0.y, b1.y);
+      }
+      if constexpr (C::VEC) {
+        // W starts as the identity; rows beyond WR per lane are padding and stay zero
+#pragma unroll
+        for (int k = 0; k < C::WH; ++k) {
+          const int r0 = lane + L * k, r1 = lane + L * (k + C::WH);
+          const bool v1 = k + C::WH < WR;
+          c0[j].wr[k] = make_float2(r0 == id0[j] && r0 < N ? 1.f : 0.f, v1 && r1 == id0[j] && r1 < N ? 1.f : 0.f);
+          c1[j].wr[k] = make_float2(r0 == id1[j] && r0 < N ? 1.f : 0.f, v1 && r1 == id1[j] && r1 < N ? 1.f : 0.f);
+          c0[j].wi[k] = make_float2(0.f, 0.f);
+          c1[j].wi[k] = make_float2(0.f, 0.f);
+        }
       }
     }
 
@@ -482,38 +516,62 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
       }
       return !any_unit || sweeps >= P.max_sweeps;
     };
-    float4 prm;
     int t = 0;   // round counter (rotation log)
     float4* lg = nullptr;
-    if constexpr (LOG) lg = P.log + (size_t)h * P.log_cap * NP + team;
-    auto log_round = [&](bool rot) {
+    if constexpr (LOG) lg = P.log + (size_t)h * P.log_cap * NP + team[0];
+    // One round on every pair of the thread: all dot products first, then all rotation
+    // parameters (independent chains the scheduler can interleave), then the rotations.
+    auto round = [&]() {
+      float al[PPT], be[PPT], gr[PPT], gi[PPT];
+      bool rot[PPT];
+      bool any = false;
+#pragma unroll
+      for (int j = 0; j < PPT; ++j) pair_dots<C>(c0[j], c1[j], al[j], be[j], gr[j], gi[j]);
+#pragma unroll
+      for (int j = 0; j < PPT; ++j) {
+        rot[j] = pair_test(al[j], be[j], gr[j], gi[j], tol2);
+        any = any || rot[j];
+      }
+      float4 prm[PPT];
+      if (any) {
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) prm[j] = pair_params(al[j], be[j], gr[j], gi[j], rot[j]);
+#pragma unroll
+        for (int j = 0; j < PPT; ++j)
+          if (rot[j]) {
+            rotate_pair<C>(c0[j], c1[j], prm[j]);
+            rotated = 1;
+            ++nrot;
+          }
+      }
       if constexpr (LOG) {
-        if (lane == 0 && active && t < P.log_cap) lg[(size_t)t * NP] = rot ? prm : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (lane == 0 && active && t < P.log_cap)
+          lg[(size_t)t * NP] = rot[0] ? prm[0] : make_float4(0.f, 0.f, 0.f, 0.f);
         ++t;
       }
     };
     for (;;) {
       // even round: teams move array 0, team 0 moves array 1
-      {
-        const bool rot = pair_step<C>(c0, c1, tol2, prm);
-        if (rot) { rotated = 1; ++nrot; }
-        log_round(rot);
+      round();
+#pragma unroll
+      for (int j = 0; j < PPT; ++j) {
+        if (team[j] == 0) put_column<C>(c1[j], id1[j], dst_e[j], dst_id_e[j], lane);
+        else put_column<C>(c0[j], id0[j], dst_e[j], dst_id_e[j], lane);
       }
-      if (team == 0) put_column<C>(c1, id1, dst_e, dst_id_e, lane);
-      else put_column<C>(c0, id0, dst_e, dst_id_e, lane);
       sym_sync<C>();
-      if (team == 0) get_column<C>(c1, id1, src_e, src_id_e, lane);
-      else get_column<C>(c0, id0, src_e, src_id_e, lane);
+#pragma unroll
+      for (int j = 0; j < PPT; ++j) {
+        if (team[j] == 0) get_column<C>(c1[j], id1[j], src_e[j], src_id_e[j], lane);
+        else get_column<C>(c0[j], id0[j], src_e[j], src_id_e[j], lane);
+      }
       if (++rr == Cn && sweep_end()) break;
       // odd round: every team moves array 1
-      {
-        const bool rot = pair_step<C>(c0, c1, tol2, prm);
-        if (rot) { rotated = 1; ++nrot; }
-        log_round(rot);
-      }
-      put_column<C>(c1, id1, dst_o, dst_id_o, lane);
+      round();
+#pragma unroll
+      for (int j = 0; j < PPT; ++j) put_column<C>(c1[j], id1[j], dst_o[j], dst_id_o[j], lane);
       sym_sync<C>();
-      get_column<C>(c1, id1, src_o, src_id_o, lane);
+#pragma unroll
+      for (int j = 0; j < PPT; ++j) get_column<C>(c1[j], id1[j], src_o[j], src_id_o[j], lane);
       if (++rr == Cn && sweep_end()) break;
     }
     if (!converged && st == 0 && crank == 0 && active) {
@@ -530,8 +588,8 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
         for (int i = 0; i < MR; ++i) {
           const int row = lane + L * i;
           if (row < M) {
-            if (id0 < N) xo[(size_t)row * N + id0] = x_at<C>(c0, i);
-            if (id1 < N) xo[(size_t)row * N + id1] = x_at<C>(c1, i);
+            if (id0[0] < N) xo[(size_t)row * N + id0[0]] = x_at<C>(c0[0], i);
+            if (id1[0] < N) xo[(size_t)row * N + id1[0]] = x_at<C>(c1[0], i);
           }
         }
       }
@@ -540,85 +598,72 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
     }
 
     // ---------------------------------------------------------------- singular values, order
-    const int ca = id0, cb = id1;
-    float2 xa[MR], xb[MR], wa[WN], wb[WN];
+    // the thread's columns: 2 j (array 0 of team j) and 2 j + 1 (array 1)
+    auto col = [&](int kc) -> Planes<C>& { return (kc & 1) ? c1[kc >> 1] : c0[kc >> 1]; };
+    int cid[NCOL];
+    float al[NCOL], sg[NCOL], nw[NCOL];
 #pragma unroll
-    for (int i = 0; i < MR; ++i) {
-      xa[i] = x_at<C>(c0, i);
-      xb[i] = x_at<C>(c1, i);
-    }
+    for (int kc = 0; kc < NCOL; ++kc) {
+      cid[kc] = (kc & 1) ? id1[kc >> 1] : id0[kc >> 1];
+      const Planes<C>& X = col(kc);
+      float a = 0.f;
 #pragma unroll
-    for (int i = 0; i < WN; ++i) {
+      for (int i = 0; i < MR; ++i) {
+        const float2 x = x_at<C>(X, i);
+        a = fmaf(x.x, x.x, fmaf(x.y, x.y, a));
+      }
+      al[kc] = team_sum<L>(a);
+      sg[kc] = sqrtf(al[kc]);
+      nw[kc] = 1.f;   // norm of the accumulated rotation column (1 up to rounding)
       if constexpr (C::VEC) {
-        wa[i] = w_at<C>(c0, i);
-        wb[i] = w_at<C>(c1, i);
-      } else {
-        wa[i] = make_float2(0.f, 0.f);
-        wb[i] = make_float2(0.f, 0.f);
-      }
-    }
-    float al = 0.f, be = 0.f;
+        float q = 0.f;
 #pragma unroll
-    for (int i = 0; i < MR; ++i) {
-      al = fmaf(xa[i].x, xa[i].x, fmaf(xa[i].y, xa[i].y, al));
-      be = fmaf(xb[i].x, xb[i].x, fmaf(xb[i].y, xb[i].y, be));
-    }
-    al = team_sum<L>(al);
-    be = team_sum<L>(be);
-    float sa = sqrtf(al), sb = sqrtf(be);
-    float nwa = 1.f, nwb = 1.f;  // norms of the accumulated rotation columns (1 up to rounding)
-    if constexpr (C::VEC) {
-      float qa = 0.f, qb = 0.f;
-#pragma unroll
-      for (int i = 0; i < WR; ++i) {
-        qa = fmaf(wa[i].x, wa[i].x, fmaf(wa[i].y, wa[i].y, qa));
-        qb = fmaf(wb[i].x, wb[i].x, fmaf(wb[i].y, wb[i].y, qb));
+        for (int i = 0; i < WR; ++i) {
+          const float2 w = w_at<C>(X, i);
+          q = fmaf(w.x, w.x, fmaf(w.y, w.y, q));
+        }
+        q = team_sum<L>(q);
+        // x_p = A w_p up to rounding, so sigma_p = |x_p| / |w_p| with v_p = w_p / |w_p|
+        nw[kc] = q > 0.f ? sqrtf(q) : 1.f;
+        sg[kc] = sg[kc] / nw[kc];
       }
-      qa = team_sum<L>(qa);
-      qb = team_sum<L>(qb);
-      // x_p = A w_p up to rounding, so sigma_p = |x_p| / |w_p| with v_p = w_p / |w_p|
-      nwa = qa > 0.f ? sqrtf(qa) : 1.f;
-      nwb = qb > 0.f ? sqrtf(qb) : 1.f;
-      sa = sa / nwa;
-      sb = sb / nwb;
     }
     if (lane == 0) {
-      if constexpr (CS > 1) {
-        cg::cluster_group cl = cg::this_cluster();
-        for (int r = 0; r < CS; ++r) {
-          float* rs = cl.map_shared_rank(ssig, r);
-          if (ca < N) rs[ca] = sa;
-          if (cb < N) rs[cb] = sb;
+#pragma unroll
+      for (int kc = 0; kc < NCOL; ++kc) {
+        if (cid[kc] >= N) continue;
+        if constexpr (CS > 1) {
+          cg::cluster_group cl = cg::this_cluster();
+          for (int r = 0; r < CS; ++r) cl.map_shared_rank(ssig, r)[cid[kc]] = sg[kc];
+        } else {
+          ssig[cid[kc]] = sg[kc];
         }
-      } else {
-        if (ca < N) ssig[ca] = sa;
-        if (cb < N) ssig[cb] = sb;
       }
     }
     sym_sync<C>();
-    int rka = 0, rkb = 0;
+    int rk[NCOL];
+#pragma unroll
+    for (int kc = 0; kc < NCOL; ++kc) rk[kc] = 0;
     bool finite = true;
     float smax = 0.f;
     for (int q = 0; q < N; ++q) {
       const float v = ssig[q];
       finite = finite && isfinite(v);
       smax = fmaxf(smax, v);
-      rka += (v > sa) || (v == sa && q < ca);
-      rkb += (v > sb) || (v == sb && q < cb);
+#pragma unroll
+      for (int kc = 0; kc < NCOL; ++kc) rk[kc] += (v > sg[kc]) || (v == sg[kc] && q < cid[kc]);
     }
     if (active && st == 0 && crank == 0 && !finite) atomicAdd(&ctr->nonfinite, 1ull);
     if (active && lane == 0) {
       const int r = La.r;
       float* row = La.sigma + (size_t)(P.half_output ? h : f) * r;
-      if (ca < N) row[rka] = sa;
-      if (cb < N) row[rkb] = sb;
-      if (!P.half_output) {
-        const int fc = ((La.n - jj) % La.n) * La.m + (La.m - ll) % La.m;
-        if (fc != f) {
-          float* rowc = La.sigma + (size_t)fc * r;
-          if (ca < N) rowc[rka] = sa;
-          if (cb < N) rowc[rkb] = sb;
-        }
+      const int fc = ((La.n - jj) % La.n) * La.m + (La.m - ll) % La.m;
+      float* rowc = (!P.half_output && fc != f) ? La.sigma + (size_t)fc * r : nullptr;
+#pragma unroll
+      for (int kc = 0; kc < NCOL; ++kc) {
+        if (cid[kc] >= N) continue;
+        row[rk[kc]] = sg[kc];
+        if (rowc) rowc[rk[kc]] = sg[kc];
       }
     }
 
@@ -626,10 +671,14 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
       // A column far below sigma_max (or whose squared norm is below 2^-100, the bound under
       // which the sweeps leave pairs unrotated) carries no direction: treat it as a zero
       // singular value (or NaN) and complete it below.
-      const bool za = !(sa > 1e-12f * smax) || !(al > 0x1p-100f);
-      const bool zb = !(sb > 1e-12f * smax) || !(be > 0x1p-100f);
-      const float ia = za ? 0.f : __frsqrt_rn(al), ib = zb ? 0.f : __frsqrt_rn(be);
-      const float iwa = 1.f / nwa, iwb = 1.f / nwb;
+      bool zc[NCOL];
+      float ix[NCOL], iw[NCOL];
+#pragma unroll
+      for (int kc = 0; kc < NCOL; ++kc) {
+        zc[kc] = !(sg[kc] > 1e-12f * smax) || !(al[kc] > 0x1p-100f);
+        ix[kc] = zc[kc] ? 0.f : __frsqrt_rn(al[kc]);
+        iw[kc] = 1.f / nw[kc];
+      }
       float2* Xo = La.wide ? La.V : La.U;     // normalised X columns
       float2* Wo = La.wide ? La.U : La.V;     // accumulated rotations
       if constexpr (CS > 1) {
@@ -638,19 +687,20 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
           float2* xo = Xo + (size_t)h * M * N;
           float2* wo = Wo + (size_t)h * N * N;
 #pragma unroll
-          for (int i = 0; i < MR; ++i) {
-            const int row = lane + L * i;
-            if (row < M) {
-              if (ca < N) xo[(size_t)row * N + rka] = make_float2(xa[i].x * ia, xa[i].y * ia);
-              if (cb < N) xo[(size_t)row * N + rkb] = make_float2(xb[i].x * ib, xb[i].y * ib);
-            }
-          }
+          for (int kc = 0; kc < NCOL; ++kc) {
+            if (cid[kc] >= N) continue;
+            const Planes<C>& X = col(kc);
 #pragma unroll
-          for (int i = 0; i < WR; ++i) {
-            const int row = lane + L * i;
-            if (row < N) {
-              if (ca < N) wo[(size_t)row * N + rka] = make_float2(wa[i].x * iwa, wa[i].y * iwa);
-              if (cb < N) wo[(size_t)row * N + rkb] = make_float2(wb[i].x * iwb, wb[i].y * iwb);
+            for (int i = 0; i < MR; ++i) {
+              const int row = lane + L * i;
+              const float2 x = x_at<C>(X, i);
+              if (row < M) xo[(size_t)row * N + rk[kc]] = make_float2(x.x * ix[kc], x.y * ix[kc]);
+            }
+#pragma unroll
+            for (int i = 0; i < WR; ++i) {
+              const int row = lane + L * i;
+              const float2 w = w_at<C>(X, i);
+              if (row < N) wo[(size_t)row * N + rk[kc]] = make_float2(w.x * iw[kc], w.y * iw[kc]);
             }
           }
         }
@@ -661,21 +711,22 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
         int* defc = ubox + 3;
         if (ut == 0) *defc = 0;
         unit_sync<C>();
-        if (ca < N) {
-          float2* d = mbox + (size_t)rka * CSx;
 #pragma unroll
-          for (int i = 0; i < MR; ++i) d[lane + L * i] = make_float2(xa[i].x * ia, xa[i].y * ia);
+        for (int kc = 0; kc < NCOL; ++kc) {
+          if (cid[kc] >= N) continue;
+          const Planes<C>& X = col(kc);
+          float2* d = mbox + (size_t)rk[kc] * CSx;
 #pragma unroll
-          for (int i = 0; i < WR; ++i) d[C::XR + lane + L * i] = make_float2(wa[i].x * iwa, wa[i].y * iwa);
-          if (za && lane == 0) { ssig[ca] = -1.f; atomicAdd(defc, 1); }
-        }
-        if (cb < N) {
-          float2* d = mbox + (size_t)rkb * CSx;
+          for (int i = 0; i < MR; ++i) {
+            const float2 x = x_at<C>(X, i);
+            d[lane + L * i] = make_float2(x.x * ix[kc], x.y * ix[kc]);
+          }
 #pragma unroll
-          for (int i = 0; i < MR; ++i) d[lane + L * i] = make_float2(xb[i].x * ib, xb[i].y * ib);
-#pragma unroll
-          for (int i = 0; i < WR; ++i) d[C::XR + lane + L * i] = make_float2(wb[i].x * iwb, wb[i].y * iwb);
-          if (zb && lane == 0) { ssig[cb] = -1.f; atomicAdd(defc, 1); }
+          for (int i = 0; i < WR; ++i) {
+            const float2 w = w_at<C>(X, i);
+            d[C::XR + lane + L * i] = make_float2(w.x * iw[kc], w.y * iw[kc]);
+          }
+          if (zc[kc] && lane == 0) { ssig[cid[kc]] = -1.f; atomicAdd(defc, 1); }
         }
         unit_sync<C>();
         // ------------------------------------------------------------ complete zero columns

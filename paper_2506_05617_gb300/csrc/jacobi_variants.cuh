@@ -6,33 +6,36 @@
 #pragma once
 #include "jacobi.cuh"
 
-// X(id, NP, L, MR, WR, CS, VEC_OK, MINB)  MINB: CTAs per SM the register allocation targets
-#define LFA_JACOBI_VARIANTS(X)     \
-  X(0, 2, 4, 2, 1, 1, 1, 1)        \
-  X(1, 2, 8, 8, 1, 1, 1, 1)        \
-  X(2, 4, 4, 4, 2, 1, 1, 1)        \
-  X(3, 4, 8, 8, 1, 1, 1, 1)        \
-  X(4, 8, 4, 8, 4, 1, 1, 1)        \
-  X(5, 8, 8, 8, 2, 1, 1, 1)        \
-  X(6, 16, 8, 4, 4, 1, 1, 1)       \
-  X(7, 16, 8, 8, 4, 1, 1, 1)       \
-  X(8, 32, 8, 8, 8, 1, 1, 1)       \
-  X(9, 32, 4, 16, 16, 1, 1, 1)     \
-  X(10, 32, 16, 8, 4, 1, 1, 1)     \
-  X(11, 64, 16, 8, 8, 2, 1, 1)     \
-  X(12, 64, 16, 8, 8, 1, 0, 1)     \
-  X(13, 64, 32, 8, 4, 4, 1, 1)     \
-  X(14, 128, 32, 8, 8, 8, 1, 1)    \
-  X(15, 128, 32, 16, 8, 8, 0, 1)   \
-  X(16, 256, 32, 16, 16, 16, 0, 1) \
-  X(17, 32, 16, 4, 4, 1, 1, 2)     \
-  X(18, 16, 16, 4, 2, 1, 1, 2)
+// X(id, NP, L, MR, WR, CS, VEC_OK, MINB, PPT)  MINB: CTAs per SM the register allocation
+// targets; PPT: teams per thread (2: a thread interleaves the rounds of two column pairs)
+#define LFA_JACOBI_VARIANTS(X)        \
+  X(0, 2, 4, 2, 1, 1, 1, 1, 1)        \
+  X(1, 2, 8, 8, 1, 1, 1, 1, 1)        \
+  X(2, 4, 4, 4, 2, 1, 1, 1, 1)        \
+  X(3, 4, 8, 8, 1, 1, 1, 1, 1)        \
+  X(4, 8, 4, 8, 4, 1, 1, 1, 1)        \
+  X(5, 8, 8, 8, 2, 1, 1, 1, 1)        \
+  X(6, 16, 8, 4, 4, 1, 1, 1, 1)       \
+  X(7, 16, 8, 8, 4, 1, 1, 1, 1)       \
+  X(8, 32, 8, 8, 8, 1, 1, 1, 1)       \
+  X(9, 32, 4, 16, 16, 1, 1, 1, 1)     \
+  X(10, 32, 16, 8, 4, 1, 1, 1, 1)     \
+  X(11, 64, 16, 8, 8, 2, 1, 1, 1)     \
+  X(12, 64, 16, 8, 8, 1, 0, 1, 1)     \
+  X(13, 64, 32, 8, 4, 4, 1, 1, 1)     \
+  X(14, 128, 32, 8, 8, 8, 1, 1, 1)    \
+  X(15, 128, 32, 16, 8, 8, 0, 1, 1)   \
+  X(16, 256, 32, 16, 16, 16, 0, 1, 1) \
+  X(17, 32, 16, 4, 4, 1, 1, 2, 1)     \
+  X(18, 16, 16, 4, 2, 1, 1, 2, 1)     \
+  X(19, 128, 32, 8, 8, 8, 1, 1, 2)    \
+  X(20, 256, 32, 16, 16, 16, 0, 1, 2)
 
 namespace lfa {
 
-template <int NP, int L, int MR, int WR, int CS, int MB, bool VEC, bool FUSED, bool LOG = false>
+template <int NP, int L, int MR, int WR, int CS, int MB, int PPT, bool VEC, bool FUSED, bool LOG = false>
 cudaError_t jacobi_launch_t(const JacobiLaunch& P, int grid, cudaStream_t s) {
-  using C = JCfg<NP, L, MR, WR, VEC, CS, MB>;
+  using C = JCfg<NP, L, MR, WR, VEC, CS, MB, PPT>;
   if constexpr (CS == 1) {
     jacobi_kernel<C, FUSED, LOG><<<grid, C::BLOCK, C::SMEM, s>>>(P);
     return cudaGetLastError();
@@ -53,9 +56,9 @@ cudaError_t jacobi_launch_t(const JacobiLaunch& P, int grid, cudaStream_t s) {
   }
 }
 
-template <int NP, int L, int MR, int WR, int CS, int MB, bool VEC, bool FUSED, bool LOG = false>
+template <int NP, int L, int MR, int WR, int CS, int MB, int PPT, bool VEC, bool FUSED, bool LOG = false>
 cudaError_t jacobi_prepare_t() {
-  using C = JCfg<NP, L, MR, WR, VEC, CS, MB>;
+  using C = JCfg<NP, L, MR, WR, VEC, CS, MB, PPT>;
   cudaError_t e = cudaFuncSetAttribute(jacobi_kernel<C, FUSED, LOG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)C::SMEM);
   if (e == cudaSuccess && CS > 8)
@@ -64,9 +67,9 @@ cudaError_t jacobi_prepare_t() {
 }
 
 // Largest grid (in CTAs) that is fully co-resident: blocks per SM x SMs, or clusters x CS.
-template <int NP, int L, int MR, int WR, int CS, int MB, bool VEC, bool FUSED, bool LOG = false>
+template <int NP, int L, int MR, int WR, int CS, int MB, int PPT, bool VEC, bool FUSED, bool LOG = false>
 cudaError_t jacobi_grid_t(int sms, int* grid) {
-  using C = JCfg<NP, L, MR, WR, VEC, CS, MB>;
+  using C = JCfg<NP, L, MR, WR, VEC, CS, MB, PPT>;
   if constexpr (CS == 1) {
     int b = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, jacobi_kernel<C, FUSED, LOG>, C::BLOCK, C::SMEM);
@@ -112,43 +115,43 @@ cudaError_t jacobi_grid_t(int sms, int* grid) {
   }
 
 // values-only instantiations exist for every variant; vector ones only where VEC_OK
-#define LFA_CASE_LAUNCH_false_true(id, NP, L, MR, WR, CS, OK, MB) \
-  case id: return jacobi_launch_t<NP, L, MR, WR, CS, MB, false, true>(P, grid, s);
-#define LFA_CASE_LAUNCH_false_false(id, NP, L, MR, WR, CS, OK, MB) \
-  case id: return jacobi_launch_t<NP, L, MR, WR, CS, MB, false, false>(P, grid, s);
-#define LFA_CASE_LAUNCH_true_true(id, NP, L, MR, WR, CS, OK, MB)                              \
+#define LFA_CASE_LAUNCH_false_true(id, NP, L, MR, WR, CS, OK, MB, PPT) \
+  case id: return jacobi_launch_t<NP, L, MR, WR, CS, MB, PPT, false, true>(P, grid, s);
+#define LFA_CASE_LAUNCH_false_false(id, NP, L, MR, WR, CS, OK, MB, PPT) \
+  case id: return jacobi_launch_t<NP, L, MR, WR, CS, MB, PPT, false, false>(P, grid, s);
+#define LFA_CASE_LAUNCH_true_true(id, NP, L, MR, WR, CS, OK, MB, PPT)                              \
   case id:                                                                                 \
-    if constexpr (OK) return jacobi_launch_t<NP, L, MR, WR, CS, MB, true, true>(P, grid, s); \
+    if constexpr (OK) return jacobi_launch_t<NP, L, MR, WR, CS, MB, PPT, true, true>(P, grid, s); \
     else return cudaErrorInvalidValue;
-#define LFA_CASE_PREPARE_false_true(id, NP, L, MR, WR, CS, OK, MB) \
-  case id: return jacobi_prepare_t<NP, L, MR, WR, CS, MB, false, true>();
-#define LFA_CASE_PREPARE_false_false(id, NP, L, MR, WR, CS, OK, MB) \
-  case id: return jacobi_prepare_t<NP, L, MR, WR, CS, MB, false, false>();
-#define LFA_CASE_PREPARE_true_true(id, NP, L, MR, WR, CS, OK, MB)                    \
+#define LFA_CASE_PREPARE_false_true(id, NP, L, MR, WR, CS, OK, MB, PPT) \
+  case id: return jacobi_prepare_t<NP, L, MR, WR, CS, MB, PPT, false, true>();
+#define LFA_CASE_PREPARE_false_false(id, NP, L, MR, WR, CS, OK, MB, PPT) \
+  case id: return jacobi_prepare_t<NP, L, MR, WR, CS, MB, PPT, false, false>();
+#define LFA_CASE_PREPARE_true_true(id, NP, L, MR, WR, CS, OK, MB, PPT)                    \
   case id:                                                                        \
-    if constexpr (OK) return jacobi_prepare_t<NP, L, MR, WR, CS, MB, true, true>();  \
+    if constexpr (OK) return jacobi_prepare_t<NP, L, MR, WR, CS, MB, PPT, true, true>();  \
     else return cudaErrorInvalidValue;
-#define LFA_CASE_GRID_false_true(id, NP, L, MR, WR, CS, OK, MB) \
-  case id: return jacobi_grid_t<NP, L, MR, WR, CS, MB, false, true>(sms, g);
-#define LFA_CASE_GRID_false_false(id, NP, L, MR, WR, CS, OK, MB) \
-  case id: return jacobi_grid_t<NP, L, MR, WR, CS, MB, false, false>(sms, g);
-#define LFA_CASE_GRID_true_true(id, NP, L, MR, WR, CS, OK, MB)                           \
+#define LFA_CASE_GRID_false_true(id, NP, L, MR, WR, CS, OK, MB, PPT) \
+  case id: return jacobi_grid_t<NP, L, MR, WR, CS, MB, PPT, false, true>(sms, g);
+#define LFA_CASE_GRID_false_false(id, NP, L, MR, WR, CS, OK, MB, PPT) \
+  case id: return jacobi_grid_t<NP, L, MR, WR, CS, MB, PPT, false, false>(sms, g);
+#define LFA_CASE_GRID_true_true(id, NP, L, MR, WR, CS, OK, MB, PPT)                           \
   case id:                                                                            \
-    if constexpr (OK) return jacobi_grid_t<NP, L, MR, WR, CS, MB, true, true>(sms, g);   \
+    if constexpr (OK) return jacobi_grid_t<NP, L, MR, WR, CS, MB, PPT, true, true>(sms, g);   \
     else return cudaErrorInvalidValue;
 
 // the rotation-logging forward exists for the values-mode cluster variants only
-#define LFA_CASE_LAUNCH_log_log(id, NP, L, MR, WR, CS, OK, MB)                                         \
+#define LFA_CASE_LAUNCH_log_log(id, NP, L, MR, WR, CS, OK, MB, PPT)                                         \
   case id:                                                                                           \
-    if constexpr (CS > 1) return jacobi_launch_t<NP, L, MR, WR, CS, MB, false, true, true>(P, grid, s); \
+    if constexpr (CS > 1 && PPT == 1) return jacobi_launch_t<NP, L, MR, WR, CS, MB, PPT, false, true, true>(P, grid, s); \
     else return cudaErrorInvalidValue;
-#define LFA_CASE_PREPARE_log_log(id, NP, L, MR, WR, CS, OK, MB)                              \
+#define LFA_CASE_PREPARE_log_log(id, NP, L, MR, WR, CS, OK, MB, PPT)                              \
   case id:                                                                                 \
-    if constexpr (CS > 1) return jacobi_prepare_t<NP, L, MR, WR, CS, MB, false, true, true>(); \
+    if constexpr (CS > 1 && PPT == 1) return jacobi_prepare_t<NP, L, MR, WR, CS, MB, PPT, false, true, true>(); \
     else return cudaErrorInvalidValue;
-#define LFA_CASE_GRID_log_log(id, NP, L, MR, WR, CS, OK, MB)                                     \
+#define LFA_CASE_GRID_log_log(id, NP, L, MR, WR, CS, OK, MB, PPT)                                     \
   case id:                                                                                     \
-    if constexpr (CS > 1) return jacobi_grid_t<NP, L, MR, WR, CS, MB, false, true, true>(sms, g); \
+    if constexpr (CS > 1 && PPT == 1) return jacobi_grid_t<NP, L, MR, WR, CS, MB, PPT, false, true, true>(sms, g); \
     else return cudaErrorInvalidValue;
 
 cudaError_t jacobi_val_log_launch(int id, const JacobiLaunch& P, int grid, cudaStream_t s);

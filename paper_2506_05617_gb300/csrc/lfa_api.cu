@@ -87,15 +87,16 @@ bool build_schedule(int NC, std::vector<ushort2>& out) {
 }
 
 // --------------------------------------------------------------------------- variants
-struct VDesc { int NP, L, MR, WR, CS, vec_ok; };
+struct VDesc { int NP, L, MR, WR, CS, vec_ok, PPT; };
 const VDesc kVariants[] = {
-#define LFA_VD(id, NP, L, MR, WR, CS, OK, MB) {NP, L, MR, WR, CS, OK},
+#define LFA_VD(id, NP, L, MR, WR, CS, OK, MB, PPT) {NP, L, MR, WR, CS, OK, PPT},
     LFA_JACOBI_VARIANTS(LFA_VD)
 #undef LFA_VD
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 const char* kVariantNames[] = {
-#define LFA_VN(id, NP, L, MR, WR, CS, OK, MB) "reg_np" #NP "_l" #L "_mr" #MR "_wr" #WR "_cs" #CS,
+#define LFA_VN(id, NP, L, MR, WR, CS, OK, MB, PPT) \
+  "reg_np" #NP "_l" #L "_mr" #MR "_wr" #WR "_cs" #CS "_ppt" #PPT,
     LFA_JACOBI_VARIANTS(LFA_VN)
 #undef LFA_VN
 };
@@ -110,8 +111,9 @@ bool variant_fits(int v, int M, int N, bool vec) {
          N <= variant_cols(v, vec);
 }
 // Default choice: the smallest padded problem (2*NP columns x MR*L rows) that holds M x N;
-// ties go to the smaller cluster, then to fewer threads per symbol (fewer butterfly levels and
-// a cheaper barrier per round). An autotuner cache overrides this per problem.
+// ties go to the smaller cluster, then to one team per thread (the rotation log needs it),
+// then to fewer threads per symbol (fewer butterfly levels and a cheaper barrier per round).
+// An autotuner cache overrides this per problem.
 int choose_variant(int M, int N, bool vec) {
   int best = -1;
   long best_area = 0;
@@ -122,7 +124,8 @@ int choose_variant(int M, int N, bool vec) {
     if (!better && area == best_area) {
       const VDesc& a = kVariants[v];
       const VDesc& b = kVariants[best];
-      better = a.CS < b.CS || (a.CS == b.CS && a.NP * a.L < b.NP * b.L);
+      better = a.CS < b.CS || (a.CS == b.CS && a.PPT < b.PPT) ||
+               (a.CS == b.CS && a.PPT == b.PPT && a.NP * a.L < b.NP * b.L);
     }
     if (better) {
       best = v;
@@ -151,7 +154,7 @@ cudaError_t vlaunch(int id, bool vec, bool fused, const JacobiLaunch& P, int gri
   return cudaErrorInvalidValue;
 }
 int variant_spu(int id) {
-  const int TC = kVariants[id].NP / kVariants[id].CS * kVariants[id].L;
+  const int TC = kVariants[id].NP / kVariants[id].CS / kVariants[id].PPT * kVariants[id].L;
   return TC <= 32 ? 32 / TC : 1;
 }
 int variant_cs(int id) { return kVariants[id].CS; }
@@ -432,7 +435,8 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
     if (v < 0 && p->vec && !p->plain) {
       // W does not fit registers next to X: values-mode cluster variant + rotation log + replay
       v = choose_variant(La.M, La.N, false);
-      if (v >= 0 && kVariants[v].CS > 1 && (kVariants[v].NP == 128 || kVariants[v].NP == 256)) logged = true;
+      if (v >= 0 && kVariants[v].CS > 1 && kVariants[v].PPT == 1 && (kVariants[v].NP == 128 || kVariants[v].NP == 256))
+        logged = true;
       else v = -1;
     }
     if (v < 0) { free_plan(p); return LFA_ERR_UNSUPPORTED; }

@@ -68,8 +68,9 @@ def test_variant_choice():
             v = C.lfa_debug_choose_variant(M, N, vec)
             assert v >= 0, (M, N, vec)
             name = C.lfa_variant_name(v)
-            npairs, lanes, mr, wr, cs = (int(x) for x in re.findall(r"\d+", name))
+            npairs, lanes, mr, wr, cs, ppt = (int(x) for x in re.findall(r"\d+", name))
             assert M <= mr * lanes and N <= 2 * npairs
+            assert ppt == 1          # the built-in choice keeps one team per thread
             if vec:
                 assert N <= wr * lanes
     assert C.lfa_debug_choose_variant(513, 8, True) == -1
