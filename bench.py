@@ -529,6 +529,45 @@ def run_reference(args):
     }
 
 
+def run_sweep(args):
+    """O(N) study: the 64->64 3x3 layer at each torus size n (values + vectors forward), one JSON
+    line per n. The time per symbol stays flat once the GPU is full, so the time grows with the
+    number of frequencies n^2, i.e. linearly in the operator size N = c n^2."""
+    import torch
+    from paper_2506_05617_gb300 import build as B
+    from paper_2506_05617_gb300.torch_api import LfaPlan
+    B.build()
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(args.flush_mb << 20, dtype=torch.uint8, device=dev)
+    for n in (int(x) for x in args.sweep_n.split(",")):
+        lay = W.conv64_sweep(n)[0]
+        w = torch.from_numpy(W.weights(lay)).to(dev)
+        for vectors in (True, False):
+            plan = LfaPlan([lay.desc()], vectors=vectors, tune_cache=args.tune_cache)
+            out = plan.alloc(dev)
+            for _ in range(max(3, args.warmup)):
+                plan.svd([w], out=out)
+            ts = []
+            for _ in range(args.steps):
+                flush.fill_(3)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                plan.svd([w], out=out)
+                b.record()
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            st, info = plan.info()
+            F_h = plan.meta[0]["F_h"]
+            plan.close()
+            ms = float(np.median(ts))
+            print(json.dumps({"sweep": "n", "workload": "conv64_k3", "n": n, "outputs": "values+vectors" if vectors
+                              else "values", "ms": ms, "symbols_half_grid": F_h,
+                              "singular_values_per_s": n * n * lay.r / (ms / 1e3),
+                              "us_per_half_grid_symbol": ms * 1e3 / F_h, "status": st,
+                              "sweeps_per_symbol": info["sweeps"] / max(1, info["symbols"])}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -544,12 +583,17 @@ def main():
     ap.add_argument("--tune-cache", default=DEFAULT_TUNE if os.path.exists(DEFAULT_TUNE) else None,
                     help="autotuner cache file read by lfa_plan")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep-n", default=None,
+                    help="comma-separated torus sizes: run the O(N) study of the 64->64 layer instead "
+                         "(one JSON line per n and output mode)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.warmup < 3:
         args.warmup = 3
+    if args.sweep_n:
+        return run_sweep(args)
     if args.impl == "reference":
         if rank != 0:
             return 0

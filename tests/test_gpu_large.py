@@ -179,3 +179,19 @@ def test_conv512_n64_values_and_vectors_sampled():
     for X in (Uu, Vv):
         assert np.max(np.abs(np.einsum("hos,hot->hst", np.conj(X), X) - np.eye(lay.r))) <= VEC_TOL
     plan.close()
+
+
+def test_paper_shape_at_n2048_values_sampled():
+    """The paper's 16->16 3x3 shape at n = 2048 (2,097,154 half-grid symbols, 67M singular values):
+    sampled frequencies against the oracle, Parseval over all of them, conjugate mirror."""
+    lay = W.Layer(16, 16, 3, 3, 2048, 2048, "normal", 2.0, 6)
+    w = W.weights(lay)
+    plan, (s, _, _), st, info = gpu_svd(w, lay.n, lay.m, vectors=False)
+    assert st == C.LFA_OK, info
+    assert s.shape == (lay.F, 16)
+    sampled_sigma_check(w, lay, s, 8, seed=4)
+    fr = np.random.default_rng(5).choice(lay.F, 64, replace=False)
+    j, l = fr // lay.m, fr % lay.m
+    fc = ((-j) % lay.n) * lay.m + (-l) % lay.m
+    assert np.array_equal(s[fr], s[fc])
+    plan.close()
