@@ -50,7 +50,7 @@ __all__ = [
     "lift", "apply_operator", "apply_adjoint", "half_grid", "lfa_backward",
     "regulariser_loss", "regulariser_grad_sigma", "folded_kernel", "edit_values",
     "spectral_edit", "dense_spectral_edit", "dense_operator_strided", "symbols_strided",
-    "lfa_svd_strided", "lfa_backward_strided", "lift_strided",
+    "lfa_svd_strided", "lfa_backward_strided", "lift_strided", "dense_operator_dirichlet",
 ]
 
 
@@ -423,3 +423,31 @@ def lift_strided(U_k, V_k, j: int, l: int, n: int, m: int, s_h: int, s_w: int):
     v = np.einsum("iabq,xy->qixayb", Vr, mode)                        # [q, i, x1, u_h, x2, u_w]
     v_hat = v.reshape(v.shape[0], c_in, n * s_h, m * s_w)
     return u_hat, v_hat
+
+
+# --------------------------------------------------------------------------- boundary conditions
+# LFA is exact for periodic boundary conditions (Sec. III); the paper compares its spectra with
+# those of the same convolution under zero (Dirichlet) padding (Sec. III "Boundary Conditions"),
+# where the operator is no longer block-diagonalised by Fourier modes and only a dense SVD applies.
+
+def dense_operator_dirichlet(w, n: int, m: int, pad_h: int = -1, pad_w: int = -1) -> np.ndarray:
+    """Dense zero-padded convolution on an n x m grid: row (o, x1, x2), column (i, z1, z2) with
+    z = x + y_ab inside the grid (taps that leave it read zero): entry += w[o, i, a, b]."""
+    w = np.asarray(w, dtype=np.float64)
+    c_out, c_in, kh, kw = w.shape
+    ph, pw = origin(kh, kw, pad_h, pad_w)
+    A = np.zeros((c_out * n * m, c_in * n * m), dtype=np.float64)
+    for a in range(kh):
+        for b in range(kw):
+            for x1 in range(n):
+                z1 = x1 + a - ph
+                if not 0 <= z1 < n:
+                    continue
+                for x2 in range(m):
+                    z2 = x2 + b - pw
+                    if not 0 <= z2 < m:
+                        continue
+                    rows = np.arange(c_out) * n * m + x1 * m + x2
+                    cols = np.arange(c_in) * n * m + z1 * m + z2
+                    A[np.ix_(rows, cols)] += w[:, :, a, b]
+    return A

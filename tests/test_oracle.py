@@ -398,3 +398,29 @@ def test_strided_lifted_vectors_and_backward():
         wm = w.copy(); wm[idx] -= h
         fd[idx] = (L(wp) - L(wm)) / (2 * h)
     np.testing.assert_allclose(dW, fd, rtol=1e-6, atol=1e-8)
+
+
+# ----------------------------------------------------------------- zero (Dirichlet) boundary conditions
+@pytest.mark.parametrize("c_out,c_in,kh,kw,n,m", [(3, 2, 3, 3, 5, 4), (2, 3, 5, 3, 4, 6), (2, 2, 1, 1, 3, 3)])
+def test_dirichlet_operator_is_torch_zero_padded_conv(c_out, c_in, kh, kw, n, m):
+    w = rand_w(c_out, c_in, kh, kw, 61)
+    A = O.dense_operator_dirichlet(w, n, m)
+    f = RNG.standard_normal((c_in, n, m))
+    ref = Fnn.conv2d(torch.as_tensor(f)[None], torch.as_tensor(w), padding=(kh // 2, kw // 2))[0].numpy()
+    np.testing.assert_allclose(A @ f.ravel(), ref.ravel(), rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("n,m,k", [(4, 4, 3), (5, 3, 3), (3, 4, 5)])
+def test_dirichlet_spectrum_interlaces_the_periodic_one_on_the_padded_torus(n, m, k):
+    """The zero-padded operator on n x m is a compression S^T A S of the periodic operator on the
+    (n + k - 1) x (m + k - 1) torus (no wrap-around reaches the grid), so its singular values are
+    bounded one by one by the periodic ones (interlacing for submatrices)."""
+    w = rand_w(3, 3, k, k, 62)
+    sd = np.sort(np.linalg.svd(O.dense_operator_dirichlet(w, n, m), compute_uv=False))[::-1]
+    sp = np.sort(O.dense_svd(w, n + k - 1, m + k - 1))[::-1]
+    assert np.all(sd <= sp[: sd.size] + 1e-12)
+
+
+def test_dirichlet_equals_periodic_for_1x1_kernels():
+    w = rand_w(4, 3, 1, 1, 63)
+    np.testing.assert_allclose(O.dense_operator_dirichlet(w, 4, 5), O.dense_operator(w, 4, 5), atol=0)
