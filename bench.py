@@ -76,7 +76,7 @@ def executed_flops(layers, info, vectors: bool) -> float:
 def kernel_sha16() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("jacobi.cuh", "jacobi_variants.cuh"):
+    for f in ("jacobi.cuh", "jacobi_variants.cuh", "lfa_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2506_05617_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
