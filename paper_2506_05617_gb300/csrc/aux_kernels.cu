@@ -63,41 +63,80 @@ __device__ int half_index(const int32_t* half, int F_h, int f) {
   return lo;
 }
 
+// A CTA serves one vector q (blockIdx.y) and kExpandRows consecutive output rows (vector
+// channel c, grid row z1); the frequency's half-grid position is found once per CTA. Each warp
+// takes rows in turn: the row's phase factor and source entry are computed once, the lanes stride
+// along the row (coalesced writes), and every phase index is an exact 32-bit product mod n or m
+// (j, x1 < n <= 65536, so j x1 < 2^32); along a stride-1 row the column index advances by a
+// constant 32 l mod m per step.
+constexpr int kExpandRows = 64;
+
 __global__ void __launch_bounds__(256) expand_kernel(LayerArgs La, const float2* U, const float2* V,
                                                      int64_t first, float2* u_hat, float2* v_hat) {
+  __shared__ int sh_h;
   const int64_t q = first + blockIdx.y;
   const int r = La.r;
   const int f = (int)(q / r), s = (int)(q - (int64_t)f * r);
-  const int j = f / La.m, l = f - j * La.m;
-  const int fc = ((La.n - j) % La.n) * La.m + (La.m - l) % La.m;
+  const unsigned j = (unsigned)(f / La.m), l = (unsigned)(f - (int)j * La.m);
+  const int fc = ((La.n - (int)j) % La.n) * La.m + (La.m - (int)l) % La.m;
   const bool conj = fc < f;
-  const int h = half_index(La.half, La.F_h, conj ? fc : f);
-  const int nm = La.n * La.m;
-  const float scale = rsqrtf((float)nm);
-  for (int pass = 0; pass < 2; ++pass) {
-    const float2* Src = pass == 0 ? U : V;
-    float2* dst = pass == 0 ? u_hat : v_hat;
-    const int C = pass == 0 ? La.c_out : La.c_in;               // rows of the factor
-    const int sh = pass == 0 ? 1 : La.sh, sw = pass == 0 ? 1 : La.sw;
-    if (dst == nullptr || Src == nullptr) continue;
-    const int G2 = La.m * sw;                                     // output grid sh n x sw m
-    const int64_t G = (int64_t)La.n * sh * G2;
-    const float2* col = Src + (size_t)h * C * r + s;
-    float2* d = dst + (size_t)blockIdx.y * C * nm;
-    const int64_t total = (int64_t)C * nm;                        // = (C / (sh sw)) * G
-    const int64_t per = (total + gridDim.x - 1) / gridDim.x;
-    const int64_t e0 = (int64_t)blockIdx.x * per, e1 = e0 + per < total ? e0 + per : total;
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      const int c = (int)(e / G);
-      const int64_t z = e - (int64_t)c * G;
-      const int z1 = (int)(z / G2), z2 = (int)(z - (int64_t)z1 * G2);
-      const int x1 = z1 / sh, uh = z1 - x1 * sh, x2 = z2 / sw, uw = z2 - x2 * sw;
-      float2 u = __ldg(col + (size_t)((c * sh + uh) * sw + uw) * r);
-      if (conj) u.y = -u.y;
-      const float2 ph = cmul(La.tw_n[(int)(((int64_t)j * x1) % La.n)],
-                             La.tw_m[(int)(((int64_t)l * x2) % La.m)]);
-      const float2 v = cmul(u, ph);
-      d[e] = make_float2(v.x * scale, v.y * scale);
+  if (threadIdx.x == 0) sh_h = half_index(La.half, La.F_h, conj ? fc : f);
+  __syncthreads();
+  const int h = sh_h;
+  const int n = La.n, m = La.m;
+  const float scale = rsqrtf((float)n * (float)m);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
+  // rows per vector: c_out n + c_w sh n <= 512 * 65536 * 8 < 2^31
+  const int rows_u = u_hat ? La.c_out * n : 0;
+  const int rows_v = v_hat ? La.c_w * La.sh * n : 0;   // input channels x fine rows
+  const int R0 = blockIdx.x * kExpandRows;
+  const int Rend = min(R0 + kExpandRows, rows_u + rows_v);
+  const unsigned step = (32u * l) % (unsigned)m;      // column phase index advance per 32 columns
+  for (int R = R0 + warp; R < Rend; R += warps) {
+    const float2* col;
+    float2* d;
+    int sh, sw, row;
+    if (R < rows_u) {
+      row = R;
+      col = U + (size_t)h * La.c_out * r + s;
+      d = u_hat + (size_t)blockIdx.y * La.c_out * n * m;
+      sh = 1; sw = 1;
+    } else {
+      row = R - rows_u;
+      col = V + (size_t)h * La.c_in * r + s;
+      d = v_hat + (size_t)blockIdx.y * La.c_in * n * m;
+      sh = La.sh; sw = La.sw;
+    }
+    // row -> (channel ci of the output grid, fine row z1); the output grid is (sh n) x (sw m)
+    const int fine_rows = sh * n;
+    const int ci = row / fine_rows;
+    const int z1 = row - ci * fine_rows;
+    const int x1 = z1 / sh, uh = z1 - x1 * sh;
+    const float2 pa = La.tw_n[((unsigned)j * (unsigned)x1) % (unsigned)n];
+    const int len = sw * m;
+    float2* out = d + ((size_t)ci * fine_rows + z1) * len;
+    const float2* src = col + (size_t)(ci * sh + uh) * sw * r;
+    float2 u0 = __ldg(src);                         // the entry for uw = 0 (the only one when sw = 1)
+    if (conj) u0.y = -u0.y;
+    const float2 a0 = make_float2((u0.x * pa.x - u0.y * pa.y) * scale, (u0.x * pa.y + u0.y * pa.x) * scale);
+    if (sw == 1) {
+      unsigned idx = ((unsigned)l * (unsigned)lane) % (unsigned)m;   // (l x2) mod m for x2 = lane
+      for (int z2 = lane; z2 < len; z2 += 32) {
+        out[z2] = cmul(a0, La.tw_m[idx]);
+        idx += step;
+        if (idx >= (unsigned)m) idx -= (unsigned)m;
+      }
+    } else {
+      for (int z2 = lane; z2 < len; z2 += 32) {
+        const int x2 = z2 / sw, uw = z2 - x2 * sw;
+        float2 a = a0;
+        if (uw != 0) {
+          float2 u = __ldg(src + (size_t)uw * r);
+          if (conj) u.y = -u.y;
+          a = make_float2((u.x * pa.x - u.y * pa.y) * scale, (u.x * pa.y + u.y * pa.x) * scale);
+        }
+        out[z2] = cmul(a, La.tw_m[((unsigned)l * (unsigned)x2) % (unsigned)m]);
+      }
     }
   }
 }
@@ -116,12 +155,11 @@ cudaError_t launch_expand(const LayerArgs& La, const float2* U, const float2* V,
     }
     return cudaSuccess;
   }
-  const int64_t per_vec = (int64_t)(La.c_out > La.c_in ? La.c_out : La.c_in) * La.n * La.m;
-  int64_t chunks = (per_vec + 8191) / 8192;                 // ~32 elements per thread
-  const int64_t want = 4 * 152 * 4;                          // enough CTAs to fill the GPU
-  if (chunks * count > want) chunks = (want + count - 1) / count;
-  if (chunks < 1) chunks = 1;
-  dim3 grid((unsigned)chunks, (unsigned)count);
+  const int64_t rows = (u_hat ? (int64_t)La.c_out * La.n : 0) + (v_hat ? (int64_t)La.c_w * La.sh * La.n : 0);
+  const int64_t blocks = (rows + kExpandRows - 1) / kExpandRows;
+  if (blocks <= 0) return cudaSuccess;
+  if (rows > 0x7fffffffLL) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)blocks, (unsigned)count);
   expand_kernel<<<grid, 256, 0, s>>>(La, U, V, first, u_hat, v_hat);
   return cudaGetLastError();
 }
@@ -365,6 +403,102 @@ __global__ void __launch_bounds__(128) backward_dw_kernel(LayerArgs La, const fl
     if (b < kw) p[b] = acc[b];
 }
 
+// Fused stages 1 + 2 for stride-1 layers with at most KK taps: one CTA per (chunk of frequencies,
+// tile of 16 output x 64 input channels). Per frequency it forms its tile of G_h in registers
+// (4 entries per thread: U rows scaled by g~ and V rows staged in shared memory, 32 singular
+// indices at a time) and adds Re(G_h[o,i] conj(P_h[a,b])) for every tap to per-thread sums,
+// with the k_h x k_w phases of the frequency in shared memory. Writes the same per-chunk partial
+// sums as stage 2; no G round trip through memory. Fixed summation order (deterministic).
+template <int KK>
+__global__ void __launch_bounds__(256) backward_fused_kernel(LayerArgs La, const float* dsigma, int half_output,
+                                                             const float2* U, const float2* V, int chunk,
+                                                             float* partial) {
+  constexpr int TO = 16, TI = 64;
+  __shared__ float2 Us[TO][33];
+  __shared__ float2 Vs[TI][33];
+  __shared__ float2 sph[KK];
+  const int r = La.r, co = La.c_out, ci = La.c_in, kk = La.kh * La.kw;
+  const int o0 = blockIdx.y * TO, i0 = blockIdx.x * TI;
+  const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;   // entries (o0 + ty + 4 q, i0 + tx), q < 4
+  const int c = blockIdx.z;
+  float acc[4][KK];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int t = 0; t < KK; ++t) acc[q][t] = 0.f;
+  const int h0 = c * chunk, h1 = min(La.F_h, h0 + chunk);
+  for (int h = h0; h < h1; ++h) {
+    const int f = La.half[h];
+    const int j = f / La.m, l = f - j * La.m;
+    const int fc = ((La.n - j) % La.n) * La.m + (La.m - l) % La.m;
+    const float* g_f = dsigma + (size_t)(half_output ? h : f) * r;
+    const float* g_c = (!half_output && fc != f) ? dsigma + (size_t)fc * r : nullptr;
+    const float2* Uh = U + (size_t)h * co * r;
+    const float2* Vh = V + (size_t)h * ci * r;
+    __syncthreads();                                       // the previous frequency is consumed
+    if (threadIdx.x < kk) sph[threadIdx.x] = tap_phase(La, j, l, threadIdx.x / La.kw, threadIdx.x % La.kw);
+    float2 g[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) g[q] = make_float2(0.f, 0.f);
+    for (int s0 = 0; s0 < r; s0 += 32) {
+      for (int e = threadIdx.x; e < TO * 32; e += 256) {
+        const int row = e >> 5, ss = e & 31, sg = s0 + ss;
+        float2 u = make_float2(0.f, 0.f);
+        if (sg < r && o0 + row < co) {
+          const float gs = g_f[sg] + (g_c ? g_c[sg] : 0.f);
+          u = Uh[(size_t)(o0 + row) * r + sg];
+          u = make_float2(u.x * gs, u.y * gs);
+        }
+        Us[row][ss] = u;
+      }
+      for (int e = threadIdx.x; e < TI * 32; e += 256) {
+        const int row = e >> 5, ss = e & 31, sg = s0 + ss;
+        Vs[row][ss] = (sg < r && i0 + row < ci) ? Vh[(size_t)(i0 + row) * r + sg] : make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int ss = 0; ss < 32; ++ss) {
+        const float2 v = Vs[tx][ss];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {                     // g += u conj(v)
+          const float2 u = Us[ty + 4 * q][ss];
+          g[q].x = fmaf(u.x, v.x, fmaf(u.y, v.y, g[q].x));
+          g[q].y = fmaf(u.y, v.x, fmaf(-u.x, v.y, g[q].y));
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int t = 0; t < KK; ++t) {
+      if (t < kk) {
+        const float2 p = sph[t];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q][t] = fmaf(g[q].x, p.x, fmaf(g[q].y, p.y, acc[q][t]));   // Re(g conj(p))
+      }
+    }
+  }
+  const int CW = co * La.c_w;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int o = o0 + ty + 4 * q, i = i0 + tx;
+    if (o >= co || i >= ci) continue;
+    float* pp = partial + ((size_t)c * CW + (size_t)o * La.c_w + i) * kk;
+#pragma unroll
+    for (int t = 0; t < KK; ++t)
+      if (t < kk) pp[t] = acc[q][t];
+  }
+}
+
+// Whether the fused backward serves a layer, and its chunk count for a GPU of 152 SMs.
+int fused_backward_chunks(const LayerArgs& La) {
+  if (La.sh != 1 || La.sw != 1 || La.kh * La.kw > 25 || La.F_h <= 0) return 0;
+  const int tiles = ((La.c_in + 63) / 64) * ((La.c_out + 15) / 16);
+  int chunks = (4 * 152 + tiles - 1) / tiles;
+  chunks = chunks < La.F_h ? chunks : La.F_h;
+  chunks = chunks < 4096 ? chunks : 4096;
+  return chunks < 1 ? 1 : chunks;
+}
+
 // Stage 3: dw = sum over chunks in order.
 __global__ void __launch_bounds__(256) backward_reduce_kernel(const float* partial, int chunks,
                                                               int64_t total, float* dw) {
@@ -382,6 +516,23 @@ cudaError_t launch_backward(const LayerArgs& La, const float* dsigma, int half_o
   *nkernels = 0;
   if (La.F_h <= 0) return cudaSuccess;
   const int CW = La.c_out * La.c_w;
+  const int kk = La.kh * La.kw;
+  if (La.sh == 1 && La.sw == 1 && kk <= 25 && chunks <= 65535) {
+    // fused: G never leaves registers
+    const int chunk = (La.F_h + chunks - 1) / chunks;
+    const int nch = (La.F_h + chunk - 1) / chunk;
+    dim3 grid((La.c_in + 63) / 64, (La.c_out + 15) / 16, nch);
+    if (kk <= 1) backward_fused_kernel<1><<<grid, 256, 0, s>>>(La, dsigma, half_output, U, V, chunk, partial);
+    else if (kk <= 9) backward_fused_kernel<9><<<grid, 256, 0, s>>>(La, dsigma, half_output, U, V, chunk, partial);
+    else backward_fused_kernel<25><<<grid, 256, 0, s>>>(La, dsigma, half_output, U, V, chunk, partial);
+    ++*nkernels;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t total = (int64_t)CW * kk;
+    backward_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(partial, nch, total, dw);
+    ++*nkernels;
+    return cudaGetLastError();
+  }
   const int chunk = (La.F_h + chunks - 1) / chunks;
   chunks = (La.F_h + chunk - 1) / chunk;
   int per_block = (int)(g_cap / chunk) < 1 ? 1 : (int)(g_cap / chunk);
@@ -414,16 +565,23 @@ cudaError_t launch_backward(const LayerArgs& La, const float* dsigma, int half_o
 
 // ----------------------------------------------------------------------------- regulariser
 // loss = max(sigma) + lam * sum (sigma - 1)^2; dsigma = 2 lam (sigma - 1) + [first argmax].
-// One CTA of 1024 threads per layer; fixed-order tree reductions (deterministic).
-__global__ void __launch_bounds__(1024) regulariser_kernel(const float* sigma, int64_t count, float lam,
-                                                           float* dsigma, float* loss) {
-  __shared__ float smax[32];
-  __shared__ long long sidx[32];
-  __shared__ float ssum[32];
+// Pass 1: kRegBlocks CTAs write dsigma = 2 lam (sigma - 1) and one (max, first argmax, sum) per
+// CTA over a contiguous slice; pass 2: one warp combines the partials in CTA order and adds the
+// 1 at the argmax. Fixed-order reductions throughout (deterministic).
+constexpr int kRegBlocks = 64;
+
+__global__ void __launch_bounds__(256) regulariser_partial_kernel(const float* sigma, int64_t count, float lam,
+                                                                  float* dsigma, float* pmax, long long* parg,
+                                                                  float* psum) {
+  __shared__ float smax[8];
+  __shared__ long long sidx[8];
+  __shared__ float ssum[8];
+  const int64_t per = (count + gridDim.x - 1) / gridDim.x;
+  const int64_t e0 = (int64_t)blockIdx.x * per, e1 = e0 + per < count ? e0 + per : count;
   float best = -1.f;
   long long bi = 0x7fffffffffffffffll;
   float sum = 0.f;
-  for (int64_t e = threadIdx.x; e < count; e += blockDim.x) {
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const float v = sigma[e];
     if (v > best) { best = v; bi = e; }
     const float d = v - 1.f;
@@ -440,21 +598,51 @@ __global__ void __launch_bounds__(1024) regulariser_kernel(const float* sigma, i
   if ((threadIdx.x & 31) == 0) { smax[w] = best; sidx[w] = bi; ssum[w] = sum; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    float b = -1.f, s = 0.f;
-    long long ix = 0;
+    float b = -1.f, t = 0.f;
+    long long ix = 0x7fffffffffffffffll;
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
       if (smax[i] > b || (smax[i] == b && sidx[i] < ix)) { b = smax[i]; ix = sidx[i]; }
-      s += ssum[i];
+      t += ssum[i];
     }
-    if (count > 0) dsigma[ix] += 1.f;
-    if (loss) *loss = b + lam * s;
+    pmax[blockIdx.x] = b;
+    parg[blockIdx.x] = ix;
+    psum[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(32) regulariser_final_kernel(const float* pmax, const long long* parg,
+                                                               const float* psum, int parts, int64_t count,
+                                                               float lam, float* dsigma, float* loss) {
+  // lane k combines parts k, k + 32, ... in order, then a fixed butterfly: deterministic
+  const int lane = threadIdx.x;
+  float b = -1.f, t = 0.f;
+  long long ix = 0x7fffffffffffffffll;
+  for (int i = lane; i < parts; i += 32) {
+    if (pmax[i] > b || (pmax[i] == b && parg[i] < ix)) { b = pmax[i]; ix = parg[i]; }
+    t += psum[i];
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const float ob = __shfl_xor_sync(0xffffffffu, b, off);
+    const long long oi = __shfl_xor_sync(0xffffffffu, ix, off);
+    if (ob > b || (ob == b && oi < ix)) { b = ob; ix = oi; }
+    t += __shfl_xor_sync(0xffffffffu, t, off);
+  }
+  if (lane == 0) {
+    if (ix >= 0 && ix < count) dsigma[ix] += 1.f;   // no index when every sigma is NaN
+    if (loss) *loss = b + lam * t;
   }
 }
 
 cudaError_t launch_regulariser(const LayerArgs& La, int half_output, const float* sigma, float lam,
-                               float* dsigma, float* loss, cudaStream_t s) {
+                               float* dsigma, float* loss, float* scratch, cudaStream_t s) {
   const int64_t count = (int64_t)(half_output ? La.F_h : La.n * La.m) * La.r;
-  regulariser_kernel<<<1, 1024, 0, s>>>(sigma, count, lam, dsigma, loss);
+  float* pmax = scratch;
+  float* psum = scratch + kRegBlocks;
+  long long* parg = reinterpret_cast<long long*>(scratch + 2 * kRegBlocks);
+  regulariser_partial_kernel<<<kRegBlocks, 256, 0, s>>>(sigma, count, lam, dsigma, pmax, parg, psum);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  regulariser_final_kernel<<<1, 32, 0, s>>>(pmax, parg, psum, kRegBlocks, count, lam, dsigma, loss);
   return cudaGetLastError();
 }
 

@@ -211,6 +211,7 @@ struct lfa_plan_s {
   int64_t g_cap_bytes = 0;
   float* partial_ws = nullptr;
   float* edit_ws = nullptr;                 // phi(sigma) / (n m) of one layer (spectral editing)
+  float* reg_ws = nullptr;                  // per-CTA partials of the regulariser
   std::vector<int> bw_chunks;      // per layer
   // graph cache
   cudaStream_t cap_stream = nullptr;
@@ -479,6 +480,8 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
       int64_t chunk = std::min<int64_t>((La.F_h + chunks - 1) / chunks, 65535);
       chunks = (La.F_h + chunk - 1) / chunk;
       g_bytes = std::max(g_bytes, (size_t)(chunk * CC * 8));
+      const int fused = fused_backward_chunks(La);   // the fused backward picks its own chunking
+      if (fused > 0) chunks = fused;
       p->bw_chunks[l] = (int)chunks;
       part_bytes = std::max(part_bytes, (size_t)(chunks * CC * La.kh * La.kw * 4));
     }
@@ -492,6 +495,7 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
       edit_bytes = std::max(edit_bytes, (size_t)(p->half_output ? p->args[l].F_h : p->args[l].n * p->args[l].m) *
                                             p->args[l].r * sizeof(float));
   const size_t off_edit = bytes; bytes += align256(edit_bytes);
+  const size_t off_reg = bytes; bytes += align256(kRegScratchBytes);
   const size_t off_log = bytes; bytes += align256(log_bytes);
   const size_t off_ranks = bytes; bytes += align256(ranks_bytes);
   const size_t off_rounds = bytes; bytes += align256(rounds_bytes);
@@ -507,6 +511,7 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
   p->g_cap_bytes = (int64_t)g_bytes;
   p->partial_ws = part_bytes ? reinterpret_cast<float*>(base + off_part) : nullptr;
   p->edit_ws = edit_bytes ? reinterpret_cast<float*>(base + off_edit) : nullptr;
+  p->reg_ws = reinterpret_cast<float*>(base + off_reg);
   p->log_ws = log_bytes ? reinterpret_cast<float4*>(base + off_log) : nullptr;
   p->xraw_ws = ranks_bytes ? reinterpret_cast<float2*>(base + off_ranks) : nullptr;
   p->rounds_ws = rounds_bytes ? reinterpret_cast<int32_t*>(base + off_rounds) : nullptr;
@@ -695,8 +700,8 @@ lfa_status_t lfa_regulariser_grad(lfa_plan_t p, const float* const* sigma, float
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   for (int l = 0; l < p->nlayers; ++l) {
     LFA_CUDA_TRY(launch_regulariser(p->args[l], p->half_output, sigma[l], lam, dsigma[l],
-                                    loss ? loss[l] : nullptr, s));
-    g_launches += 1;
+                                    loss ? loss[l] : nullptr, p->reg_ws, s));
+    g_launches += 2;
   }
   return LFA_OK;
 }

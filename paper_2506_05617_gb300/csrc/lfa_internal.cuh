@@ -140,6 +140,8 @@ cudaError_t prepare_replay(int NP);   // kernel attributes, once per plan
 
 // Auxiliary kernels (aux_kernels.cu).
 cudaError_t launch_symbols(const LayerArgs& La, float2* out, cudaStream_t s);
+// chunk count of the fused backward (stride 1, at most 25 taps), or 0 when it does not apply
+int fused_backward_chunks(const LayerArgs& La);
 // unit vectors for the exactly zero columns of the X-side factors [symbols][M][N] of a layer
 cudaError_t launch_complete(const LayerArgs& La, float2* X, int symbols, cudaStream_t s);
 cudaError_t launch_expand(const LayerArgs& La, const float2* U, const float2* V, int64_t first,
@@ -149,7 +151,9 @@ cudaError_t launch_backward(const LayerArgs& La, const float* dsigma, int half_o
                             float* partial, int chunks, float* dw, cudaStream_t s, int* nkernels);
 cudaError_t launch_edit_values(const LayerArgs& La, int half_output, const float* sigma, int mode, float a,
                                float b, float* g, cudaStream_t s);
+// scratch: kRegScratchBytes of device memory for the per-CTA partials (plan-owned)
+constexpr size_t kRegScratchBytes = 1024;
 cudaError_t launch_regulariser(const LayerArgs& La, int half_output, const float* sigma, float lam,
-                               float* dsigma, float* loss, cudaStream_t s);
+                               float* dsigma, float* loss, float* scratch, cudaStream_t s);
 
 }  // namespace lfa
