@@ -103,10 +103,15 @@ typedef struct lfa_options {
                            max(2^-22, 4 sqrt(M) 2^-24), M = max(c_out, c_in) */
   int32_t max_sweeps;   /* sweep cap per symbol; <= 0: default 30 */
   int32_t variant;      /* -1: built-in / autotuned choice; >= 0 forces a kernel variant
-                           (see lfa_variant_name) for every layer it can run */
+                           (see lfa_variant_name) for every layer it can run;
+                           LFA_VARIANT_LOGGED | v (plans with LFA_VECTORS) runs values-mode
+                           variant v with the rotation log, the W replay and the finalize
+                           kernel instead of carrying W in registers */
   int32_t use_graph;    /* 1 (default if <0): lfa_svd replays a captured CUDA graph */
   const char* tune_cache; /* nullable path of the autotuner's cache (text); read at plan time */
 } lfa_options_t;
+
+#define LFA_VARIANT_LOGGED 0x10000
 
 typedef struct lfa_plan_s* lfa_plan_t;
 
@@ -251,7 +256,8 @@ lfa_status_t lfa_destroy(lfa_plan_t plan);
  * LFA_ERR_NOT_CONVERGED if a symbol hit max_sweeps, else LFA_OK. */
 lfa_status_t lfa_get_info(lfa_plan_t plan, lfa_info_t* info);
 
-/* Per-layer queries: half-grid size F_h, r, the kernel variant chosen, and the
+/* Per-layer queries: half-grid size F_h, r, the kernel variant chosen (with
+ * LFA_VARIANT_LOGGED set when the layer runs the rotation-log route), and the
  * half-grid frequency list (host int32 array of F_h entries, may be NULL). */
 lfa_status_t lfa_layer_query(lfa_plan_t plan, int32_t layer, int64_t* F_h, int32_t* r,
                              int32_t* variant, int32_t* half_grid);

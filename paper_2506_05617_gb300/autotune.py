@@ -26,9 +26,13 @@ def candidates(M: int, N: int, vectors: bool) -> List[int]:
     out = []
     for v in range(C.lfa_debug_variant_count()):
         npairs, lanes, mr, wr, cs, ppt = (int(x) for x in re.findall(r"\d+", C.lfa_variant_name(v)))
-        if M > mr * lanes or N > 2 * npairs or (vectors and N > wr * lanes):
+        if M > mr * lanes or N > 2 * npairs:
             continue
-        out.append(v)
+        if not vectors or N <= wr * lanes:
+            out.append(v)
+        # vectors through the rotation log and the W replay (values-mode forward)
+        if vectors and ppt == 1 and npairs in (16, 32, 64, 128, 256) and npairs * lanes // cs >= 32 and N <= 512:
+            out.append(v | C.LFA_VARIANT_LOGGED)
     return out
 
 
@@ -94,10 +98,11 @@ def write_cache(path: str, best: Dict[Tuple[int, int, int], Tuple[int, float]]):
     if os.path.exists(path):
         for line in open(path):
             parts = line.split("#")[0].split()
-            if len(parts) == 4:
+            if len(parts) in (4, 5):
                 old[tuple(int(x) for x in parts[:3])] = line.rstrip("\n")
     for (M, N, vec), (v, ms) in best.items():
-        old[(M, N, vec)] = f"{M} {N} {vec} {v}  # {C.lfa_variant_name(v)} {ms:.3f} ms"
+        route = f"{v & (C.LFA_VARIANT_LOGGED - 1)} log" if v & C.LFA_VARIANT_LOGGED else f"{v}"
+        old[(M, N, vec)] = f"{M} {N} {vec} {route}  # {C.lfa_variant_name(v)} {ms:.3f} ms"
     with open(path, "w") as fh:
         fh.write("# LFA Jacobi variant cache: M N vectors variant  (written by paper_2506_05617_gb300.autotune)\n")
         for k in sorted(old):

@@ -333,8 +333,8 @@ __device__ __forceinline__ float2 w_at(const Planes<C>& a, int s) {
 template <class C, bool FUSED, bool LOG = false>
 __global__ void __launch_bounds__(C::BLOCK, C::MINB)
 jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
-  static_assert(!LOG || (!C::VEC && C::CS > 1 && C::PPT == 1),
-                "the rotation log serves values-mode cluster variants");
+  static_assert(!LOG || (!C::VEC && C::PPT == 1 && C::SPU == 1),
+                "the rotation log serves values-mode variants with one symbol per unit");
   constexpr int NP = C::NP, L = C::L, MR = C::MR, WR = C::WR, TC = C::TC, NC = C::NC;
   constexpr int TPC = C::TPC, CS = C::CS, RS = C::RS, PPT = C::PPT;
   constexpr int NCOL = 2 * PPT;   // columns a thread holds rows of

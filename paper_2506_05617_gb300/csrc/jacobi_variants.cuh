@@ -140,18 +140,18 @@ cudaError_t jacobi_grid_t(int sms, int* grid) {
     if constexpr (OK) return jacobi_grid_t<NP, L, MR, WR, CS, MB, PPT, true, true>(sms, g);   \
     else return cudaErrorInvalidValue;
 
-// the rotation-logging forward exists for the values-mode cluster variants only
+// the rotation-logging forward exists for values-mode variants with one symbol per unit
 #define LFA_CASE_LAUNCH_log_log(id, NP, L, MR, WR, CS, OK, MB, PPT)                                         \
   case id:                                                                                           \
-    if constexpr (CS > 1 && PPT == 1) return jacobi_launch_t<NP, L, MR, WR, CS, MB, PPT, false, true, true>(P, grid, s); \
+    if constexpr (PPT == 1 && NP * L / CS >= 32) return jacobi_launch_t<NP, L, MR, WR, CS, MB, PPT, false, true, true>(P, grid, s); \
     else return cudaErrorInvalidValue;
 #define LFA_CASE_PREPARE_log_log(id, NP, L, MR, WR, CS, OK, MB, PPT)                              \
   case id:                                                                                 \
-    if constexpr (CS > 1 && PPT == 1) return jacobi_prepare_t<NP, L, MR, WR, CS, MB, PPT, false, true, true>(); \
+    if constexpr (PPT == 1 && NP * L / CS >= 32) return jacobi_prepare_t<NP, L, MR, WR, CS, MB, PPT, false, true, true>(); \
     else return cudaErrorInvalidValue;
 #define LFA_CASE_GRID_log_log(id, NP, L, MR, WR, CS, OK, MB, PPT)                                     \
   case id:                                                                                     \
-    if constexpr (CS > 1 && PPT == 1) return jacobi_grid_t<NP, L, MR, WR, CS, MB, PPT, false, true, true>(sms, g); \
+    if constexpr (PPT == 1 && NP * L / CS >= 32) return jacobi_grid_t<NP, L, MR, WR, CS, MB, PPT, false, true, true>(sms, g); \
     else return cudaErrorInvalidValue;
 
 cudaError_t jacobi_val_log_launch(int id, const JacobiLaunch& P, int grid, cudaStream_t s);

@@ -159,21 +159,33 @@ int variant_spu(int id) {
 }
 int variant_cs(int id) { return kVariants[id].CS; }
 
-// Optional autotuner cache: text lines "M N vec variant" (first match wins).
+// The rotation-log route for vectors: values-mode variant v logs its rotations, W is replayed.
+bool logged_ok(int v, int M, int N) {
+  return variant_fits(v, M, N, false) && kVariants[v].PPT == 1 && replay_supported(kVariants[v].NP) &&
+         kVariants[v].NP * kVariants[v].L / kVariants[v].CS >= 32 && N <= 512;
+}
+
+// Optional autotuner cache: text lines "M N vec variant [log]" (first match wins); "log" marks
+// the rotation-log route (returned as variant | LFA_VARIANT_LOGGED).
 int tuned_variant(const char* path, int M, int N, bool vec) {
   if (path == nullptr || path[0] == 0) return -1;
   FILE* fh = std::fopen(path, "r");
   if (!fh) return -1;
   int m, n, v, id, found = -1;
-  char line[256];
+  char line[256], word[16];
+  bool log = false;
   while (std::fgets(line, sizeof line, fh)) {
     if (line[0] == '#') continue;
-    if (std::sscanf(line, "%d %d %d %d", &m, &n, &v, &id) == 4 && m == M && n == N && (v != 0) == vec) {
+    word[0] = 0;
+    const int got = std::sscanf(line, "%d %d %d %d %15s", &m, &n, &v, &id, word);
+    if (got >= 4 && m == M && n == N && (v != 0) == vec) {
       found = id;
+      log = got == 5 && std::strcmp(word, "log") == 0;
       break;
     }
   }
   std::fclose(fh);
+  if (log) return vec && logged_ok(found, M, N) ? (found | LFA_VARIANT_LOGGED) : -1;
   return variant_fits(found, M, N, vec) ? found : -1;
 }
 
@@ -429,15 +441,24 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
     const float tol = p->tol_opt > 0.f ? p->tol_opt : default_tol(La.M);
     La.tol2 = tol * tol;
     int v = -1;
-    if (opt && opt->variant >= 0 && variant_fits(opt->variant, La.M, La.N, p->vec)) v = opt->variant;
-    if (v < 0) v = tuned_variant(opt ? opt->tune_cache : nullptr, La.M, La.N, p->vec);
-    if (v < 0) v = choose_variant(La.M, La.N, p->vec);
     bool logged = false;
-    if (v < 0 && p->vec && !p->plain) {
-      // W does not fit registers next to X: values-mode cluster variant + rotation log + replay
+    const bool can_log = p->vec && !p->plain;
+    // a requested (option, then autotuner cache) variant, possibly with the rotation-log route
+    const int requested[2] = {opt ? opt->variant : -1, tuned_variant(opt ? opt->tune_cache : nullptr, La.M, La.N, p->vec)};
+    for (int rq : requested) {
+      if (v >= 0 || rq < 0) continue;
+      if (rq & LFA_VARIANT_LOGGED) {
+        const int id = rq & (LFA_VARIANT_LOGGED - 1);
+        if (can_log && id < kNumVariants && logged_ok(id, La.M, La.N)) { v = id; logged = true; }
+      } else if (variant_fits(rq, La.M, La.N, p->vec)) {
+        v = rq;
+      }
+    }
+    if (v < 0) v = choose_variant(La.M, La.N, p->vec);
+    if (v < 0 && can_log) {
+      // W does not fit registers next to X: values-mode variant + rotation log + replay
       v = choose_variant(La.M, La.N, false);
-      if (v >= 0 && kVariants[v].CS > 1 && kVariants[v].PPT == 1 && (kVariants[v].NP == 128 || kVariants[v].NP == 256))
-        logged = true;
+      if (v >= 0 && logged_ok(v, La.M, La.N)) logged = true;
       else v = -1;
     }
     if (v < 0) { free_plan(p); return LFA_ERR_UNSUPPORTED; }
@@ -741,7 +762,11 @@ lfa_status_t lfa_layer_query(lfa_plan_t p, int32_t layer, int64_t* F_h, int32_t*
   if (p == nullptr || layer < 0 || layer >= p->nlayers) return LFA_ERR_INVALID_ARG;
   if (F_h) *F_h = p->args[layer].F_h;
   if (r) *r = p->args[layer].r;
-  if (variant) *variant = p->variant[layer];
+  if (variant) {
+    const bool logged = std::any_of(p->logged.begin(), p->logged.end(),
+                                    [layer](const lfa_plan_s::Logged& q) { return q.layer == layer; });
+    *variant = p->variant[layer] | (logged ? LFA_VARIANT_LOGGED : 0);
+  }
   if (half_grid) std::memcpy(half_grid, p->half_host[layer].data(), p->half_host[layer].size() * 4);
   return LFA_OK;
 }
@@ -761,6 +786,15 @@ const char* lfa_status_string(lfa_status_t s) {
 }
 
 const char* lfa_variant_name(int32_t v) {
+  static const std::vector<std::string> logged_names = [] {
+    std::vector<std::string> out;
+    for (int i = 0; i < kNumVariants; ++i) out.push_back(std::string(kVariantNames[i]) + "_log");
+    return out;
+  }();
+  if (v >= 0 && (v & LFA_VARIANT_LOGGED)) {
+    const int id = v & (LFA_VARIANT_LOGGED - 1);
+    return id < kNumVariants ? logged_names[id].c_str() : "none";
+  }
   if (v < 0 || v >= kNumVariants) return "none";
   return kVariantNames[v];
 }

@@ -137,6 +137,7 @@ struct ReplayArgs {
 };
 cudaError_t launch_replay(int NP, const ReplayArgs& R, int symbols, cudaStream_t s, int* nkernels);
 cudaError_t prepare_replay(int NP);   // kernel attributes, once per plan
+bool replay_supported(int NP);        // a replay configuration exists for NP pairs
 
 // Auxiliary kernels (aux_kernels.cu).
 cudaError_t launch_symbols(const LayerArgs& La, float2* out, cudaStream_t s);

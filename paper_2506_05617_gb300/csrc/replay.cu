@@ -1,6 +1,6 @@
 // Replay of a rotation log onto W = I: the right (or, for wide symbols, left) singular
 // vectors of symbols whose accumulated rotation matrix W does not fit in registers next to X
-// (512 columns). The forward kernel ran in values mode and logged, per round and team, the
+// (512 columns), or whose forward is faster without carrying W (the autotuner's choice). The forward kernel ran in values mode and logged, per round and team, the
 // rotation it applied; rotations act on columns, so the rows of W are independent and can be
 // rebuilt in row blocks by one CTA each, following the same round-robin schedule (the same
 // team movement and exchange as the forward kernel) with the logged parameters.
@@ -53,26 +53,36 @@ __global__ void __launch_bounds__(C::BLOCK) replay_kernel(const __grid_constant_
 
   const int T = R.rounds[slot];
   const float4* lg = R.log + (size_t)slot * R.log_cap * NP + team;
-  for (int t = 0; t < T; t += 2) {
-    // even round: teams move array 0, team 0 moves array 1
-    {
-      const float4 e = __ldg(lg + (size_t)t * NP);
-      if (e.x != 0.f || e.y != 0.f || e.z != 0.f) apply_rotation<C>(c0, c1, e);
+  // The log is read four rounds ahead (the rounds themselves have no other long-latency step).
+  // T is the same for every thread, so every break below is uniform and the barriers stay aligned.
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 cur[4], nxt[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) cur[k] = k < T ? __ldg(lg + (size_t)k * NP) : zero;
+  auto rotate = [&](const float4& e) {
+    if (e.x != 0.f || e.y != 0.f || e.z != 0.f) apply_rotation<C>(c0, c1, e);
+  };
+  for (int t = 0; t < T; t += 4) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) nxt[k] = t + 4 + k < T ? __ldg(lg + (size_t)(t + 4 + k) * NP) : zero;
+    // rounds t and t + 2 are even (teams move array 0, team 0 moves array 1), t + 1 and t + 3 odd
+#pragma unroll
+    for (int k = 0; k < 4; k += 2) {
+      if (t + k >= T) break;
+      rotate(cur[k]);
+      if (team == 0) put_column<C>(c1, id1, dst_e, dst_id_e, lane);
+      else put_column<C>(c0, id0, dst_e, dst_id_e, lane);
+      __syncthreads();
+      if (team == 0) get_column<C>(c1, id1, src_e, src_id_e, lane);
+      else get_column<C>(c0, id0, src_e, src_id_e, lane);
+      if (t + k + 1 >= T) break;
+      rotate(cur[k + 1]);
+      put_column<C>(c1, id1, dst_o, dst_id_o, lane);
+      __syncthreads();
+      get_column<C>(c1, id1, src_o, src_id_o, lane);
     }
-    if (team == 0) put_column<C>(c1, id1, dst_e, dst_id_e, lane);
-    else put_column<C>(c0, id0, dst_e, dst_id_e, lane);
-    __syncthreads();
-    if (team == 0) get_column<C>(c1, id1, src_e, src_id_e, lane);
-    else get_column<C>(c0, id0, src_e, src_id_e, lane);
-    if (t + 1 >= T) break;
-    // odd round: every team moves array 1
-    {
-      const float4 e = __ldg(lg + (size_t)(t + 1) * NP);
-      if (e.x != 0.f || e.y != 0.f || e.z != 0.f) apply_rotation<C>(c0, c1, e);
-    }
-    put_column<C>(c1, id1, dst_o, dst_id_o, lane);
-    __syncthreads();
-    get_column<C>(c1, id1, src_o, src_id_o, lane);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) cur[k] = nxt[k];
   }
 
   // the block's rows of the team's two columns, in column order
@@ -152,9 +162,15 @@ __global__ void __launch_bounds__(512) finalize_kernel(const __grid_constant__ R
   }
 }
 
-// 32-row blocks, two lanes per pair: 16 rows of each of the team's two columns per lane.
+// 32-row blocks: 16 rows of each of the team's two columns per lane on two lanes per pair (four
+// lanes of 8 rows for 16 pairs, so that every replay CTA has at least 32 threads, one unit).
 using ReplayC256 = JCfg<256, 2, 16, 1, false, 1>;
 using ReplayC128 = JCfg<128, 2, 16, 1, false, 1>;
+using ReplayC64 = JCfg<64, 2, 16, 1, false, 1>;
+using ReplayC32 = JCfg<32, 2, 16, 1, false, 1>;
+using ReplayC16 = JCfg<16, 4, 8, 1, false, 1>;
+static_assert(ReplayC16::XR == 32 && ReplayC32::XR == 32 && ReplayC16::SPU == 1 && ReplayC32::SPU == 1,
+              "replay blocks are 32 rows, one symbol per CTA");
 
 template <class C>
 static cudaError_t replay_t(const ReplayArgs& R, int symbols, cudaStream_t s) {
@@ -168,13 +184,21 @@ static cudaError_t replay_t(const ReplayArgs& R, int symbols, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <class C>
+static cudaError_t prepare_t() {
+  return cudaFuncSetAttribute(replay_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+}
+
+bool replay_supported(int NP) { return NP == 16 || NP == 32 || NP == 64 || NP == 128 || NP == 256; }
+
 cudaError_t prepare_replay(int NP) {
-  if (NP == 256)
-    return cudaFuncSetAttribute(replay_kernel<ReplayC256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)ReplayC256::SMEM);
-  if (NP == 128)
-    return cudaFuncSetAttribute(replay_kernel<ReplayC128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)ReplayC128::SMEM);
+  switch (NP) {
+    case 256: return prepare_t<ReplayC256>();
+    case 128: return prepare_t<ReplayC128>();
+    case 64: return prepare_t<ReplayC64>();
+    case 32: return prepare_t<ReplayC32>();
+    case 16: return prepare_t<ReplayC16>();
+  }
   return cudaErrorInvalidValue;
 }
 
@@ -182,8 +206,13 @@ cudaError_t launch_replay(int NP, const ReplayArgs& R, int symbols, cudaStream_t
   *nkernels = 2;
   if (symbols <= 0) return cudaSuccess;
   if (symbols > 65535 || R.La.N > 512) return cudaErrorInvalidValue;
-  if (NP == 256) return replay_t<ReplayC256>(R, symbols, s);
-  if (NP == 128) return replay_t<ReplayC128>(R, symbols, s);
+  switch (NP) {
+    case 256: return replay_t<ReplayC256>(R, symbols, s);
+    case 128: return replay_t<ReplayC128>(R, symbols, s);
+    case 64: return replay_t<ReplayC64>(R, symbols, s);
+    case 32: return replay_t<ReplayC32>(R, symbols, s);
+    case 16: return replay_t<ReplayC16>(R, symbols, s);
+  }
   return cudaErrorInvalidValue;
 }
 

@@ -24,6 +24,7 @@ LFA_VALUES = 0x1
 LFA_VECTORS = 0x2
 LFA_HALF_OUTPUT = 0x4
 LFA_PLAIN = 0x8
+LFA_VARIANT_LOGGED = 0x10000   # options.variant flag: values variant + rotation log + W replay
 
 # spectral editing modes
 LFA_EDIT_CLIP = 0

@@ -50,3 +50,29 @@ def test_forced_variant_matches_oracle(v, vectors):
     if vectors:
         check_vectors(w, n, m, s, U, V)
     plan.close()
+
+
+def logged_variants():
+    out = []
+    for v in range(C.lfa_debug_variant_count()):
+        npairs, lanes, mr, wr, cs, ppt = (int(x) for x in re.findall(r"\d+", C.lfa_variant_name(v)))
+        if ppt == 1 and npairs in (16, 32, 64, 128, 256) and npairs * lanes // cs >= 32:
+            out.append(v)
+    return out
+
+
+@pytest.mark.parametrize("v", logged_variants(), ids=lambda v: C.lfa_variant_name(v) + "_log")
+def test_forced_rotation_log_route_matches_oracle(v):
+    """Vectors through the values-mode forward with the rotation log, the W replay, the finalize
+    and the zero-column completion, forced on every variant that has a replay configuration."""
+    c_out, c_in = shape_for(v, vectors=False)
+    c_in = min(c_in, 512)
+    n, m = 3, 2
+    w = rand_w(c_out, c_in, 3, 3, seed=200 + v)
+    plan, (s, U, V), st, info = gpu_svd(w, n, m, vectors=True, variant=v | C.LFA_VARIANT_LOGGED)
+    assert plan.meta[0]["variant"] == v | C.LFA_VARIANT_LOGGED, plan.meta[0]
+    assert st == C.LFA_OK, info
+    check_sigma(w, n, m, s)
+    assert np.all(np.diff(s, axis=1) <= 0)
+    check_vectors(w, n, m, s, U, V)
+    plan.close()
