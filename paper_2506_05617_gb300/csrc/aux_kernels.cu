@@ -421,13 +421,13 @@ __global__ void __launch_bounds__(256) backward_fused_kernel(LayerArgs La, const
   const int o0 = blockIdx.y * TO, i0 = blockIdx.x * TI;
   const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;   // entries (o0 + ty + 4 q, i0 + tx), q < 4
   const int c = blockIdx.z;
-  float acc[4][KK];
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-#pragma unroll
-    for (int t = 0; t < KK; ++t) acc[q][t] = 0.f;
   const int h0 = c * chunk, h1 = min(La.F_h, h0 + chunk);
-  for (int h = h0; h < h1; ++h) {
+  const int nsc = (r + 31) / 32;                            // s-chunks per frequency
+  const int iters = (h1 > h0 ? h1 - h0 : 0) * nsc;
+  // staged tile of one (frequency, s-chunk): thread rows e = threadIdx.x + 256 k, s = e & 31
+  float2 ur[2], vr[8];
+  auto fetch = [&](int it) {
+    const int h = h0 + it / nsc, s0 = (it % nsc) * 32;
     const int f = La.half[h];
     const int j = f / La.m, l = f - j * La.m;
     const int fc = ((La.n - j) % La.n) * La.m + (La.m - l) % La.m;
@@ -435,45 +435,70 @@ __global__ void __launch_bounds__(256) backward_fused_kernel(LayerArgs La, const
     const float* g_c = (!half_output && fc != f) ? dsigma + (size_t)fc * r : nullptr;
     const float2* Uh = U + (size_t)h * co * r;
     const float2* Vh = V + (size_t)h * ci * r;
-    __syncthreads();                                       // the previous frequency is consumed
-    if (threadIdx.x < kk) sph[threadIdx.x] = tap_phase(La, j, l, threadIdx.x / La.kw, threadIdx.x % La.kw);
-    float2 g[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) g[q] = make_float2(0.f, 0.f);
-    for (int s0 = 0; s0 < r; s0 += 32) {
-      for (int e = threadIdx.x; e < TO * 32; e += 256) {
-        const int row = e >> 5, ss = e & 31, sg = s0 + ss;
-        float2 u = make_float2(0.f, 0.f);
-        if (sg < r && o0 + row < co) {
-          const float gs = g_f[sg] + (g_c ? g_c[sg] : 0.f);
-          u = Uh[(size_t)(o0 + row) * r + sg];
-          u = make_float2(u.x * gs, u.y * gs);
-        }
-        Us[row][ss] = u;
+    for (int k = 0; k < 2; ++k) {
+      const int e = threadIdx.x + 256 * k, row = e >> 5, sg = s0 + (e & 31);
+      float2 u = make_float2(0.f, 0.f);
+      if (sg < r && o0 + row < co) {
+        const float gs = g_f[sg] + (g_c ? g_c[sg] : 0.f);
+        u = Uh[(size_t)(o0 + row) * r + sg];
+        u = make_float2(u.x * gs, u.y * gs);
       }
-      for (int e = threadIdx.x; e < TI * 32; e += 256) {
-        const int row = e >> 5, ss = e & 31, sg = s0 + ss;
-        Vs[row][ss] = (sg < r && i0 + row < ci) ? Vh[(size_t)(i0 + row) * r + sg] : make_float2(0.f, 0.f);
-      }
-      __syncthreads();
-#pragma unroll 8
-      for (int ss = 0; ss < 32; ++ss) {
-        const float2 v = Vs[tx][ss];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {                     // g += u conj(v)
-          const float2 u = Us[ty + 4 * q][ss];
-          g[q].x = fmaf(u.x, v.x, fmaf(u.y, v.y, g[q].x));
-          g[q].y = fmaf(u.y, v.x, fmaf(-u.x, v.y, g[q].y));
-        }
-      }
-      __syncthreads();
+      ur[k] = u;
     }
 #pragma unroll
-    for (int t = 0; t < KK; ++t) {
-      if (t < kk) {
-        const float2 p = sph[t];
+    for (int k = 0; k < 8; ++k) {
+      const int e = threadIdx.x + 256 * k, row = e >> 5, sg = s0 + (e & 31);
+      vr[k] = (sg < r && i0 + row < ci) ? Vh[(size_t)(i0 + row) * r + sg] : make_float2(0.f, 0.f);
+    }
+  };
+  float acc[4][KK];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q][t] = fmaf(g[q].x, p.x, fmaf(g[q].y, p.y, acc[q][t]));   // Re(g conj(p))
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int t = 0; t < KK; ++t) acc[q][t] = 0.f;
+  float2 g[4];
+  if (iters > 0) fetch(0);
+  for (int it = 0; it < iters; ++it) {
+    const int hh = h0 + it / nsc, sc = it % nsc;
+    __syncthreads();                                       // the previous tile (and phases) are consumed
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int e = threadIdx.x + 256 * k;
+      Us[e >> 5][e & 31] = ur[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int e = threadIdx.x + 256 * k;
+      Vs[e >> 5][e & 31] = vr[k];
+    }
+    if (sc == 0) {
+      const int f = La.half[hh];
+      const int j = f / La.m, l = f - j * La.m;
+      if (threadIdx.x < kk) sph[threadIdx.x] = tap_phase(La, j, l, threadIdx.x / La.kw, threadIdx.x % La.kw);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) g[q] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    if (it + 1 < iters) fetch(it + 1);                     // the next tile's loads overlap this tile's math
+#pragma unroll 8
+    for (int ss = 0; ss < 32; ++ss) {
+      const float2 v = Vs[tx][ss];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {                       // g += u conj(v)
+        const float2 u = Us[ty + 4 * q][ss];
+        g[q].x = fmaf(u.x, v.x, fmaf(u.y, v.y, g[q].x));
+        g[q].y = fmaf(u.y, v.x, fmaf(-u.x, v.y, g[q].y));
+      }
+    }
+    if (sc == nsc - 1) {
+#pragma unroll
+      for (int t = 0; t < KK; ++t) {
+        if (t < kk) {
+          const float2 p = sph[t];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[q][t] = fmaf(g[q].x, p.x, fmaf(g[q].y, p.y, acc[q][t]));   // Re(g conj(p))
+        }
       }
     }
   }
