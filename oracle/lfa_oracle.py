@@ -49,7 +49,7 @@ __all__ = [
     "origin", "dense_operator", "dense_svd", "symbols", "fft_symbols", "lfa_svd",
     "lift", "apply_operator", "apply_adjoint", "half_grid", "lfa_backward",
     "regulariser_loss", "regulariser_grad_sigma", "folded_kernel", "edit_values",
-    "spectral_edit", "dense_spectral_edit", "dense_operator_strided", "symbols_strided",
+    "spectral_edit", "dense_spectral_edit", "pinv_projection", "dense_pinv_projection", "dense_operator_strided", "symbols_strided",
     "lfa_svd_strided", "lfa_backward_strided", "lift_strided", "dense_operator_dirichlet",
 ]
 
@@ -327,6 +327,40 @@ def dense_spectral_edit(w, n: int, m: int, mode: str, a: float, b: float = 0.0, 
         basis[idx] = 1.0
         T = dense_operator(basis, n, m, pad_h, pad_w)
         out[idx] = np.real(np.sum(B * T)) / np.sum(T * T)
+        basis[idx] = 0.0
+    return out
+
+
+def pinv_projection(w, n: int, m: int, a: float, pad_h: int = -1, pad_w: int = -1):
+    """The kh x kw kernel [c_in, c_out, kh, kw] of a c_out -> c_in convolution nearest to the
+    pseudo-inverse A^+ of the layer (singular values <= a treated as zero), the pseudo-inverse
+    application of Sec. II. A^+ has the symbols B_k = V_k S_k^+ U_k^* (same Fourier modes), so the
+    projection is the formula of ``spectral_edit`` with the roles of U and V exchanged:
+        w'[i,o,a,b] = (1/(n m)) sum_k Re(B_k[i,o] exp(-2 pi i <k, y_ab>)).
+    """
+    w = np.asarray(w, dtype=np.float64)
+    s, U, V = lfa_svd(w, n, m, pad_h, pad_w)
+    inv = np.where(s > a, 1.0 / np.where(s > a, s, 1.0), 0.0)
+    shape_t = np.zeros((w.shape[1], w.shape[0], w.shape[2], w.shape[3]))
+    return lfa_backward(shape_t, n, m, inv / (n * m), V, U, pad_h, pad_w)
+
+
+def dense_pinv_projection(w, n: int, m: int, a: float, pad_h: int = -1, pad_w: int = -1):
+    """The same kernel from the dense operator: LAPACK pseudo-inverse of the unrolled matrix
+    (values <= a dropped), then <A^+, T> / <T, T> for the tap operators T of a c_out -> c_in
+    convolution built entry by entry (small sizes only). Independent of the symbols."""
+    w = np.asarray(w, dtype=np.float64)
+    c_out, c_in, kh, kw = w.shape
+    A = dense_operator(w, n, m, pad_h, pad_w)
+    Uu, sv, Vh = np.linalg.svd(A, full_matrices=False)
+    keep = sv > a
+    B = (Vh[keep].T / sv[keep]) @ Uu[:, keep].T                    # [c_in n m, c_out n m]
+    out = np.zeros((c_in, c_out, kh, kw))
+    basis = np.zeros_like(out)
+    for idx in np.ndindex(out.shape):
+        basis[idx] = 1.0
+        T = dense_operator(basis, n, m, pad_h, pad_w)
+        out[idx] = np.sum(B * T) / np.sum(T * T)
         basis[idx] = 0.0
     return out
 

@@ -424,3 +424,22 @@ def test_dirichlet_spectrum_interlaces_the_periodic_one_on_the_padded_torus(n, m
 def test_dirichlet_equals_periodic_for_1x1_kernels():
     w = rand_w(4, 3, 1, 1, 63)
     np.testing.assert_allclose(O.dense_operator_dirichlet(w, 4, 5), O.dense_operator(w, 4, 5), atol=0)
+
+
+# ----------------------------------------------------------------- pseudo-inverse projected on taps
+@pytest.mark.parametrize("c_out,c_in,k,n,m,a", [(3, 2, 3, 4, 5, 0.0), (2, 3, 3, 5, 4, 0.0), (3, 3, 3, 4, 4, 0.3)])
+def test_pinv_projection_matches_the_dense_pseudo_inverse(c_out, c_in, k, n, m, a):
+    w = rand_w(c_out, c_in, k, k, 71)
+    got = O.pinv_projection(w, n, m, a)
+    ref = O.dense_pinv_projection(w, n, m, a)
+    assert got.shape == (c_in, c_out, k, k)
+    np.testing.assert_allclose(got, ref, atol=1e-10 * np.max(np.abs(ref)))
+
+
+def test_pinv_of_a_scaled_identity_kernel_is_exact():
+    """w = 2 delta I: the operator is 2 Id, its inverse 0.5 Id, itself a 3x3 kernel."""
+    w = np.zeros((3, 3, 3, 3))
+    w[:, :, 1, 1] = 2.0 * np.eye(3)
+    ref = np.zeros_like(w)
+    ref[:, :, 1, 1] = 0.5 * np.eye(3)
+    np.testing.assert_allclose(O.pinv_projection(w, 4, 5, 0.0), ref, atol=1e-14)
