@@ -195,6 +195,8 @@ lfa_status_t lfa_svd_backward(lfa_plan_t plan, const float* const* dsigma, const
 #define LFA_EDIT_CLAMP      1  /* phi(s) = min(max(s, a), b) */
 #define LFA_EDIT_THRESHOLD  2  /* phi(s) = s if s >= a else 0 (hard threshold; a global low rank) */
 #define LFA_EDIT_RANK       3  /* keep the first round(a) singular values of every frequency */
+#define LFA_EDIT_PINV       4  /* the pseudo-inverse: phi(s) = 1/s for s > a, else 0, with the
+                                  roles of U and V exchanged (a c_out -> c_in convolution) */
 
 /* Spectral editing: the applications the paper motivates (Sec. I-II: spectral-norm
  * regularisation, low-rank compression) edit the singular values of the operator. This
@@ -205,8 +207,12 @@ lfa_status_t lfa_svd_backward(lfa_plan_t plan, const float* const* dsigma, const
  * kh <= n and kw <= m). When the kernel covers the torus (kh = n, kw = m) the edit is exact.
  *  sigma[l], U[l], V[l]  the layer's lfa_svd outputs (plan with LFA_VECTORS)
  *  mode, a, b            LFA_EDIT_* and its parameters
- *  w_out[l]              device float32 [c_out][c_in][kh][kw], overwritten
- * Uses the plan's backward workspace; deterministic; asynchronous. Errors: LFA_ERR_INVALID_ARG. */
+ *  w_out[l]              device float32 [c_out][c_in][kh][kw], overwritten; with LFA_EDIT_PINV
+ *                        [c_in][c_out][kh][kw]: the kernel of a c_out -> c_in convolution nearest
+ *                        to the pseudo-inverse A^+ (symbols V_k S_k^+ U_k^*; the paper's
+ *                        pseudo-inverse application, Sec. II), taps at the same offsets y_ab
+ * Uses the plan's backward workspace; deterministic; asynchronous. Errors: LFA_ERR_INVALID_ARG,
+ * LFA_ERR_UNSUPPORTED (LFA_EDIT_PINV on a strided layer). */
 lfa_status_t lfa_spectral_edit(lfa_plan_t plan, const float* const* sigma, const float* const* U,
                                const float* const* V, int32_t mode, float a, float b,
                                float* const* w_out, void* stream);

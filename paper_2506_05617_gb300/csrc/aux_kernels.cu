@@ -691,7 +691,8 @@ __global__ void __launch_bounds__(256) edit_values_kernel(LayerArgs La, int half
   if (mode == 0) p = fminf(v, a);
   else if (mode == 1) p = fminf(fmaxf(v, a), b);
   else if (mode == 2) p = v >= a ? v : 0.f;
-  else p = (float)s < rintf(a) ? v : 0.f;
+  else if (mode == 3) p = (float)s < rintf(a) ? v : 0.f;
+  else p = v > a ? 1.f / v : 0.f;   // pseudo-inverse (correctly rounded reciprocal)
   float mult = 1.f;
   if (half_output) {
     const int f = La.half[row];

@@ -695,18 +695,28 @@ lfa_status_t lfa_spectral_edit(lfa_plan_t p, const float* const* sigma, const fl
                                void* stream) {
   if (p == nullptr || !p->vec || sigma == nullptr || U == nullptr || V == nullptr || w_out == nullptr)
     return LFA_ERR_INVALID_ARG;
-  if (mode < LFA_EDIT_CLIP || mode > LFA_EDIT_RANK || !std::isfinite(a) || !std::isfinite(b)) return LFA_ERR_INVALID_ARG;
-  for (int l = 0; l < p->nlayers; ++l)
+  if (mode < LFA_EDIT_CLIP || mode > LFA_EDIT_PINV || !std::isfinite(a) || !std::isfinite(b)) return LFA_ERR_INVALID_ARG;
+  for (int l = 0; l < p->nlayers; ++l) {
     if (!sigma[l] || !U[l] || !V[l] || !w_out[l]) return LFA_ERR_INVALID_ARG;
+    if (mode == LFA_EDIT_PINV && (p->args[l].sh != 1 || p->args[l].sw != 1)) return LFA_ERR_UNSUPPORTED;
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   for (int l = 0; l < p->nlayers; ++l) {
-    const LayerArgs& La = p->args[l];
+    LayerArgs La = p->args[l];
+    const float2* Ul = reinterpret_cast<const float2*>(U[l]);
+    const float2* Vl = reinterpret_cast<const float2*>(V[l]);
     LFA_CUDA_TRY(launch_edit_values(La, p->half_output, sigma[l], mode, a, b, p->edit_ws, s));
+    if (mode == LFA_EDIT_PINV) {
+      // A^+ has the symbols V S^+ U^*: the backward of the transposed layer, U and V exchanged
+      std::swap(La.c_out, La.c_in);
+      La.c_w = La.c_in;
+      La.wide = La.c_in > La.c_out ? 1 : 0;
+      std::swap(Ul, Vl);
+    }
     const int64_t CC = (int64_t)La.c_out * La.c_in;
     const int64_t g_cap = p->g_cap_bytes / (CC * 8);
     int nk = 0;
-    LFA_CUDA_TRY(launch_backward(La, p->edit_ws, p->half_output, reinterpret_cast<const float2*>(U[l]),
-                                 reinterpret_cast<const float2*>(V[l]), p->g_ws, g_cap, p->partial_ws,
+    LFA_CUDA_TRY(launch_backward(La, p->edit_ws, p->half_output, Ul, Vl, p->g_ws, g_cap, p->partial_ws,
                                  p->bw_chunks[l], w_out[l], s, &nk));
     g_launches += 1 + nk;
   }

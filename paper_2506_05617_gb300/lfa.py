@@ -31,6 +31,7 @@ LFA_EDIT_CLIP = 0
 LFA_EDIT_CLAMP = 1
 LFA_EDIT_THRESHOLD = 2
 LFA_EDIT_RANK = 3
+LFA_EDIT_PINV = 4
 
 # status codes
 LFA_OK = 0

@@ -97,10 +97,14 @@ class LfaPlan:
         return dsigma, loss
 
     def spectral_edit(self, sigma, U, V, mode: str, a: float, b: float = 0.0, stream=None):
-        """Kernels nearest to the operators with edited singular values (see lfa_spectral_edit)."""
+        """Kernels nearest to the operators with edited singular values (see lfa_spectral_edit);
+        mode "pinv" returns [c_in, c_out, kh, kw] kernels nearest to the pseudo-inverses."""
         modes = {"clip": C.LFA_EDIT_CLIP, "clamp": C.LFA_EDIT_CLAMP, "threshold": C.LFA_EDIT_THRESHOLD,
-                 "rank": C.LFA_EDIT_RANK}
-        out = [torch.empty(self.layers[i][:4], dtype=torch.float32, device=U[0].device) for i in range(len(self.layers))]
+                 "rank": C.LFA_EDIT_RANK, "pinv": C.LFA_EDIT_PINV}
+        def shape(i):
+            c_out, c_in, kh, kw = self.layers[i][:4]
+            return (c_in, c_out, kh, kw) if mode == "pinv" else (c_out, c_in, kh, kw)
+        out = [torch.empty(shape(i), dtype=torch.float32, device=U[0].device) for i in range(len(self.layers))]
         stream = stream if stream is not None else torch.cuda.current_stream(U[0].device)
         C.lfa_spectral_edit(self.handle, [s.data_ptr() for s in sigma], [u.data_ptr() for u in U],
                             [v.data_ptr() for v in V], modes[mode], a, b, [o.data_ptr() for o in out], stream)

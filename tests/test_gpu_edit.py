@@ -70,3 +70,43 @@ def test_conv64_n32_clip_full_size():
     ref = O.spectral_edit(w, lay.n, lay.m, "clip", 1.0)
     assert np.linalg.norm(got - ref) <= 1e-4 * np.linalg.norm(ref)
     plan.close()
+
+
+@pytest.mark.parametrize("half", [False, True])
+@pytest.mark.parametrize("shape", [(4, 4, 3, 3, 8, 8), (6, 3, 3, 3, 5, 7), (3, 5, 5, 3, 6, 6), (16, 16, 3, 3, 8, 8)])
+def test_pseudo_inverse_projection_matches_oracle(shape, half):
+    """Kernel of the c_out -> c_in convolution nearest to the pseudo-inverse (values <= a dropped).
+    1/sigma amplifies the fp32 error of small values: the tolerance is 1e-4 * sigma_max / a."""
+    c_out, c_in, kh, kw, n, m = shape
+    w = rand_w(c_out, c_in, kh, kw, seed=53)
+    s_ref = O.lfa_svd(w, n, m, compute_uv=False)
+    v = np.sort(s_ref.ravel())
+    lo, hi = len(v) // 5, 3 * len(v) // 5
+    k = lo + int(np.argmax(np.diff(v[lo:hi])))
+    a = 0.5 * (v[k] + v[k + 1])
+    plan = LfaPlan([shape], vectors=True, half_output=half)
+    sig, U, V = plan.svd([torch.from_numpy(w).cuda()])
+    got = plan.spectral_edit(sig, U, V, "pinv", a)[0].cpu().numpy()
+    ref = O.pinv_projection(w, n, m, a)
+    assert got.shape == (c_in, c_out, kh, kw)
+    assert np.linalg.norm(got - ref) <= 1e-4 * (float(v[-1]) / a) * np.linalg.norm(ref)
+    plan.close()
+
+
+def test_pseudo_inverse_of_a_scaled_identity_is_exact_and_strided_layers_are_refused():
+    from paper_2506_05617_gb300 import lfa as C
+    w = np.zeros((5, 5, 3, 3), np.float32)
+    w[:, :, 1, 1] = 2.0 * np.eye(5)
+    plan = LfaPlan([(5, 5, 3, 3, 6, 4)], vectors=True)
+    sig, U, V = plan.svd([torch.from_numpy(w).cuda()])
+    got = plan.spectral_edit(sig, U, V, "pinv", 0.0)[0].cpu().numpy()
+    ref = np.zeros_like(w)
+    ref[:, :, 1, 1] = 0.5 * np.eye(5)
+    assert np.max(np.abs(got - ref)) <= 1e-6
+    plan.close()
+    plan = LfaPlan([(4, 2, 3, 3, 4, 4, -1, -1, 2, 2)], vectors=True)
+    sig, U, V = plan.svd([torch.from_numpy(rand_w(4, 2, 3, 3, seed=54)).cuda()])
+    with pytest.raises(C.LfaError) as ei:
+        plan.spectral_edit(sig, U, V, "pinv", 0.0)
+    assert ei.value.status == C.LFA_ERR_UNSUPPORTED
+    plan.close()
