@@ -43,6 +43,9 @@
  *    non-finite entry) are counted on the device and read by lfa_get_info().
  *  - No call aborts the process or raises; every failure is a status code.
  *  - A plan is not thread-safe: use one plan per host thread or serialise.
+ *  - The calls of one plan share its device workspace (counters, work queue, backward and
+ *    log buffers): calls issued on different streams must not overlap on the device. Use
+ *    one plan per concurrent stream (e.g. two plans for double-buffered pipelining).
  */
 #ifndef LFA_H_
 #define LFA_H_
