@@ -59,11 +59,14 @@ struct JCfg {
   static constexpr int MH = MR / 2;               // X row pairs per lane
   static constexpr int WH = (WR + 1) / 2;         // W row pairs per lane (last one half padding if WR odd)
   static constexpr int WRC = VEC ? 2 * WH * L : 0;  // W row capacity in the mailbox
-  // slot stride = L mod 16 (float2): neighbouring teams of a warp hit different banks
-  static constexpr int RS = XR + WRC + (((L - (XR + WRC)) % 16) + 16) % 16;
+  // slot stride = 2 L mod 16 (float2): a column moves as 16-byte (re, im) pairs, a shared-memory
+  // phase serves 8 lanes, so the L lanes of neighbouring teams must be L * 16 bytes apart mod 128
+  static constexpr int RS = XR + WRC + (((2 * L - (XR + WRC)) % 16) + 16) % 16;
+  static_assert(RS % 2 == 0, "mailbox slots start on 16-byte boundaries");
   static constexpr int MBOX = 2 * TPC * RS;       // [parity][team][RS] float2
   static constexpr size_t SYM_BYTES = (size_t)(MBOX + kMaxTaps) * 8 + NC * 4 + 2 * TPC * 4 + 64;
   static constexpr size_t UNIT_BYTES = SPU * SYM_BYTES + 64;
+  static_assert(SYM_BYTES % 16 == 0 && UNIT_BYTES % 16 == 0, "every symbol's mailbox is 16-byte aligned");
   static constexpr size_t SMEM = UPB * UNIT_BYTES;
   static constexpr int MINB = MINB_;   // resident CTAs per SM the register allocation aims for
   static_assert((size_t)NC * (XR + WRC) <= (size_t)MBOX || CS > 1, "staging must fit the mailbox");
@@ -278,23 +281,20 @@ __device__ __forceinline__ void apply_rotation(Planes<C>& a, Planes<C>& b, float
   }
 }
 
-// Write column `a` (id `ida`) to a mailbox slot, planes lane-interleaved. No barrier inside: the
-// caller may branch around this (team 0 moves a different array); the barrier that follows
-// must be reached by every thread in uniform control flow (aligned CTA / cluster barriers).
+// Write column `a` (id `ida`) to a mailbox slot: lane l stores (re, im) of its row pair k as one
+// 16-byte value at k L + l. No barrier inside: the caller may branch around this (team 0 moves a
+// different array); the barrier that follows must be reached by every thread in uniform control
+// flow (aligned CTA / cluster barriers).
 template <class C>
 __device__ __forceinline__ void put_column(const Planes<C>& a, int ida, float2* dst, int* dst_id, int lane) {
   constexpr int MH = C::MH, WH = C::WH, L = C::L;
+  float4* d = reinterpret_cast<float4*>(dst);
 #pragma unroll
-  for (int k = 0; k < MH; ++k) {
-    dst[(2 * k) * L + lane] = a.xr[k];
-    dst[(2 * k + 1) * L + lane] = a.xi[k];
-  }
+  for (int k = 0; k < MH; ++k) d[k * L + lane] = make_float4(a.xr[k].x, a.xr[k].y, a.xi[k].x, a.xi[k].y);
   if constexpr (C::VEC) {
+    float4* dw = reinterpret_cast<float4*>(dst + C::XR);
 #pragma unroll
-    for (int k = 0; k < WH; ++k) {
-      dst[C::XR + (2 * k) * L + lane] = a.wr[k];
-      dst[C::XR + (2 * k + 1) * L + lane] = a.wi[k];
-    }
+    for (int k = 0; k < WH; ++k) dw[k * L + lane] = make_float4(a.wr[k].x, a.wr[k].y, a.wi[k].x, a.wi[k].y);
   }
   if (lane == 0) *dst_id = ida;
 }
@@ -303,16 +303,20 @@ __device__ __forceinline__ void put_column(const Planes<C>& a, int ida, float2* 
 template <class C>
 __device__ __forceinline__ void get_column(Planes<C>& a, int& ida, const float2* src, const int* src_id, int lane) {
   constexpr int MH = C::MH, WH = C::WH, L = C::L;
+  const float4* d = reinterpret_cast<const float4*>(src);
 #pragma unroll
   for (int k = 0; k < MH; ++k) {
-    a.xr[k] = src[(2 * k) * L + lane];
-    a.xi[k] = src[(2 * k + 1) * L + lane];
+    const float4 v = d[k * L + lane];
+    a.xr[k] = make_float2(v.x, v.y);
+    a.xi[k] = make_float2(v.z, v.w);
   }
   if constexpr (C::VEC) {
+    const float4* dw = reinterpret_cast<const float4*>(src + C::XR);
 #pragma unroll
     for (int k = 0; k < WH; ++k) {
-      a.wr[k] = src[C::XR + (2 * k) * L + lane];
-      a.wi[k] = src[C::XR + (2 * k + 1) * L + lane];
+      const float4 v = dw[k * L + lane];
+      a.wr[k] = make_float2(v.x, v.y);
+      a.wi[k] = make_float2(v.z, v.w);
     }
   }
   ida = *src_id;
