@@ -184,14 +184,24 @@ __global__ void __launch_bounds__(256) complete_kernel(float2* X, int M, int N) 
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (tid == 0) nzero = 0;
   __syncthreads();
+  // loops over rows keep four independent accumulators (four loads in flight per thread)
   for (int c = tid; c < N; c += blockDim.x) {
-    float q = 0.f;
-    for (int m = 0; m < M; ++m) {
-      const float2 x = P[(size_t)m * N + c];
-      q = fmaf(x.x, x.x, fmaf(x.y, x.y, q));
+    float q[4] = {0.f, 0.f, 0.f, 0.f};
+    int m = 0;
+    for (; m + 4 <= M; m += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float2 x = P[(size_t)(m + u) * N + c];
+        q[u] = fmaf(x.x, x.x, fmaf(x.y, x.y, q[u]));
+      }
     }
-    zero[c] = q == 0.f;
-    if (q == 0.f) atomicAdd(&nzero, 1);
+    for (; m < M; ++m) {
+      const float2 x = P[(size_t)m * N + c];
+      q[0] = fmaf(x.x, x.x, fmaf(x.y, x.y, q[0]));
+    }
+    const float qq = (q[0] + q[1]) + (q[2] + q[3]);
+    zero[c] = qq == 0.f;
+    if (qq == 0.f) atomicAdd(&nzero, 1);
   }
   __syncthreads();
   if (nzero == 0) return;
@@ -232,15 +242,24 @@ __global__ void __launch_bounds__(256) complete_kernel(float2* X, int M, int N) 
     for (int m = tid; m < M; m += blockDim.x) v[m] = make_float2(m == ks ? 1.f : 0.f, 0.f);
     __syncthreads();
     for (int pass = 0; pass < 2; ++pass) {
-      // c = P^* v (one thread per column: coalesced rows)
+      // c = P^* v (one thread per column: coalesced rows), four row streams per thread
       for (int c = tid; c < N; c += blockDim.x) {
-        float cr = 0.f, ci = 0.f;
-        for (int m = 0; m < M; ++m) {
-          const float2 x = P[(size_t)m * N + c], y = v[m];
-          cr = fmaf(x.x, y.x, fmaf(x.y, y.y, cr));       // Re(conj(x) y)
-          ci = fmaf(x.x, y.y, fmaf(-x.y, y.x, ci));      // Im(conj(x) y)
+        float cr[4] = {0.f, 0.f, 0.f, 0.f}, ci[4] = {0.f, 0.f, 0.f, 0.f};
+        int m = 0;
+        for (; m + 4 <= M; m += 4) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float2 x = P[(size_t)(m + u) * N + c], y = v[m + u];
+            cr[u] = fmaf(x.x, y.x, fmaf(x.y, y.y, cr[u]));   // Re(conj(x) y)
+            ci[u] = fmaf(x.x, y.y, fmaf(-x.y, y.x, ci[u]));  // Im(conj(x) y)
+          }
         }
-        cq[c] = make_float2(cr, ci);
+        for (; m < M; ++m) {
+          const float2 x = P[(size_t)m * N + c], y = v[m];
+          cr[0] = fmaf(x.x, y.x, fmaf(x.y, y.y, cr[0]));
+          ci[0] = fmaf(x.x, y.y, fmaf(-x.y, y.x, ci[0]));
+        }
+        cq[c] = make_float2((cr[0] + cr[1]) + (cr[2] + cr[3]), (ci[0] + ci[1]) + (ci[2] + ci[3]));
       }
       __syncthreads();
       // v -= P c (one warp per row)
