@@ -65,8 +65,12 @@ struct JCfg {
   static_assert(RS % 2 == 0, "mailbox slots start on 16-byte boundaries");
   static constexpr int MBOX = 2 * TPC * RS;       // [parity][team][RS] float2
   static constexpr size_t SYM_BYTES = (size_t)(MBOX + kMaxTaps) * 8 + NC * 4 + 2 * TPC * 4 + 64;
-  static constexpr size_t UNIT_BYTES = SPU * SYM_BYTES + 64;
+  // unit tail: ubox[4] (item, sweep votes, zero-column count) + one float per warp of the unit
+  // for unit_sum's reduction
+  static constexpr size_t TAIL_BYTES = (16 + 4 * (UT / 32) + 15) / 16 * 16 < 64 ? 64 : (16 + 4 * (UT / 32) + 15) / 16 * 16;
+  static constexpr size_t UNIT_BYTES = SPU * SYM_BYTES + TAIL_BYTES;
   static_assert(SYM_BYTES % 16 == 0 && UNIT_BYTES % 16 == 0, "every symbol's mailbox is 16-byte aligned");
+  static_assert(!VEC || CS > 1 || XR <= kMaxTaps, "the in-kernel completion's row buffer fits the phase grid");
   static constexpr size_t SMEM = UPB * UNIT_BYTES;
   static constexpr int MINB = MINB_;   // resident CTAs per SM the register allocation aims for
   static_assert((size_t)NC * (XR + WRC) <= (size_t)MBOX || CS > 1, "staging must fit the mailbox");
@@ -365,7 +369,7 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
   float2* phs = mbox + C::MBOX;
   float* ssig = reinterpret_cast<float*>(phs + kMaxTaps);
   int* ubox = reinterpret_cast<int*>(ubase + (size_t)C::SPU * C::SYM_BYTES);  // item, vote[2], zeros
-  float* ured = reinterpret_cast<float*>(ubox + 4);
+  float* ured = reinterpret_cast<float*>(ubox + 4);                             // UT / 32 floats
 
   Counters* ctr = P.counters;
   unsigned int* queue = &ctr->queue[P.queue_slot];
