@@ -495,6 +495,8 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
     const float tol2 = La.tol2;
     int sweeps = 0, nrot = 0, rr = 0, rotated = 0;
     bool converged = false;
+    int t = 0;       // round counter (rotation log)
+    int t_rot = 0;   // rounds up to the end of the last sweep in which this symbol rotated
     // a sweep ends every Cn rounds; returns true when the unit stops
     auto sweep_end = [&]() -> bool {
       rr = 0;
@@ -518,13 +520,13 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
         any_sym = any_unit;
       }
       rotated = 0;
+      if (any_sym) t_rot = t;
       if (!any_sym && !converged) {
         converged = true;
         if (st == 0 && crank == 0 && active) atomicAdd(&ctr->sweeps, (unsigned long long)sweeps);
       }
       return !any_unit || sweeps >= P.max_sweeps;
     };
-    int t = 0;   // round counter (rotation log)
     float4* lg = nullptr;
     if constexpr (LOG) lg = P.log + (size_t)h * P.log_cap * NP + team[0];
     // One round on every pair of the thread: all dot products first, then all rotation
@@ -588,8 +590,10 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
     }
     if (lane == 0 && nrot && active) atomicAdd(&ctr->rotations, (unsigned long long)nrot);
     if constexpr (LOG) {
-      // raw X columns in column order; sigma, order and vectors come from the finalize kernel
-      if (st == 0 && crank == 0 && active) P.rounds[h] = t < P.log_cap ? t : P.log_cap;
+      // raw X columns in column order; sigma, order and vectors come from the finalize kernel.
+      // The replay stops after the last sweep that rotated: later rounds only move columns,
+      // and W is written by column id.
+      if (st == 0 && crank == 0 && active) P.rounds[h] = t_rot < P.log_cap ? t_rot : P.log_cap;
       if (active) {
         float2* xo = P.xraw + (size_t)h * M * N;
 #pragma unroll

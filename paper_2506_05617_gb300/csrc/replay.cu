@@ -9,7 +9,7 @@
 namespace lfa {
 
 template <class C>
-__global__ void __launch_bounds__(C::BLOCK) replay_kernel(const __grid_constant__ ReplayArgs R) {
+__global__ void __launch_bounds__(C::TC) replay_kernel(const __grid_constant__ ReplayArgs R) {
   constexpr int NP = C::NP, L = C::L, MR = C::MR, NC = C::NC, TPC = C::TPC, RS = C::RS;
   constexpr int Cn = NC - 1, FIX = NC - 1, RB = C::XR;
   static_assert(C::CS == 1 && !C::VEC, "the replay runs one CTA per row block");
@@ -162,22 +162,28 @@ __global__ void __launch_bounds__(512) finalize_kernel(const __grid_constant__ R
   }
 }
 
-// 32-row blocks: 16 rows of each of the team's two columns per lane on two lanes per pair (four
-// lanes of 8 rows for 16 pairs, so that every replay CTA has at least 32 threads, one unit).
+// Row blocks of XR = MR L = 32 rows: 16 rows of each of the team's two columns per lane on two
+// lanes per pair (four lanes of 8 rows for 16 pairs; one lane of 32 rows for 32 pairs, a one-warp
+// CTA whose barrier is a warp's), so that every replay CTA has at least 32 threads, one unit.
+// (16-row blocks for 32 pairs were slower: every block re-reads the symbol's log.)
 using ReplayC256 = JCfg<256, 2, 16, 1, false, 1>;
 using ReplayC128 = JCfg<128, 2, 16, 1, false, 1>;
 using ReplayC64 = JCfg<64, 2, 16, 1, false, 1>;
-using ReplayC32 = JCfg<32, 2, 16, 1, false, 1>;
+using ReplayC32 = JCfg<32, 1, 32, 1, false, 1>;   // one lane per team, 32 rows: a one-warp CTA
 using ReplayC16 = JCfg<16, 4, 8, 1, false, 1>;
-static_assert(ReplayC16::XR == 32 && ReplayC32::XR == 32 && ReplayC16::SPU == 1 && ReplayC32::SPU == 1,
-              "replay blocks are 32 rows, one symbol per CTA");
+static_assert(ReplayC16::SPU == 1 && ReplayC32::SPU == 1, "one symbol per replay CTA");
+
+// A replay CTA holds one symbol's row block: TC threads and one unit of shared memory (a
+// configuration whose unit is a single warp would otherwise be launched as four units).
+template <class C>
+constexpr size_t replay_smem() { return C::SYM_BYTES + C::TAIL_BYTES; }
 
 template <class C>
 static cudaError_t replay_t(const ReplayArgs& R, int symbols, cudaStream_t s) {
   cudaError_t e;
   const int N = R.La.N;
   dim3 grid((unsigned)((N + C::XR - 1) / C::XR), (unsigned)symbols);
-  replay_kernel<C><<<grid, C::BLOCK, C::SMEM, s>>>(R);
+  replay_kernel<C><<<grid, C::TC, replay_smem<C>(), s>>>(R);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   finalize_kernel<<<symbols, 512, 0, s>>>(R);
@@ -186,7 +192,8 @@ static cudaError_t replay_t(const ReplayArgs& R, int symbols, cudaStream_t s) {
 
 template <class C>
 static cudaError_t prepare_t() {
-  return cudaFuncSetAttribute(replay_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  return cudaFuncSetAttribute(replay_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)replay_smem<C>());
 }
 
 bool replay_supported(int NP) { return NP == 16 || NP == 32 || NP == 64 || NP == 128 || NP == 256; }
