@@ -31,6 +31,15 @@ int32_t lfa_debug_choose_variant(int32_t M, int32_t N, int32_t vectors);
 /* Number of kernel variants (ids 0 .. count-1, named by lfa_variant_name). */
 int32_t lfa_debug_variant_count(void);
 
+/* The route an autotuner cache file (text lines "M N vectors variant [log]") selects for an
+ * M x N problem: the variant id, with LFA_VARIANT_LOGGED set for the rotation-log route; -1 when
+ * the file has no usable line for it (missing, or a variant that cannot hold the problem). */
+int32_t lfa_debug_tuned_variant(const char* path, int32_t M, int32_t N, int32_t vectors);
+
+/* 1 if values variant v can serve vectors through the rotation log and the W replay for an
+ * M x N problem (a replay configuration exists for its pairs), else 0. */
+int32_t lfa_debug_logged_ok(int32_t v, int32_t M, int32_t N);
+
 #ifdef __cplusplus
 }
 #endif

@@ -842,4 +842,12 @@ int32_t lfa_debug_choose_variant(int32_t M, int32_t N, int32_t vectors) {
 
 int32_t lfa_debug_variant_count(void) { return kNumVariants; }
 
+int32_t lfa_debug_tuned_variant(const char* path, int32_t M, int32_t N, int32_t vectors) {
+  return tuned_variant(path, M, N, vectors != 0);
+}
+
+int32_t lfa_debug_logged_ok(int32_t v, int32_t M, int32_t N) {
+  return v >= 0 && v < kNumVariants && logged_ok(v, M, N) ? 1 : 0;
+}
+
 }  // extern "C"

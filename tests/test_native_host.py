@@ -141,3 +141,38 @@ def test_plan_without_gpu_fails_with_a_status():
     with pytest.raises(C.LfaError) as ei:
         C.lfa_plan([(4, 4, 3, 3, 8, 8)], C.LFA_VALUES)
     assert ei.value.status in (C.LFA_ERR_CUDA, C.LFA_ERR_UNSUPPORTED)
+
+
+def test_tune_cache_parsing_and_rotation_log_routes(tmp_path):
+    """The autotuner cache selects a variant (or the rotation-log route) per problem; lines that
+    name a variant unable to hold the problem are ignored."""
+    cache = tmp_path / "tune.txt"
+    cache.write_text("# comment\n64 64 1 9  # in registers\n128 128 1 12 log  # rotation log\n"
+                     "128 128 0 12\n32 32 1 16\n512 512 1 16 log\n")
+    LOG = C.LFA_VARIANT_LOGGED
+    assert C.lfa_debug_tuned_variant(str(cache), 64, 64, True) == 9
+    assert C.lfa_debug_tuned_variant(str(cache), 128, 128, True) == 12 | LOG
+    assert C.lfa_debug_tuned_variant(str(cache), 128, 128, False) == 12
+    assert C.lfa_debug_tuned_variant(str(cache), 32, 32, True) == -1       # 16 holds no vectors
+    assert C.lfa_debug_tuned_variant(str(cache), 512, 512, True) == 16 | LOG
+    assert C.lfa_debug_tuned_variant(str(cache), 100, 100, True) == -1
+    assert C.lfa_debug_tuned_variant(str(tmp_path / "missing.txt"), 64, 64, True) == -1
+    assert C.lfa_variant_name(12 | LOG).endswith("_log")
+    # the route exists exactly where a replay configuration serves the variant's pairs
+    for v in range(C.lfa_debug_variant_count()):
+        npairs, lanes, mr, wr, cs, ppt = (int(x) for x in re.findall(r"\d+", C.lfa_variant_name(v)))
+        expect = ppt == 1 and npairs in (16, 32, 64, 128, 256) and npairs * lanes // cs >= 32
+        M, N = min(mr * lanes, 512), min(2 * npairs, 512)
+        assert C.lfa_debug_logged_ok(v, M, N) == expect, C.lfa_variant_name(v)
+
+
+def test_committed_tune_cache_parses_for_every_entry():
+    path = os.path.join(os.path.dirname(os.path.dirname(__file__)), "paper_2506_05617_gb300", "tune_gb300.txt")
+    for line in open(path):
+        parts = line.split("#")[0].split()
+        if not parts:
+            continue
+        M, N, vec = (int(x) for x in parts[:3])
+        got = C.lfa_debug_tuned_variant(path, M, N, bool(vec))
+        assert got >= 0, line
+        assert (got & C.LFA_VARIANT_LOGGED) == (C.LFA_VARIANT_LOGGED if len(parts) == 5 else 0), line
