@@ -36,6 +36,10 @@ int32_t lfa_debug_variant_count(void);
  * the file has no usable line for it (missing, or a variant that cannot hold the problem). */
 int32_t lfa_debug_tuned_variant(const char* path, int32_t M, int32_t N, int32_t vectors);
 
+/* Position in the half-grid list of the representative of full-grid frequency f (f itself or
+ * its conjugate), the closed form the lifting kernel uses; -1 on invalid input. */
+int64_t lfa_debug_half_position(int32_t n, int32_t m, int32_t f);
+
 /* 1 if values variant v can serve vectors through the rotation log and the W replay for an
  * M x N problem (a replay configuration exists for its pairs), else 0. */
 int32_t lfa_debug_logged_ok(int32_t v, int32_t M, int32_t N);

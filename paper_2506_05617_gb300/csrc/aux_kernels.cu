@@ -4,6 +4,7 @@
 //  * lifting of symbol singular vectors to global singular vectors,
 //  * the backward pass dL/dw,
 //  * the spectral regulariser's dL/dsigma.
+#include "half_grid.cuh"
 #include "lfa_internal.cuh"
 
 namespace lfa {
@@ -54,88 +55,94 @@ cudaError_t launch_symbols(const LayerArgs& La, float2* out, cudaStream_t s) {
 // row (ci, uh, uw) of V_f with the coarse mode of (x1, x2).
 // Grid (element chunk, vector q); threads stride over the chunk's outputs (the last grid
 // coordinate fastest: coalesced writes).
-__device__ int half_index(const int32_t* half, int F_h, int f) {
-  int lo = 0, hi = F_h - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (half[mid] < f) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
 
-// A CTA serves one vector q (blockIdx.y) and kExpandRows consecutive output rows (vector
-// channel c, grid row z1); the frequency's half-grid position is found once per CTA. Each warp
-// takes rows in turn: the row's phase factor and source entry are computed once, the lanes stride
-// along the row (coalesced writes), and every phase index is an exact 32-bit product mod n or m
-// (j, x1 < n <= 65536, so j x1 < 2^32); along a stride-1 row the column index advances by a
-// constant 32 l mod m per step.
-constexpr int kExpandRows = 64;
+// A warp serves one output row (vector channel c, grid row z1) for a group of kExpandVecs
+// consecutive vectors q (blockIdx.y). Lane i works out vector q0 + i's frequency, half-grid position
+// (a closed form), row phase and scaled source entry, all lanes at once (one load each, in
+// parallel); the warp then writes the row of each vector in turn, coalesced, taking that vector's
+// values from lane i by shuffles. Phase indices are exact 32-bit products mod n or m (j, x1 < n <=
+// 65536, so j x1 < 2^32); along a stride-1 row the column index advances by 32 l mod m per step.
+constexpr int kExpandRowsPerCTA = 8;   // one row per warp
+constexpr int kExpandVecs = 32;
 
 __global__ void __launch_bounds__(256) expand_kernel(LayerArgs La, const float2* U, const float2* V,
-                                                     int64_t first, float2* u_hat, float2* v_hat) {
-  __shared__ int sh_h;
-  const int64_t q = first + blockIdx.y;
-  const int r = La.r;
-  const int f = (int)(q / r), s = (int)(q - (int64_t)f * r);
-  const unsigned j = (unsigned)(f / La.m), l = (unsigned)(f - (int)j * La.m);
-  const int fc = ((La.n - (int)j) % La.n) * La.m + (La.m - (int)l) % La.m;
-  const bool conj = fc < f;
-  if (threadIdx.x == 0) sh_h = half_index(La.half, La.F_h, conj ? fc : f);
-  __syncthreads();
-  const int h = sh_h;
-  const int n = La.n, m = La.m;
+                                                     int64_t first, int64_t count, float2* u_hat,
+                                                     float2* v_hat) {
+  const int n = La.n, m = La.m, r = La.r;
   const float scale = rsqrtf((float)n * (float)m);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31;
   // rows per vector: c_out n + c_w sh n <= 512 * 65536 * 8 < 2^31
   const int rows_u = u_hat ? La.c_out * n : 0;
   const int rows_v = v_hat ? La.c_w * La.sh * n : 0;   // input channels x fine rows
-  const int R0 = blockIdx.x * kExpandRows;
-  const int Rend = min(R0 + kExpandRows, rows_u + rows_v);
-  const unsigned step = (32u * l) % (unsigned)m;      // column phase index advance per 32 columns
-  for (int R = R0 + warp; R < Rend; R += warps) {
-    const float2* col;
-    float2* d;
-    int sh, sw, row;
-    if (R < rows_u) {
-      row = R;
-      col = U + (size_t)h * La.c_out * r + s;
-      d = u_hat + (size_t)blockIdx.y * La.c_out * n * m;
-      sh = 1; sw = 1;
-    } else {
-      row = R - rows_u;
-      col = V + (size_t)h * La.c_in * r + s;
-      d = v_hat + (size_t)blockIdx.y * La.c_in * n * m;
-      sh = La.sh; sw = La.sw;
-    }
-    // row -> (channel ci of the output grid, fine row z1); the output grid is (sh n) x (sw m)
-    const int fine_rows = sh * n;
-    const int ci = row / fine_rows;
-    const int z1 = row - ci * fine_rows;
-    const int x1 = z1 / sh, uh = z1 - x1 * sh;
-    const float2 pa = La.tw_n[((unsigned)j * (unsigned)x1) % (unsigned)n];
-    const int len = sw * m;
-    float2* out = d + ((size_t)ci * fine_rows + z1) * len;
-    const float2* src = col + (size_t)(ci * sh + uh) * sw * r;
-    float2 u0 = __ldg(src);                         // the entry for uw = 0 (the only one when sw = 1)
-    if (conj) u0.y = -u0.y;
-    const float2 a0 = make_float2((u0.x * pa.x - u0.y * pa.y) * scale, (u0.x * pa.y + u0.y * pa.x) * scale);
+  const int R = blockIdx.x * kExpandRowsPerCTA + (threadIdx.x >> 5);
+  if (R >= rows_u + rows_v) return;                    // whole warps; no barriers below
+  const bool upart = R < rows_u;
+  const int row = upart ? R : R - rows_u;
+  const int sh = upart ? 1 : La.sh, sw = upart ? 1 : La.sw;
+  const int C = upart ? La.c_out : La.c_in;            // rows of the source factor
+  const float2* Src = upart ? U : V;
+  float2* dst = upart ? u_hat : v_hat;
+  // row -> (channel ci of the output grid, fine row z1); the output grid is (sh n) x (sw m)
+  const int fine_rows = sh * n;
+  const int ci = row / fine_rows;
+  const int z1 = row - ci * fine_rows;
+  const int x1 = z1 / sh, uh = z1 - x1 * sh;
+  const int len = sw * m;
+  const size_t row_off = ((size_t)ci * fine_rows + z1) * len;
+  const int src_row = (ci * sh + uh) * sw;              // + u_w along a strided row
+  const int64_t q0 = first + (int64_t)blockIdx.y * kExpandVecs;
+  const int nv = (int)(first + count - q0 < kExpandVecs ? first + count - q0 : kExpandVecs);
+  // lane i < nv: vector q0 + i
+  float2 my_a = make_float2(0.f, 0.f), my_pa = make_float2(0.f, 0.f);
+  unsigned my_l = 0;
+  int my_conj = 0;
+  int64_t my_src = 0;
+  if (lane < nv) {
+    const int64_t q = q0 + lane;
+    const int f = (int)(q / r), sv = (int)(q - (int64_t)f * r);
+    const unsigned j = (unsigned)(f / m);
+    my_l = (unsigned)(f - (int)j * m);
+    const int fc = ((n - (int)j) % n) * m + (m - (int)my_l) % m;
+    my_conj = fc < f;
+    my_pa = La.tw_n[(j * (unsigned)x1) % (unsigned)n];
+    my_src = ((int64_t)half_position(n, m, f) * C + src_row) * r + sv;
+    float2 u0 = __ldg(Src + my_src);                   // the entry for u_w = 0 (all when sw = 1)
+    if (my_conj) u0.y = -u0.y;
+    my_a = make_float2((u0.x * my_pa.x - u0.y * my_pa.y) * scale, (u0.x * my_pa.y + u0.y * my_pa.x) * scale);
+  }
+  float2* out = dst + (size_t)(q0 - first) * C * n * m + row_off;
+  const size_t vec_stride = (size_t)C * n * m;
+  // consecutive vectors mostly share the frequency: the column phase start and step are
+  // recomputed only when l changes (l is warp-uniform, so is the branch)
+  unsigned lprev = 0xffffffffu, idx0 = 0, step = 0;
+  for (int i = 0; i < nv; ++i, out += vec_stride) {
+    const float2 a0 = make_float2(__shfl_sync(0xffffffffu, my_a.x, i), __shfl_sync(0xffffffffu, my_a.y, i));
+    const unsigned l = __shfl_sync(0xffffffffu, my_l, i);
     if (sw == 1) {
-      unsigned idx = ((unsigned)l * (unsigned)lane) % (unsigned)m;   // (l x2) mod m for x2 = lane
+      if (l != lprev) {
+        lprev = l;
+        idx0 = (l * (unsigned)lane) % (unsigned)m;   // (l x2) mod m for x2 = lane
+        step = (32u * l) % (unsigned)m;
+      }
+      unsigned idx = idx0;
       for (int z2 = lane; z2 < len; z2 += 32) {
         out[z2] = cmul(a0, La.tw_m[idx]);
         idx += step;
         if (idx >= (unsigned)m) idx -= (unsigned)m;
       }
     } else {
+      const float2 pa = make_float2(__shfl_sync(0xffffffffu, my_pa.x, i), __shfl_sync(0xffffffffu, my_pa.y, i));
+      const int conj = __shfl_sync(0xffffffffu, my_conj, i);
+      const int64_t so = (int64_t)__shfl_sync(0xffffffffu, (unsigned long long)my_src, i);
       for (int z2 = lane; z2 < len; z2 += 32) {
         const int x2 = z2 / sw, uw = z2 - x2 * sw;
         float2 a = a0;
         if (uw != 0) {
-          float2 u = __ldg(src + (size_t)uw * r);
+          float2 u = __ldg(Src + so + (int64_t)uw * r);
           if (conj) u.y = -u.y;
           a = make_float2((u.x * pa.x - u.y * pa.y) * scale, (u.x * pa.y + u.y * pa.x) * scale);
         }
-        out[z2] = cmul(a, La.tw_m[((unsigned)l * (unsigned)x2) % (unsigned)m]);
+        out[z2] = cmul(a, La.tw_m[(l * (unsigned)x2) % (unsigned)m]);
       }
     }
   }
@@ -144,10 +151,12 @@ __global__ void __launch_bounds__(256) expand_kernel(LayerArgs La, const float2*
 cudaError_t launch_expand(const LayerArgs& La, const float2* U, const float2* V, int64_t first,
                           int64_t count, float2* u_hat, float2* v_hat, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  if (count > 65535) {
-    // more vectors than one grid dimension holds: split the range
-    for (int64_t q0 = 0; q0 < count; q0 += 65535) {
-      const int64_t cnt = count - q0 < 65535 ? count - q0 : 65535;
+  const int64_t groups = (count + kExpandVecs - 1) / kExpandVecs;
+  if (groups > 65535) {
+    // more vector groups than one grid dimension holds: split the range
+    const int64_t per = (int64_t)65535 * kExpandVecs;
+    for (int64_t q0 = 0; q0 < count; q0 += per) {
+      const int64_t cnt = count - q0 < per ? count - q0 : per;
       cudaError_t e = launch_expand(La, U, V, first + q0, cnt,
                                     u_hat ? u_hat + (size_t)q0 * La.c_out * La.n * La.m : nullptr,
                                     v_hat ? v_hat + (size_t)q0 * La.c_in * La.n * La.m : nullptr, s);
@@ -156,11 +165,10 @@ cudaError_t launch_expand(const LayerArgs& La, const float2* U, const float2* V,
     return cudaSuccess;
   }
   const int64_t rows = (u_hat ? (int64_t)La.c_out * La.n : 0) + (v_hat ? (int64_t)La.c_w * La.sh * La.n : 0);
-  const int64_t blocks = (rows + kExpandRows - 1) / kExpandRows;
-  if (blocks <= 0) return cudaSuccess;
+  if (rows <= 0) return cudaSuccess;
   if (rows > 0x7fffffffLL) return cudaErrorInvalidValue;
-  dim3 grid((unsigned)blocks, (unsigned)count);
-  expand_kernel<<<grid, 256, 0, s>>>(La, U, V, first, u_hat, v_hat);
+  dim3 grid((unsigned)((rows + kExpandRowsPerCTA - 1) / kExpandRowsPerCTA), (unsigned)groups);
+  expand_kernel<<<grid, 256, 0, s>>>(La, U, V, first, count, u_hat, v_hat);
   return cudaGetLastError();
 }
 

@@ -16,6 +16,7 @@
 
 #include "../../include/lfa.h"
 #include "../../include/lfa_debug.h"
+#include "half_grid.cuh"
 #include "jacobi_variants.cuh"
 #include "lfa_internal.cuh"
 
@@ -664,7 +665,8 @@ lfa_status_t lfa_expand(lfa_plan_t p, int32_t layer, const float* U, const float
   const int64_t total = (int64_t)La.n * La.m * La.r;
   if (first < 0 || count < 0 || first + count > total) return LFA_ERR_INVALID_ARG;
   if ((u_hat && !U) || (v_hat && !V)) return LFA_ERR_INVALID_ARG;
-  if (count > 0) g_launches += (count + 65534) / 65535;
+  // launch_expand splits a range into launches of at most 65535 groups of 32 vectors
+  if (count > 0) g_launches += (count + 65535LL * 32 - 1) / (65535LL * 32);
   return from_cuda(launch_expand(La, reinterpret_cast<const float2*>(U), reinterpret_cast<const float2*>(V),
                                  first, count, reinterpret_cast<float2*>(u_hat),
                                  reinterpret_cast<float2*>(v_hat), static_cast<cudaStream_t>(stream)));
@@ -844,6 +846,11 @@ int32_t lfa_debug_variant_count(void) { return kNumVariants; }
 
 int32_t lfa_debug_tuned_variant(const char* path, int32_t M, int32_t N, int32_t vectors) {
   return tuned_variant(path, M, N, vectors != 0);
+}
+
+int64_t lfa_debug_half_position(int32_t n, int32_t m, int32_t f) {
+  if (n < 1 || m < 1 || (int64_t)n * m > 0x7fffffffLL || f < 0 || (int64_t)f >= (int64_t)n * m) return -1;
+  return half_position(n, m, f);
 }
 
 int32_t lfa_debug_logged_ok(int32_t v, int32_t M, int32_t N) {

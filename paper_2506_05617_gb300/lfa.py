@@ -50,7 +50,7 @@ EXPORTS = [
     "lfa_destroy", "lfa_get_info", "lfa_layer_query", "lfa_status_string", "lfa_variant_name",
     "lfa_last_cuda_error", "lfa_kernel_launches", "lfa_version",
     "lfa_debug_schedule", "lfa_debug_half_grid", "lfa_debug_choose_variant", "lfa_debug_variant_count",
-    "lfa_debug_tuned_variant", "lfa_debug_logged_ok",
+    "lfa_debug_tuned_variant", "lfa_debug_logged_ok", "lfa_debug_half_position",
 ]
 
 
@@ -133,6 +133,7 @@ def lib():
         "lfa_debug_variant_count": (c_int32, []),
         "lfa_debug_tuned_variant": (c_int32, [c_char_p, c_int32, c_int32, c_int32]),
         "lfa_debug_logged_ok": (c_int32, [c_int32, c_int32, c_int32]),
+        "lfa_debug_half_position": (c_int64, [c_int32, c_int32, c_int32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -302,3 +303,7 @@ def lfa_debug_tuned_variant(path: str, M: int, N: int, vectors: bool) -> int:
 
 def lfa_debug_logged_ok(v: int, M: int, N: int) -> bool:
     return bool(lib().lfa_debug_logged_ok(v, M, N))
+
+
+def lfa_debug_half_position(n: int, m: int, f: int) -> int:
+    return lib().lfa_debug_half_position(n, m, f)

@@ -176,3 +176,17 @@ def test_committed_tune_cache_parses_for_every_entry():
         got = C.lfa_debug_tuned_variant(path, M, N, bool(vec))
         assert got >= 0, line
         assert (got & C.LFA_VARIANT_LOGGED) == (C.LFA_VARIANT_LOGGED if len(parts) == 5 else 0), line
+
+
+@pytest.mark.parametrize("n,m", [(1, 1), (1, 7), (6, 1), (2, 2), (3, 3), (4, 5), (5, 4), (8, 8), (7, 9), (32, 32), (9, 16)])
+def test_half_position_closed_form_matches_the_list(n, m):
+    """The lifting kernel's closed-form position of a frequency's representative in the half grid,
+    against the oracle's half-grid list and conjugation rule, for every frequency."""
+    half = list(O.half_grid(n, m))
+    pos = {f: i for i, f in enumerate(half)}
+    for f in range(n * m):
+        j, l = divmod(f, m)
+        fc = ((-j) % n) * m + (-l) % m
+        rep = f if f in pos else fc
+        assert C.lfa_debug_half_position(n, m, f) == pos[rep], (n, m, f)
+    assert C.lfa_debug_half_position(n, m, n * m) == -1
