@@ -351,6 +351,48 @@ def run_lfa(args, rank: int, world: int, local_rank: int):
     barrier()
     plain_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in pev]))
 
+    peaks = {}
+    if os.path.exists(PEAKS_FILE):
+        try:
+            peaks = json.load(open(PEAKS_FILE))
+        except (OSError, ValueError):
+            peaks = {}
+
+    # ---- the lifting kernel alone (HBM-write bound): vector pairs of layer 0 writing about
+    # 512 MiB per launch, more than L2 holds, so back-to-back launches each go to DRAM
+    lift = None
+    if vectors and not args.no_lift_roofline:
+        l0 = layers[0]
+        per_pair = 8 * (l0.c_out * l0.n * l0.m + l0.c_in * l0.sh * l0.n * l0.sw * l0.m)
+        cnt = int(min(l0.F * l0.r, max(1, -(-(512 << 20) // per_pair))))
+        luh = torch.empty((cnt, l0.c_out, l0.n, l0.m), dtype=torch.complex64, device=dev)
+        lvh = torch.empty((cnt, l0.c_in, l0.sh * l0.n, l0.sw * l0.m), dtype=torch.complex64, device=dev)
+        u0, v0 = outs[len(layers)], outs[2 * len(layers)]     # U and V of layer 0
+
+        def lift_call():
+            C.lfa_expand(plan.handle, 0, u0.data_ptr(), v0.data_ptr(), 0, cnt, luh.data_ptr(), lvh.data_ptr(), sptr)
+
+        for _ in range(3):
+            lift_call()
+        barrier()
+        la, lb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 10
+        la.record(stream)
+        for _ in range(reps):
+            lift_call()
+        lb.record(stream)
+        barrier()
+        lift_ms = la.elapsed_time(lb) / reps
+        gbs = per_pair * cnt / (lift_ms * 1e-3) / 1e9
+        hbm = peaks.get("hbm_gbs")
+        hbm_peak, hbm_src = (float(hbm), "measured copy bandwidth") if hbm else (6800.0, "fallback")
+        lift = {"kernel": "expand_kernel (lifting, layer 0)", "bound": "hbm", "pairs": cnt,
+                "bytes_per_launch": int(per_pair * cnt), "us_per_launch": lift_ms * 1e3,
+                "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                "peak_source": hbm_src,
+                "timing": f"mean of {reps} back-to-back launches, each writing more than L2 holds"}
+        del luh, lvh
+
     # ---- end to end through the public API from pinned host buffers, pipelined as a serving loop
     # would run it: step i's outputs go back to the host on a copy stream while step i + 1
     # computes into the other of two output sets (two plans, one captured graph each). Every
@@ -410,12 +452,6 @@ def run_lfa(args, rank: int, world: int, local_rank: int):
     peak = fp32_peak_tflops()
     achieved = flops / (fwd_mean / 1e3) / 1e12
     traffic = measured_traffic(args.workload)
-    peaks = {}
-    if os.path.exists(PEAKS_FILE):
-        try:
-            peaks = json.load(open(PEAKS_FILE))
-        except (OSError, ValueError):
-            peaks = {}
 
     out = {
         "metric": METRIC,
@@ -465,6 +501,8 @@ def run_lfa(args, rank: int, world: int, local_rank: int):
         "accuracy": {"unconverged": info["unconverged"], "nonfinite": info["nonfinite"]},
         "measured_peaks": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")} if peaks else None,
     }
+    if lift is not None:
+        out["lift_roofline"] = lift
     if e2e is not None:
         out["e2e"] = e2e
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -583,6 +621,8 @@ def main():
     ap.add_argument("--tune-cache", default=DEFAULT_TUNE if os.path.exists(DEFAULT_TUNE) else None,
                     help="autotuner cache file read by lfa_plan")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-lift-roofline", action="store_true",
+                    help="skip the separate timing of the lifting kernel on a larger-than-L2 output")
     ap.add_argument("--sweep-n", default=None,
                     help="comma-separated torus sizes: run the O(N) study of the 64->64 layer instead "
                          "(one JSON line per n and output mode)")
