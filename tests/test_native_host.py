@@ -190,3 +190,25 @@ def test_half_position_closed_form_matches_the_list(n, m):
         rep = f if f in pos else fc
         assert C.lfa_debug_half_position(n, m, f) == pos[rep], (n, m, f)
     assert C.lfa_debug_half_position(n, m, n * m) == -1
+
+
+def test_every_variant_shared_memory_layout_fits(tmp_path):
+    """tests/layout_check.cu, compiled for the host, walks every Jacobi variant (values, and
+    values+vectors where built): the unit tail holds the four control words and one float per warp,
+    a CTA stays within 227 KB, and neighbouring teams' mailbox slots are 2 L mod 16 float2 apart."""
+    import shutil
+    import subprocess
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    exe = str(tmp_path / "layout_check")
+    subprocess.run([nvcc, "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-o", exe,
+                    os.path.join(ROOT, "tests", "layout_check.cu")], check=True, capture_output=True, timeout=300)
+    res = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    lines = res.stdout.strip().splitlines()
+    assert res.returncode == 0, res.stdout
+    assert all(ln.endswith(" ok") for ln in lines)
+    ids = {int(ln.split()[0]) for ln in lines}
+    assert ids == set(range(C.lfa_debug_variant_count()))
+    smem = [int(re.search(r"smem=(\d+)", ln).group(1)) for ln in lines]
+    assert max(smem) <= 227 * 1024
