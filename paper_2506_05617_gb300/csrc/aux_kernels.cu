@@ -53,9 +53,7 @@ cudaError_t launch_symbols(const LayerArgs& La, float2* out, cudaStream_t s) {
 // (U^_k = F_k U_k, Sec. III). U_f = U[h] on the half grid, conj(U[h(fc)]) otherwise.
 // For a stride, v_hat lives on the fine torus: v_hat[q][ci][sh x1 + uh][sw x2 + uw] takes
 // row (ci, uh, uw) of V_f with the coarse mode of (x1, x2).
-// Grid (element chunk, vector q); threads stride over the chunk's outputs (the last grid
-// coordinate fastest: coalesced writes).
-
+//
 // A warp serves one output row (vector channel c, grid row z1) for a group of kExpandVecs
 // consecutive vectors q (blockIdx.y). Lane i works out vector q0 + i's frequency, half-grid position
 // (a closed form), row phase and scaled source entry, all lanes at once (one load each, in
