@@ -115,6 +115,18 @@ def aggregate_rate(units_per_rank_step: float, steps: int, world: int, slowest_m
     return world * units_per_rank_step * steps / (slowest_ms / 1e3)
 
 
+def lift_bytes_per_pair(l: W.Layer) -> int:
+    """Bytes the lifting kernel writes per vector pair: u_hat on the n x m torus (c_out channels)
+    and v_hat on the input torus s_h n x s_w m (c_in channels), complex64."""
+    return 8 * (l.c_out * l.n * l.m + l.c_in * l.sh * l.n * l.sw * l.m)
+
+
+def lift_pairs(l: W.Layer, target_bytes: int = 512 << 20) -> int:
+    """Vector pairs per timed lifting launch: enough to write about target_bytes (more than the
+    L2 holds), at most every pair of the layer."""
+    return int(min(l.F * l.r, max(1, -(-target_bytes // lift_bytes_per_pair(l)))))
+
+
 def fp32_peak_tflops() -> float:
     return SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
@@ -363,8 +375,8 @@ def run_lfa(args, rank: int, world: int, local_rank: int):
     lift = None
     if vectors and not args.no_lift_roofline:
         l0 = layers[0]
-        per_pair = 8 * (l0.c_out * l0.n * l0.m + l0.c_in * l0.sh * l0.n * l0.sw * l0.m)
-        cnt = int(min(l0.F * l0.r, max(1, -(-(512 << 20) // per_pair))))
+        per_pair = lift_bytes_per_pair(l0)
+        cnt = lift_pairs(l0)
         luh = torch.empty((cnt, l0.c_out, l0.n, l0.m), dtype=torch.complex64, device=dev)
         lvh = torch.empty((cnt, l0.c_in, l0.sh * l0.n, l0.sw * l0.m), dtype=torch.complex64, device=dev)
         u0, v0 = outs[len(layers)], outs[2 * len(layers)]     # U and V of layer 0
