@@ -181,6 +181,32 @@ def test_conv512_n64_values_and_vectors_sampled():
     plan.close()
 
 
+def test_conv64_n256_values_and_vectors_sampled():
+    """64->64 3x3 on 256x256 (32,770 half-grid symbols, the largest point of the n sweep): sampled
+    values and vectors against the oracle, Parseval over all 4.2M singular values."""
+    lay = W.Layer(64, 64, 3, 3, 256, 256, "normal", 2.0, 2)
+    w = W.weights(lay)
+    plan = LfaPlan([(lay.c_out, lay.c_in, lay.kh, lay.kw, lay.n, lay.m)], vectors=True)
+    sig, U, V = plan.svd([torch.from_numpy(w).cuda()])
+    torch.cuda.synchronize()
+    st, info = plan.info()
+    assert st == C.LFA_OK, info
+    s = sig[0].cpu().numpy()
+    assert s.shape == (lay.F, 64)
+    sampled_sigma_check(w, lay, s, 8, seed=9)
+    half = O.half_grid(lay.n, lay.m)
+    pick = np.random.default_rng(10).choice(len(half), 6, replace=False)
+    S = O.symbols(w, lay.n, lay.m, freqs=half[pick])
+    Uu = U[0][torch.from_numpy(pick).cuda()].cpu().numpy().astype(np.complex128)
+    Vv = V[0][torch.from_numpy(pick).cuda()].cpu().numpy().astype(np.complex128)
+    ss = s[half[pick]].astype(np.float64)
+    res = np.einsum("hoi,his->hos", S, Vv) - Uu * ss[:, None, :]
+    assert np.max(np.linalg.norm(res, axis=1)) <= VEC_TOL * s.max()
+    for X in (Uu, Vv):
+        assert np.max(np.abs(np.einsum("hos,hot->hst", np.conj(X), X) - np.eye(lay.r))) <= VEC_TOL
+    plan.close()
+
+
 def test_paper_shape_at_n2048_values_sampled():
     """The paper's 16->16 3x3 shape at n = 2048 (2,097,154 half-grid symbols, 67M singular values):
     sampled frequencies against the oracle, Parseval over all of them, conjugate mirror."""
