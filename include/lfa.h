@@ -1,7 +1,8 @@
 /*
  * lfa.h -- C ABI of the GB300 (sm_103a) library for the singular value
- * decomposition of stride-1 periodic multi-channel 2-D convolutions by local
- * Fourier analysis (LFA), arXiv 2506.05617.
+ * decomposition of periodic multi-channel 2-D convolutions by local Fourier
+ * analysis (LFA), arXiv 2506.05617: stride-1 layers, and strided layers viewed
+ * as crystals (see lfa_layer_desc_t).
  *
  * The method (Sec. III of the paper): a stride-1 convolution on the periodic
  * n x m torus, (A f)(x) = sum_{y in N} M_y f(x + y) with M_y in R^{c_out x c_in}
@@ -81,8 +82,8 @@ typedef enum lfa_status {
  * symbol is the c_out x (c_in s_h s_w) matrix
  *   A_k[o][(i, u)] = sum_{taps with y_ab = s q + u} w[o,i,a,b] exp(2 pi i <k, q>),
  * q = floor(y_ab / s) componentwise, column (i, u_h, u_w) at i s_h s_w + u_h s_w + u_w.
- * Everywhere below "c_in" of a symbol, of V and of v_hat then means c_in s_h s_w; the
- * weights keep c_in.
+ * Everywhere below "c_in" of a symbol, of r and of V then means c_in s_h s_w; the weights
+ * and v_hat (which lives on the fine torus, see lfa_expand) keep c_in.
  *
  * Limits: 1 <= c_out <= 512; 1 <= c_in * s_h * s_w <= 512; 1 <= kh, kw <= 15;
  * 1 <= s_h, s_w <= 8; 1 <= n, m <= 65536; n*m <= 2^31 - 1; 0 <= pad < k or -1. */
