@@ -40,6 +40,11 @@ int32_t lfa_debug_tuned_variant(const char* path, int32_t M, int32_t N, int32_t 
  * its conjugate), the closed form the lifting kernel uses; -1 on invalid input. */
 int64_t lfa_debug_half_position(int32_t n, int32_t m, int32_t f);
 
+/* 1 if variant v holds an M x N problem in registers (with the accumulated rotations W when
+ * vectors != 0, which needs a variant built with vectors), else 0: the rule the built-in choice
+ * and the autotuner cache apply. */
+int32_t lfa_debug_variant_fits(int32_t v, int32_t M, int32_t N, int32_t vectors);
+
 /* 1 if values variant v can serve vectors through the rotation log and the W replay for an
  * M x N problem (a replay configuration exists for its pairs), else 0. */
 int32_t lfa_debug_logged_ok(int32_t v, int32_t M, int32_t N);

@@ -20,18 +20,15 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def candidates(M: int, N: int, vectors: bool) -> List[int]:
-    """Variant ids that can hold an M x N problem (per the library's own capacity rules)."""
-    import re
+    """Variant ids that can hold an M x N problem, by the library's own rules: register-resident
+    variants (with W when vectors), and with vectors also the values-mode variants that can run
+    the rotation log and the W replay (flagged LFA_VARIANT_LOGGED)."""
     from . import lfa as C
     out = []
     for v in range(C.lfa_debug_variant_count()):
-        npairs, lanes, mr, wr, cs, ppt = (int(x) for x in re.findall(r"\d+", C.lfa_variant_name(v)))
-        if M > mr * lanes or N > 2 * npairs:
-            continue
-        if not vectors or N <= wr * lanes:
+        if C.lfa_debug_variant_fits(v, M, N, vectors):
             out.append(v)
-        # vectors through the rotation log and the W replay (values-mode forward)
-        if vectors and ppt == 1 and npairs in (16, 32, 64, 128, 256) and npairs * lanes // cs >= 32 and N <= 512:
+        if vectors and C.lfa_debug_logged_ok(v, M, N):
             out.append(v | C.LFA_VARIANT_LOGGED)
     return out
 

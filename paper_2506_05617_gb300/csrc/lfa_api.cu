@@ -853,6 +853,10 @@ int64_t lfa_debug_half_position(int32_t n, int32_t m, int32_t f) {
   return half_position(n, m, f);
 }
 
+int32_t lfa_debug_variant_fits(int32_t v, int32_t M, int32_t N, int32_t vectors) {
+  return variant_fits(v, M, N, vectors != 0) ? 1 : 0;
+}
+
 int32_t lfa_debug_logged_ok(int32_t v, int32_t M, int32_t N) {
   return v >= 0 && v < kNumVariants && logged_ok(v, M, N) ? 1 : 0;
 }

@@ -50,7 +50,7 @@ EXPORTS = [
     "lfa_destroy", "lfa_get_info", "lfa_layer_query", "lfa_status_string", "lfa_variant_name",
     "lfa_last_cuda_error", "lfa_kernel_launches", "lfa_version",
     "lfa_debug_schedule", "lfa_debug_half_grid", "lfa_debug_choose_variant", "lfa_debug_variant_count",
-    "lfa_debug_tuned_variant", "lfa_debug_logged_ok", "lfa_debug_half_position",
+    "lfa_debug_tuned_variant", "lfa_debug_variant_fits", "lfa_debug_logged_ok", "lfa_debug_half_position",
 ]
 
 
@@ -132,6 +132,7 @@ def lib():
         "lfa_debug_choose_variant": (c_int32, [c_int32, c_int32, c_int32]),
         "lfa_debug_variant_count": (c_int32, []),
         "lfa_debug_tuned_variant": (c_int32, [c_char_p, c_int32, c_int32, c_int32]),
+        "lfa_debug_variant_fits": (c_int32, [c_int32, c_int32, c_int32, c_int32]),
         "lfa_debug_logged_ok": (c_int32, [c_int32, c_int32, c_int32]),
         "lfa_debug_half_position": (c_int64, [c_int32, c_int32, c_int32]),
     }
@@ -299,6 +300,10 @@ def lfa_debug_variant_count() -> int:
 
 def lfa_debug_tuned_variant(path: str, M: int, N: int, vectors: bool) -> int:
     return lib().lfa_debug_tuned_variant(path.encode(), M, N, int(vectors))
+
+
+def lfa_debug_variant_fits(v: int, M: int, N: int, vectors: bool) -> bool:
+    return bool(lib().lfa_debug_variant_fits(v, M, N, int(bool(vectors))))
 
 
 def lfa_debug_logged_ok(v: int, M: int, N: int) -> bool:

@@ -212,3 +212,51 @@ def test_every_variant_shared_memory_layout_fits(tmp_path):
     assert ids == set(range(C.lfa_debug_variant_count()))
     smem = [int(re.search(r"smem=(\d+)", ln).group(1)) for ln in lines]
     assert max(smem) <= 227 * 1024
+
+
+AUTOTUNE_SHAPES = [(4, 4), (9, 3), (33, 17), (64, 12), (64, 64), (100, 77), (128, 128), (200, 200),
+                   (256, 128), (256, 256), (400, 400), (512, 256), (512, 512)]
+
+
+def test_autotuner_candidates_are_exactly_what_a_cache_line_can_select(tmp_path):
+    """Every route the autotuner times is one that a cache line can select for that problem, and
+    every route a cache line can select is timed (register variants, and rotation-log routes)."""
+    from paper_2506_05617_gb300 import autotune as A
+    cache = str(tmp_path / "tune.txt")
+    nv = C.lfa_debug_variant_count()
+    for M, N in AUTOTUNE_SHAPES:
+        for vec in (False, True):
+            accepted = set()
+            for v in range(nv):
+                for route, want in [(f"{v}", v), (f"{v} log", v | C.LFA_VARIANT_LOGGED)]:
+                    if route.endswith("log") and not vec:
+                        continue
+                    with open(cache, "w") as fh:
+                        fh.write(f"{M} {N} {int(vec)} {route}\n")
+                    if C.lfa_debug_tuned_variant(cache, M, N, vec) == want:
+                        accepted.add(want)
+            cands = A.candidates(M, N, vec)
+            assert len(cands) == len(set(cands))
+            assert set(cands) == accepted, (M, N, vec, sorted(set(cands) ^ accepted))
+            assert cands, (M, N, vec)
+            # the built-in choice is among them; with vectors and no register variant that holds
+            # W, the plan runs the values-mode choice through the rotation log
+            bi = C.lfa_debug_choose_variant(M, N, vec)
+            if bi < 0:
+                assert vec
+                bi = C.lfa_debug_choose_variant(M, N, False) | C.LFA_VARIANT_LOGGED
+            assert bi in cands
+
+
+def test_autotuner_cache_round_trips_through_the_library(tmp_path):
+    from paper_2506_05617_gb300 import autotune as A
+    cache = str(tmp_path / "tune.txt")
+    with open(cache, "w") as fh:
+        fh.write("# an older cache\n64 64 1 9  # kept\n100 77 0 7\n")
+    logged = [v for v in A.candidates(128, 128, True) if v & C.LFA_VARIANT_LOGGED][0]
+    A.write_cache(cache, {(128, 128, 1): (logged, 1.5), (100, 77, 0): (A.candidates(100, 77, False)[-1], 0.2)})
+    assert C.lfa_debug_tuned_variant(cache, 128, 128, True) == logged
+    assert C.lfa_debug_tuned_variant(cache, 100, 77, False) == A.candidates(100, 77, False)[-1]
+    assert C.lfa_debug_tuned_variant(cache, 64, 64, True) == 9          # untouched line kept
+    lines = [ln for ln in open(cache) if not ln.startswith("#")]
+    assert len(lines) == 3 and lines == sorted(lines, key=lambda ln: tuple(int(x) for x in ln.split()[:3]))
