@@ -260,3 +260,16 @@ def test_autotuner_cache_round_trips_through_the_library(tmp_path):
     assert C.lfa_debug_tuned_variant(cache, 64, 64, True) == 9          # untouched line kept
     lines = [ln for ln in open(cache) if not ln.startswith("#")]
     assert len(lines) == 3 and lines == sorted(lines, key=lambda ln: tuple(int(x) for x in ln.split()[:3]))
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the built CUDA library every call raises: there is no CPU or other fallback."""
+    monkeypatch.setattr(C, "_LIB", None)
+    monkeypatch.setattr(C, "LIB_PATH", str(tmp_path / "liblfa.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        C.lib()
+    with pytest.raises(RuntimeError, match="not built"):
+        C.lfa_plan([(4, 4, 3, 3, 8, 8)], C.LFA_VALUES)
+    from paper_2506_05617_gb300.torch_api import LfaPlan
+    with pytest.raises(RuntimeError, match="not built"):
+        LfaPlan([(4, 4, 3, 3, 8, 8)])
