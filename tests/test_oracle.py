@@ -318,6 +318,75 @@ def test_spectral_edit_matches_dense_projection(mode, a, b):
                                atol=1e-12)
 
 
+def _edit_input():
+    """Descending rows of singular values with ties, zeros and entries equal to the parameters."""
+    rng = np.random.default_rng(41)
+    s = np.sort(rng.uniform(0.0, 2.0, (7, 6)), axis=1)[:, ::-1].copy()
+    s[0, :] = [1.5, 0.9, 0.5, 0.5, 0.3, 0.0]      # exact parameter values 0.5 and 0.3, a zero
+    s[1, :] = 0.7                                 # a fully degenerate frequency
+    return s
+
+
+def test_edit_values_clip_properties():
+    s = _edit_input()
+    out = O.edit_values(s, "clip", 0.6)
+    assert np.all(out <= 0.6)
+    keep = s <= 0.6
+    assert np.array_equal(out[keep], s[keep])           # unchanged below the cap
+    assert np.all(out[~keep] == 0.6)                     # capped above it
+
+
+def test_edit_values_clamp_properties():
+    s = _edit_input()
+    lo, hi = 0.3, 0.9
+    out = O.edit_values(s, "clamp", lo, hi)
+    assert np.all((out >= lo) & (out <= hi))             # swapped bounds would break this
+    inside = (s >= lo) & (s <= hi)
+    assert np.array_equal(out[inside], s[inside])
+    assert np.all(out[s < lo] == lo) and np.all(out[s > hi] == hi)
+    assert np.array_equal(out, np.clip(s, lo, hi))       # the library's clip routine agrees
+
+
+def test_edit_values_threshold_properties():
+    s = _edit_input()
+    a = 0.5
+    out = O.edit_values(s, "threshold", a)
+    assert np.all(out[s < a] == 0.0)
+    kept = s >= a
+    assert np.array_equal(out[kept], s[kept])            # values equal to a are kept (>=, not >)
+    assert out[0, 2] == 0.5 and out[0, 3] == 0.5 and out[0, 4] == 0.0
+
+
+@pytest.mark.parametrize("a,k", [(0, 0), (2, 2), (2.4, 2), (2.6, 3), (6, 6), (9, 6)])
+def test_edit_values_rank_properties(a, k):
+    s = _edit_input() + 1.0                              # all positive: non-zeros are countable
+    out = O.edit_values(s, "rank", a)
+    assert np.all(np.count_nonzero(out, axis=1) == k)    # round(a) values per frequency
+    assert np.array_equal(out[:, :k], s[:, :k])          # the leading (largest) ones
+    assert np.all(out[:, k:] == 0.0)
+
+
+@pytest.mark.parametrize("mode,a,b", [("clamp", 0.3, 0.9), ("threshold", 0.5, 0), ("rank", 2, 0)])
+def test_spectral_edit_is_exact_for_a_kernel_covering_the_torus(mode, a, b):
+    """With kh = n and kw = m every operator is a convolution, so the edited kernel's spectrum
+    is the edited spectrum itself; checked by properties of the multiset, not by phi."""
+    wf = rand_w(3, 3, 4, 4, 34)
+    n = m = 4
+    smax = O.lfa_svd(wf, n, m, compute_uv=False).max()
+    s = O.lfa_svd(wf, n, m, compute_uv=False)
+    aa, bb = (a * smax, b * smax) if mode != "rank" else (a, b)
+    got = O.lfa_svd(O.spectral_edit(wf, n, m, mode, aa, bb), n, m, compute_uv=False)
+    if mode == "clamp":
+        np.testing.assert_allclose(np.sort(got.ravel()), np.sort(np.clip(s, aa, bb).ravel()), atol=1e-12)
+    elif mode == "threshold":
+        nz = np.sort(got.ravel())[::-1][: int(np.sum(s >= aa))]
+        np.testing.assert_allclose(nz, np.sort(s[s >= aa])[::-1], atol=1e-12)
+        assert np.sum(got > 1e-9) == np.sum(s >= aa)
+    else:
+        np.testing.assert_allclose(got[:, :2], s[:, :2], atol=1e-12)   # per frequency, leading two
+        assert np.all(got[:, 2:] < 1e-9)
+
+
 def test_spectral_edit_identity_and_full_support():
     w = rand_w(3, 2, 3, 3, 32)
     n, m = 5, 4
