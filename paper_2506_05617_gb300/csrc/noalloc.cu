@@ -35,22 +35,58 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 std::mutex g_setup_mutex;
-void* g_scratch_ptr[kMaxDevices] = {};
+struct ScratchAddr {
+  unsigned long long ctx_id;   // driver context the address belongs to (0: unknown)
+  void* ptr;
+};
+ScratchAddr g_scratch[kMaxDevices] = {};
 
-// Set-up, once per device, with that device current: the device address of the array.
+// The unique id of the calling thread's current driver context, or 0 when it cannot be read.
+// The driver calls are reached through the runtime's entry-point query, so the library does not
+// link the driver library itself.
+unsigned long long current_context_id() {
+  typedef int (*GetCurrentFn)(void**);
+  typedef int (*GetIdFn)(void*, unsigned long long*);
+  static GetCurrentFn get_current = nullptr;
+  static GetIdFn get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    looked_up = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetIdFn>(f);
+  }
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current && get_id && get_current(&ctx) == 0 && ctx != nullptr && get_id(ctx, &id) == 0) return id;
+  return 0;
+}
+
+// Set-up, once per device and driver context, with that device current: the device address of
+// the array. A device reset (or another context made current) gives a new context id, and the
+// address is looked up again.
 cudaError_t scratch_for_current_device(unsigned char** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (g_scratch_ptr[dev] == nullptr) {
+  const unsigned long long id = current_context_id();
+  ScratchAddr& a = g_scratch[dev];
+  if (a.ptr == nullptr || id == 0 || id != a.ctx_id) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = p;
+    a.ptr = p;
+    a.ctx_id = current_context_id();   // the lookup above makes the primary context current if none was
   }
-  *out = static_cast<unsigned char*>(g_scratch_ptr[dev]);
+  *out = static_cast<unsigned char*>(a.ptr);
   return cudaSuccess;
 }
 
@@ -114,23 +150,58 @@ extern "C" lfa_status_t lfa_svd_backward_noalloc(const lfa_layer_desc_t* layer, 
   La.tol2 = 0.f;
 
   // scratch layout: half-grid list | twiddles n | twiddles m | partial sums | G workspace.
-  // The partial sums get at most half the array; G gets the rest and must hold one chunk.
+  const int64_t CW = (int64_t)La.c_out * La.c_w;    // weight (o, i) pairs
   const int64_t CC = (int64_t)La.c_out * La.c_in;   // symbol entries (>= weight pairs)
   const int64_t kk = (int64_t)d.kh * d.kw;
+  const size_t slab = (size_t)(CW * kk * 4);        // partial sums of one chunk
   const size_t fixed = align256((size_t)La.F_h * 4) + align256((size_t)d.n * 8) + align256((size_t)d.m * 8);
   if (fixed >= kScratchBytes / 2) return LFA_ERR_UNSUPPORTED;
-  const size_t part_budget = kScratchBytes / 2 - fixed;
-  int64_t chunks = (int64_t)(part_budget / (size_t)(CC * kk * 4));
-  if (chunks < 1) return LFA_ERR_UNSUPPORTED;                       // one partial slab does not fit
-  chunks = chunks < La.F_h ? chunks : La.F_h;
-  chunks = chunks < 4096 ? chunks : 4096;
-  int64_t chunk = (La.F_h + chunks - 1) / chunks;
-  if (chunk > 65535) return LFA_ERR_UNSUPPORTED;
-  chunks = (La.F_h + chunk - 1) / chunk;
-  const size_t part_bytes = align256((size_t)(chunks * CC * kk * 4));
-  const size_t g_bytes = kScratchBytes - fixed - part_bytes;
-  const int64_t g_cap = (int64_t)(g_bytes / (size_t)(CC * 8));
-  if (g_cap < chunk) return LFA_ERR_UNSUPPORTED;                    // one chunk of G does not fit
+  int64_t chunks = 0, chunk = 0, g_cap = 0;
+  size_t part_bytes = 0;
+  const int fused = fused_backward_chunks(La);
+  if (fused > 0) {
+    // Stride-1 layers with at most 25 taps take the fused route: G_k never leaves registers, so
+    // the whole array after the tables holds partial sums. The chunk count is the planned
+    // backward's (same rounding order) when its partials fit, else the largest count that fits.
+    const int64_t fit = (int64_t)((kScratchBytes - fixed) / slab);
+    if (fit < 1) return LFA_ERR_UNSUPPORTED;                      // one partial slab does not fit
+    chunks = fused < fit ? fused : fit;
+    chunk = (La.F_h + chunks - 1) / chunks;
+    chunks = (La.F_h + chunk - 1) / chunk;
+    part_bytes = align256((size_t)chunks * slab);
+  } else {
+    // G route: the partial sums get at most half the array; G gets the rest and must hold one
+    // chunk of G_k blocks. The planned backward's chunk count is used when it fits.
+    const size_t part_budget = kScratchBytes / 2 - fixed;
+    const int64_t fit = (int64_t)(part_budget / slab);
+    if (fit < 1) return LFA_ERR_UNSUPPORTED;                      // one partial slab does not fit
+    int64_t want = (155648 + CC - 1) / CC;                          // the plan's count for a roomy G
+    want = want < La.F_h ? want : La.F_h;
+    want = want < 4096 ? want : 4096;
+    chunks = want < fit ? want : fit;
+    chunk = (La.F_h + chunks - 1) / chunks;
+    if (chunk > 65535) return LFA_ERR_UNSUPPORTED;
+    chunks = (La.F_h + chunk - 1) / chunk;
+    part_bytes = align256((size_t)chunks * slab);
+    const size_t g_bytes = kScratchBytes - fixed - part_bytes;
+    g_cap = (int64_t)(g_bytes / (size_t)(CC * 8));
+    if (g_cap < chunk) {
+      // more, smaller chunks leave more room for G: take the count that balances the two
+      for (int64_t c = chunks + 1; c <= fit && c <= La.F_h; ++c) {
+        const int64_t ch = (La.F_h + c - 1) / c;
+        const size_t pb = align256((size_t)((La.F_h + ch - 1) / ch) * slab);
+        if (pb > part_budget) break;
+        if ((int64_t)((kScratchBytes - fixed - pb) / (size_t)(CC * 8)) >= ch) {
+          chunk = ch;
+          chunks = (La.F_h + ch - 1) / ch;
+          part_bytes = pb;
+          break;
+        }
+      }
+      g_cap = (int64_t)((kScratchBytes - fixed - part_bytes) / (size_t)(CC * 8));
+      if (g_cap < chunk) return LFA_ERR_UNSUPPORTED;                // one chunk of G does not fit
+    }
+  }
 
   unsigned char* base = nullptr;
   cudaError_t e = scratch_for_current_device(&base);
@@ -139,7 +210,7 @@ extern "C" lfa_status_t lfa_svd_backward_noalloc(const lfa_layer_desc_t* layer, 
   float2* tw_n = reinterpret_cast<float2*>(base + align256((size_t)La.F_h * 4));
   float2* tw_m = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(tw_n) + align256((size_t)d.n * 8));
   float* partial = reinterpret_cast<float*>(base + fixed);
-  float2* G = reinterpret_cast<float2*>(base + fixed + part_bytes);
+  float2* G = g_cap > 0 ? reinterpret_cast<float2*>(base + fixed + part_bytes) : nullptr;
   La.half = half;
   La.tw_n = tw_n;
   La.tw_m = tw_m;
