@@ -7,8 +7,9 @@ A step is one pass of the whole path over one synthetic layer batch:
   -> backward dL/dw -> lifting of the r global singular vector pairs of one frequency.
 Metric: singular values per second (full-grid count n*m*r per layer per step).
 
-Default workload: one 64->64 3x3 stride-1 periodic conv on a 32x32 torus
-(1024 frequencies, 514 decomposed on the half grid), values + vectors.
+Default workload: the largest configuration, one 512->512 3x3 stride-1 periodic conv on a
+64x64 torus (4096 frequencies, 2050 decomposed on the half grid), values + vectors. Other
+workloads (--workload): conv64_k3_n32, resnet18_body, reg4_c128_n32, stem3to64_k7_n224, ...
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--workload NAME]
 
@@ -238,11 +239,53 @@ def run_oracle(lay: W.Layer, seconds: float, nfreq: int, steps: int | None = Non
     r1 = resource.getrusage(resource.RUSAGE_SELF)
     cpu = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
     return {"value": sig / wall, "unit": "singular values/s", "cores": round(cpu / wall, 2),
+            "s_per_frequency": wall / (done * nf),
             "cores_available": os.cpu_count(), "kind": "oracle",
             "sample": f"{done} x {nf} of {lay.F} frequencies of {lay.c_out}->{lay.c_in} k={lay.kh} n={lay.n}: "
                       + ("FP64 symbols + LAPACK SVD with U,V + regulariser grad + dL/dw + one lifted pair"
                          if vectors else "FP64 symbols + LAPACK SVD values"),
             "seconds": round(wall, 3), "step_s": times}
+
+
+def run_oracle_one_core(workload: str, seconds: float, nfreq: int, vectors: bool):
+    """The same oracle sample on one host core: a fresh interpreter whose BLAS/LAPACK and OpenMP
+    pools are limited to one thread before numpy loads (a thread count cannot change afterwards).
+    Returns the cpu_baseline-style dict, or a dict with "error"."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1", VECLIB_MAXIMUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-leg", "--workload", workload,
+           "--cpu-seconds", str(seconds), "--cpu-freqs", str(nfreq)] + ([] if vectors else ["--values-only"])
+    try:
+        r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=max(120.0, 6 * seconds))
+        return json.loads(r.stdout.strip().splitlines()[-1])
+    except (subprocess.SubprocessError, ValueError, IndexError) as e:
+        return {"error": f"one-core oracle leg failed: {e}"}
+
+
+def run_fft_route(lay: W.Layer, svd_s_per_freq: float, vectors: bool, budget_s: float = 5.0):
+    """The paper's comparison route (Sec. II, Table II) on the host in FP64: numpy's fft2 of the
+    zero-padded kernel gives every symbol at once, then one LAPACK SVD per frequency (full grid, no
+    conjugate symmetry, as in the paper). The transform is timed on a block of output channels and
+    scaled to the layer (its cost is proportional to the channel pairs); the per-frequency SVD time
+    is the oracle leg's. Table III splits the paper's time the same way (s_F, s_SVD)."""
+    import oracle as O
+    rows = max(1, min(lay.c_out, int(2 ** 27 // (16 * lay.c_in * lay.n * lay.m))))   # <= 2 GiB complex
+    sub = W.weights(lay)[:rows]
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        O.fft_symbols(sub, lay.n, lay.m, lay.pad_h, lay.pad_w)
+        reps += 1
+        if time.perf_counter() - t0 >= budget_s or reps >= 20:
+            break
+    t_rows = (time.perf_counter() - t0) / reps
+    t_fft = t_rows * lay.c_out / rows
+    t_svd = svd_s_per_freq * lay.F
+    return {"transform_s": t_fft, "svd_s": t_svd, "total_s": t_fft + t_svd,
+            "value": lay.n_sigma / (t_fft + t_svd), "unit": "singular values/s",
+            "sample": f"fft2 of {rows} of {lay.c_out} output channels timed ({reps} reps) and scaled; "
+                      f"SVD time = {lay.F} full-grid frequencies x the oracle leg's time per frequency"
+                      + (" (values and vectors)" if vectors else " (values)")}
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -282,7 +325,7 @@ def run_lfa(args, rank: int, world: int, local_rank: int):
         dw = [torch.empty_like(w) for w in ws]
         l0 = layers[0]
         f_exp = 1 if l0.F > 1 else 0
-        cnt = l0.r
+        cnt = min(l0.r, 64)                   # vector pairs of one frequency lifted per step
         uh = torch.empty((cnt, l0.c_out, l0.n, l0.m), dtype=torch.complex64, device=dev)
         vh = torch.empty((cnt, l0.c_in, l0.sh * l0.n, l0.sw * l0.m), dtype=torch.complex64, device=dev)
         u_ptrs = [u.data_ptr() for u in U]
@@ -354,7 +397,9 @@ def run_lfa(args, rank: int, world: int, local_rank: int):
     for _ in range(3):
         C.lfa_svd(plain.handle, pw, pp, None, None, sptr)
     barrier()
-    pev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(min(K, 50))]
+    # the plain and end-to-end legs repeat the step about 20 s worth (at least 2, at most K, 50)
+    reps_aux = max(2, min(K, 50, int(20000.0 / max(total_ms / K, 1e-3)) + 1))
+    pev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(reps_aux)]
     for e in pev:
         flush.fill_(1)
         e[0].record(stream)
@@ -422,7 +467,7 @@ def run_lfa(args, rank: int, world: int, local_rank: int):
         for st_ in sets:                      # warm both graphs
             st_[1]()
             st_[2]()
-        KE = min(K, 50)
+        KE = reps_aux
         done = [torch.cuda.Event() for _ in range(2)]      # output set free again (its copy finished)
         ready = [torch.cuda.Event() for _ in range(KE)]    # step i computed
         for e in done:
@@ -482,7 +527,8 @@ def run_lfa(args, rank: int, world: int, local_rank: int):
             "workload": args.workload,
             "layers": [layer_name(l) for l in layers],
             "outputs": "values+vectors (U, V per half-grid frequency)" if vectors else "values only",
-            "step": ("fwd(assembly+Jacobi, graph) + regulariser dL/dsigma + bwd dL/dw + lift r vector pairs"
+            "step": ("fwd(assembly+Jacobi, graph) + regulariser dL/dsigma + bwd dL/dw + lift min(r, 64) vector "
+                     "pairs of one frequency"
                      if vectors else "fwd(assembly+Jacobi, all layers in one graph-replayed launch per variant)"),
             "l2": f"flushed between timed steps ({args.flush_mb} MB write, outside the timed events)",
             "parallelism": f"dp{world} (independent layers per rank)",
@@ -526,6 +572,10 @@ def run_lfa(args, rank: int, world: int, local_rank: int):
         s_gpu = sig[0].cpu().numpy()[fr]
         cb["sigma_err_vs_oracle_rel_sigma_max"] = float(np.max(np.abs(s_gpu - s_ref)) / s_ref.max())
         cb.pop("step_s", None)
+        one = run_oracle_one_core(args.workload, args.cpu_seconds, max(1, args.cpu_freqs // 4), vectors)
+        one.pop("step_s", None)
+        cb["one_core"] = one
+        cb["fft_route"] = run_fft_route(layers[0], cb["s_per_frequency"], vectors)
         out["cpu_baseline"] = cb
     if dist is not None:
         dist.destroy_process_group()
@@ -624,10 +674,12 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["lfa", "reference"], default="lfa")
-    ap.add_argument("--workload", default="conv64_k3_n32", choices=sorted(W.WORKLOADS))
+    ap.add_argument("--workload", default="conv512_k3_n64", choices=sorted(W.WORKLOADS))
     ap.add_argument("--flush-mb", type=int, default=256)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--cpu-freqs", type=int, default=64)
+    ap.add_argument("--cpu-freqs", type=int, default=None,
+                    help="oracle frequencies per sample step (default: 64, or 2 for 512-channel layers)")
+    ap.add_argument("--cpu-leg", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--values-only", action="store_true", help="values only (no vectors, backward, lifting)")
     ap.add_argument("--tune-cache", default=DEFAULT_TUNE if os.path.exists(DEFAULT_TUNE) else None,
@@ -644,6 +696,14 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.warmup < 3:
         args.warmup = 3
+    if args.cpu_freqs is None:
+        lay0 = W.layers(args.workload)[0]
+        args.cpu_freqs = 2 if max(lay0.c_out, lay0.cols) >= 512 else 64
+    if args.cpu_leg:
+        # the one-core oracle leg, run by run_oracle_one_core in a fresh interpreter
+        vectors = not (args.values_only or args.workload in VALUES_ONLY)
+        print(json.dumps(run_oracle(W.layers(args.workload)[0], args.cpu_seconds, args.cpu_freqs, vectors=vectors)))
+        return 0
     if args.sweep_n:
         return run_sweep(args)
     if args.impl == "reference":

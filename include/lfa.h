@@ -104,7 +104,9 @@ typedef struct lfa_layer_desc {
 typedef struct lfa_options {
   float tol;            /* one-sided Jacobi threshold: a pair (p, q) is rotated while
                            |x_p^H x_q| > tol * ||x_p|| ||x_q||. <= 0: default
-                           max(2^-22, 4 sqrt(M) 2^-24), M = max(c_out, c_in) */
+                           max(2^-22, 4 sqrt(M) 2^-24), M = max(c_out, c_in), and at most
+                           2^-20 for wide symbols (c_out < c_in), so that A v = sigma u holds
+                           to 1e-5 sigma_max for them too */
   int32_t max_sweeps;   /* sweep cap per symbol; <= 0: default 30 */
   int32_t variant;      /* -1: built-in / autotuned choice; >= 0 forces a kernel variant
                            (see lfa_variant_name) for every layer it can run;
@@ -113,6 +115,19 @@ typedef struct lfa_options {
                            kernel instead of carrying W in registers */
   int32_t use_graph;    /* 1 (default if <0): lfa_svd replays a captured CUDA graph */
   const char* tune_cache; /* nullable path of the autotuner's cache (text); read at plan time */
+  /* Frequency sharding (the frequencies are independent problems, Algorithm 1; the paper calls
+   * LFA embarrassingly parallel, Sec. V). With shard_count = R > 1 every layer's half grid
+   * (F_h frequencies, increasing order) is split into R contiguous ranges, range r being
+   * [floor(r F_h / R), floor((r + 1) F_h / R)), and the plan decomposes range shard_rank only:
+   * one plan per rank (GPU) of a job. F_h, the half-grid list (lfa_layer_query), U, V and the
+   * half-grid sigma then cover the shard only ([F_h_shard][...], in the same order); the
+   * full-grid sigma layout writes only the shard's frequencies and their conjugates.
+   * lfa_svd_backward and lfa_spectral_edit return the shard's contribution (a sum over its
+   * frequencies): the job's dL/dw is the sum over ranks (one all-reduce). lfa_expand and
+   * lfa_regulariser_grad (whose max term spans all frequencies) return LFA_ERR_UNSUPPORTED on a
+   * sharded plan. shard_count <= 1: no sharding (shard_rank must be 0). */
+  int32_t shard_rank;
+  int32_t shard_count;
 } lfa_options_t;
 
 #define LFA_VARIANT_LOGGED 0x10000
@@ -246,13 +261,17 @@ lfa_status_t lfa_regulariser_grad(lfa_plan_t plan, const float* const* sigma, fl
  * Its scratch (twiddles, half-grid list, G_k workspace, partial sums) lives in one
  * file-scope device array of LFA_NOALLOC_SCRATCH_BYTES that every GPU loading the
  * library holds until the process exits. The first call on a device looks up that
- * array's device address (cudaGetSymbolAddress) and caches it; make that first call
- * before any stream capture. All calls share the array and it keeps the last call's
- * contents (each call writes what it reads, nothing must start at zero); calls that
- * overlap on the GPU race. A layer needs about 4*c_out*c_in*kh*kw bytes of partial
- * sums per chunk (at least one chunk in half the array) and 8*c_out*c_in bytes of G per
- * half-grid frequency of a chunk in the other half; layers that do not fit (e.g.
- * c_out = c_in = 512 with k = 3) are rejected with LFA_ERR_UNSUPPORTED before any work.
+ * array's device address (cudaGetSymbolAddress) and caches it per driver context (a
+ * device reset or another current context makes the next call look it up again); make
+ * that first call before any stream capture. All calls share the array and it keeps the
+ * last call's contents (each call writes what it reads, nothing must start at zero);
+ * calls that overlap on the GPU race. A layer needs 4*c_out*c_in*kh*kw bytes of partial
+ * sums per frequency chunk. Stride-1 layers with at most 25 taps keep G_k in registers
+ * and may use the whole array for partial sums (at least one chunk); other layers split
+ * it: partial sums in half of it and 8*c_out*c_in*s_h*s_w bytes of G per half-grid
+ * frequency of a chunk in the rest. Layers that do not fit (e.g. c_out = c_in = 512 with
+ * k = 7: one chunk of partial sums is 51 MB) are rejected with LFA_ERR_UNSUPPORTED
+ * before any work.
  * Asynchronous on `stream`. Errors: LFA_ERR_INVALID_ARG, LFA_ERR_UNSUPPORTED, LFA_ERR_CUDA. */
 lfa_status_t lfa_svd_backward_noalloc(const lfa_layer_desc_t* layer, uint32_t flags, const float* dsigma,
                                       const float* U, const float* V, float* dw, void* stream);

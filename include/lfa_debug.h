@@ -49,6 +49,12 @@ int32_t lfa_debug_variant_fits(int32_t v, int32_t M, int32_t N, int32_t vectors)
  * M x N problem (a replay configuration exists for its pairs), else 0. */
 int32_t lfa_debug_logged_ok(int32_t v, int32_t M, int32_t N);
 
+/* The contiguous half-grid range [*first, *first + *count) that shard `rank` of `count_shards`
+ * decomposes for an n x m torus (lfa_options_t.shard_rank / shard_count): [floor(r F_h / R),
+ * floor((r + 1) F_h / R)). Returns F_h, or -1 on invalid input. */
+int64_t lfa_debug_shard_range(int32_t n, int32_t m, int32_t rank, int32_t count_shards, int64_t* first,
+                              int64_t* count);
+
 #ifdef __cplusplus
 }
 #endif

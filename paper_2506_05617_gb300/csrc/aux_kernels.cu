@@ -564,9 +564,10 @@ cudaError_t launch_backward(const LayerArgs& La, const float* dsigma, int half_o
                             const float2* U, const float2* V, float2* G, int64_t g_cap, float* partial,
                             int chunks, float* dw, cudaStream_t s, int* nkernels) {
   *nkernels = 0;
-  if (La.F_h <= 0) return cudaSuccess;
   const int CW = La.c_out * La.c_w;
   const int kk = La.kh * La.kw;
+  // no frequencies (an empty shard of the half grid): the contribution is zero
+  if (La.F_h <= 0) return cudaMemsetAsync(dw, 0, (size_t)CW * kk * sizeof(float), s);
   if (La.sh == 1 && La.sw == 1 && kk <= 25 && chunks <= 65535) {
     // fused: G never leaves registers
     const int chunk = (La.F_h + chunks - 1) / chunks;

@@ -48,6 +48,13 @@ bool fault(const char* what) {
 
 // --------------------------------------------------------------------------- half grid
 // Frequencies f = j*m + l with f <= fc, fc the index of -k; increasing order.
+// Half-grid range [first, first + count) of shard r of R: [floor(r F_h / R), floor((r + 1) F_h / R)).
+void shard_range(int64_t F_h, int r, int R, int64_t* first, int64_t* count) {
+  const int64_t a = F_h * r / R, b = F_h * (r + 1) / R;
+  *first = a;
+  *count = b - a;
+}
+
 void build_half_grid(int n, int m, std::vector<int32_t>& out) {
   out.clear();
   for (int j = 0; j < n; ++j)
@@ -203,7 +210,9 @@ struct lfa_plan_s {
   std::vector<lfa_layer_desc_t> desc;
   std::vector<LayerArgs> args;        // device table pointers filled, per-call pointers not
   std::vector<int> variant;           // per layer
-  std::vector<std::vector<int32_t>> half_host;
+  std::vector<std::vector<int32_t>> half_host;   // the plan's (shard of the) half grid per layer
+  int shard_rank = 0, shard_count = 1;
+  std::vector<int64_t> shard_first;               // position of the shard's first frequency in the half grid
   // variant groups: one persistent launch each
   struct Group { int variant; std::vector<int> layers; int items; int grid; };
   std::vector<Group> groups;
@@ -247,9 +256,15 @@ lfa_status_t validate_layer(const lfa_layer_desc_t& d) {
   return layer_geometry(d, La) ? LFA_OK : LFA_ERR_INVALID_ARG;
 }
 
-float default_tol(int M) {
-  const float t = 4.f * std::sqrt((float)M) * std::ldexp(1.f, -24);
-  return std::max(t, std::ldexp(1.f, -22));
+// Default Jacobi threshold. One-sided Jacobi on X keeps X w_p = x_p to rounding, so for a tall
+// symbol (X = A_k) A v = sigma u holds exactly and the threshold only has to stay above the fp32
+// noise of the M-term dot products: max(2^-22, 4 sqrt(M) 2^-24). A wide symbol is decomposed as
+// X = A_k^*, and there A v - sigma u = W (X^* x_p - sigma_p^2 e_p) / sigma_p is bounded by the final
+// column orthogonality, tau ||A_k||_F: its threshold is capped at 2^-20 (~9.5e-7), which keeps
+// that residual below 1e-5 sigma_max for 512-column symbols at ~1 more sweep.
+float default_tol(int M, bool wide) {
+  const float t = std::max(4.f * std::sqrt((float)M) * std::ldexp(1.f, -24), std::ldexp(1.f, -22));
+  return wide ? std::min(t, std::ldexp(1.f, -20)) : t;
 }
 
 void free_plan(lfa_plan_s* p) {
@@ -399,6 +414,9 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
     if (st != LFA_OK) return st;
   }
   if (opt && (opt->max_sweeps > 1000 || !(opt->tol < 1.f))) return LFA_ERR_INVALID_ARG;
+  const int shard_count = (opt && opt->shard_count > 1) ? opt->shard_count : 1;
+  const int shard_rank = opt ? opt->shard_rank : 0;
+  if (shard_count > 65536 || shard_rank < 0 || shard_rank >= shard_count) return LFA_ERR_INVALID_ARG;
   if (fault("alloc")) return LFA_ERR_OOM;
 
   int dev = 0;
@@ -426,6 +444,9 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
   p->half_host.resize(nlayers);
   p->bw_chunks.resize(nlayers);
   p->plain_grid.assign(nlayers, 1);
+  p->shard_rank = shard_rank;
+  p->shard_count = shard_count;
+  p->shard_first.assign(nlayers, 0);
 
   // ---- per-layer host tables and variant choice
   size_t bytes = align256(sizeof(Counters));
@@ -438,8 +459,15 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
     std::memset(&La, 0, sizeof La);
     layer_geometry(d, La);   // validated above
     build_half_grid(d.n, d.m, p->half_host[l]);
+    if (shard_count > 1) {
+      int64_t first = 0, count = 0;
+      shard_range((int64_t)p->half_host[l].size(), shard_rank, shard_count, &first, &count);
+      std::vector<int32_t> part(p->half_host[l].begin() + first, p->half_host[l].begin() + first + count);
+      p->half_host[l].swap(part);
+      p->shard_first[l] = first;
+    }
     La.F_h = (int)p->half_host[l].size();
-    const float tol = p->tol_opt > 0.f ? p->tol_opt : default_tol(La.M);
+    const float tol = p->tol_opt > 0.f ? p->tol_opt : default_tol(La.M, La.wide != 0);
     La.tol2 = tol * tol;
     int v = -1;
     bool logged = false;
@@ -496,6 +524,7 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
     for (int l = 0; l < nlayers; ++l) {
       const LayerArgs& La = p->args[l];
       const int64_t CC = (int64_t)La.c_out * La.c_in;
+      if (La.F_h <= 0) { p->bw_chunks[l] = 1; continue; }   // an empty shard
       const int64_t cap = std::max<int64_t>(1, (int64_t)(g_bytes / (CC * 8)));
       int64_t chunks = std::max<int64_t>((155648 + CC - 1) / CC, (La.F_h + cap - 1) / cap);
       chunks = std::min<int64_t>(std::min<int64_t>(chunks, La.F_h), 4096);
@@ -661,6 +690,7 @@ lfa_status_t lfa_symbols(lfa_plan_t p, int32_t layer, const float* w, float* out
 lfa_status_t lfa_expand(lfa_plan_t p, int32_t layer, const float* U, const float* V, int64_t first,
                         int64_t count, float* u_hat, float* v_hat, void* stream) {
   if (p == nullptr || layer < 0 || layer >= p->nlayers || !p->vec) return LFA_ERR_INVALID_ARG;
+  if (p->shard_count > 1) return LFA_ERR_UNSUPPORTED;
   const LayerArgs& La = p->args[layer];
   const int64_t total = (int64_t)La.n * La.m * La.r;
   if (first < 0 || count < 0 || first + count > total) return LFA_ERR_INVALID_ARG;
@@ -728,6 +758,7 @@ lfa_status_t lfa_spectral_edit(lfa_plan_t p, const float* const* sigma, const fl
 lfa_status_t lfa_regulariser_grad(lfa_plan_t p, const float* const* sigma, float lam,
                                   float* const* dsigma, float* const* loss, void* stream) {
   if (p == nullptr || sigma == nullptr || dsigma == nullptr || !std::isfinite(lam)) return LFA_ERR_INVALID_ARG;
+  if (p->shard_count > 1) return LFA_ERR_UNSUPPORTED;
   for (int l = 0; l < p->nlayers; ++l)
     if (!sigma[l] || !dsigma[l]) return LFA_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -754,7 +785,15 @@ lfa_status_t lfa_get_info(lfa_plan_t p, lfa_info_t* info) {
   std::memset(info, 0, sizeof *info);
   for (int l = 0; l < p->nlayers; ++l) {
     info->symbols += p->args[l].F_h;
-    info->singular_values += (int64_t)p->args[l].n * p->args[l].m * p->args[l].r;
+    info->singular_values += p->shard_count > 1 ? 0 : (int64_t)p->args[l].n * p->args[l].m * p->args[l].r;
+    if (p->shard_count > 1) {
+      // the shard's frequencies: a half-grid frequency stands for itself and its conjugate
+      for (int32_t f : p->half_host[l]) {
+        const int j = f / p->args[l].m, ll = f - j * p->args[l].m;
+        const int fc = ((p->args[l].n - j) % p->args[l].n) * p->args[l].m + (p->args[l].m - ll) % p->args[l].m;
+        info->singular_values += (int64_t)(fc == f ? 1 : 2) * p->args[l].r;
+      }
+    }
   }
   info->unconverged = (int64_t)c.unconverged;
   info->nonfinite = (int64_t)c.nonfinite;
@@ -763,7 +802,7 @@ lfa_status_t lfa_get_info(lfa_plan_t p, lfa_info_t* info) {
   info->plan_device_bytes = (int64_t)p->dbytes;
   info->nlayers = p->nlayers;
   info->max_sweeps = p->max_sweeps;
-  info->tol = p->tol_opt > 0.f ? p->tol_opt : default_tol(p->args[0].M);
+  info->tol = p->tol_opt > 0.f ? p->tol_opt : default_tol(p->args[0].M, p->args[0].wide != 0);
   if (c.nonfinite) return LFA_ERR_NONFINITE;
   if (c.unconverged) return LFA_ERR_NOT_CONVERGED;
   return LFA_OK;
@@ -855,6 +894,17 @@ int64_t lfa_debug_half_position(int32_t n, int32_t m, int32_t f) {
 
 int32_t lfa_debug_variant_fits(int32_t v, int32_t M, int32_t N, int32_t vectors) {
   return variant_fits(v, M, N, vectors != 0) ? 1 : 0;
+}
+
+int64_t lfa_debug_shard_range(int32_t n, int32_t m, int32_t rank, int32_t count_shards, int64_t* first,
+                              int64_t* count) {
+  if (n < 1 || m < 1 || (int64_t)n * m > 0x7fffffffLL || count_shards < 1 || count_shards > 65536 || rank < 0 ||
+      rank >= count_shards || first == nullptr || count == nullptr)
+    return -1;
+  const int64_t s = (1 + (n % 2 == 0)) * (1 + (m % 2 == 0));
+  const int64_t F_h = ((int64_t)n * m + s) / 2;
+  shard_range(F_h, rank, count_shards, first, count);
+  return F_h;
 }
 
 int32_t lfa_debug_logged_ok(int32_t v, int32_t M, int32_t N) {

@@ -51,6 +51,7 @@ EXPORTS = [
     "lfa_last_cuda_error", "lfa_kernel_launches", "lfa_version",
     "lfa_debug_schedule", "lfa_debug_half_grid", "lfa_debug_choose_variant", "lfa_debug_variant_count",
     "lfa_debug_tuned_variant", "lfa_debug_variant_fits", "lfa_debug_logged_ok", "lfa_debug_half_position",
+    "lfa_debug_shard_range",
 ]
 
 
@@ -73,7 +74,8 @@ def layer_desc(d) -> "LayerDesc":
 
 class Options(ctypes.Structure):
     _fields_ = [("tol", c_float), ("max_sweeps", c_int32), ("variant", c_int32),
-                ("use_graph", c_int32), ("tune_cache", c_char_p)]
+                ("use_graph", c_int32), ("tune_cache", c_char_p), ("shard_rank", c_int32),
+                ("shard_count", c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -135,6 +137,7 @@ def lib():
         "lfa_debug_variant_fits": (c_int32, [c_int32, c_int32, c_int32, c_int32]),
         "lfa_debug_logged_ok": (c_int32, [c_int32, c_int32, c_int32]),
         "lfa_debug_half_position": (c_int64, [c_int32, c_int32, c_int32]),
+        "lfa_debug_shard_range": (c_int64, [c_int32, c_int32, c_int32, c_int32, POINTER(c_int64), POINTER(c_int64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -166,13 +169,14 @@ def _stream(s) -> Optional[int]:
 
 # ----------------------------------------------------------------------------- entry points
 def lfa_plan(layers: Iterable, flags: int = LFA_VALUES, tol: float = 0.0, max_sweeps: int = 0,
-             variant: int = -1, use_graph: int = -1, tune_cache: Optional[str] = None) -> int:
+             variant: int = -1, use_graph: int = -1, tune_cache: Optional[str] = None,
+             shard_rank: int = 0, shard_count: int = 1) -> int:
     """Creates a plan; ``layers`` holds LayerDesc or
     (c_out, c_in, kh, kw, n, m[, pad_h, pad_w[, stride_h, stride_w]])."""
     descs = [layer_desc(d) for d in layers]
     arr = (LayerDesc * max(1, len(descs)))(*descs)
     opt = Options(float(tol), int(max_sweeps), int(variant), int(use_graph),
-                  tune_cache.encode() if tune_cache else None)
+                  tune_cache.encode() if tune_cache else None, int(shard_rank), int(shard_count))
     h = c_void_p()
     _check(lib().lfa_plan(ctypes.byref(h), arr, len(descs), int(flags), ctypes.byref(opt)), "lfa_plan")
     return int(h.value)
@@ -312,3 +316,10 @@ def lfa_debug_logged_ok(v: int, M: int, N: int) -> bool:
 
 def lfa_debug_half_position(n: int, m: int, f: int) -> int:
     return lib().lfa_debug_half_position(n, m, f)
+
+
+def lfa_debug_shard_range(n: int, m: int, rank: int, count: int):
+    """(F_h, first, count) of shard ``rank`` of ``count`` on an n x m torus; F_h = -1 on invalid input."""
+    a, c = c_int64(0), c_int64(0)
+    F_h = lib().lfa_debug_shard_range(n, m, rank, count, ctypes.byref(a), ctypes.byref(c))
+    return int(F_h), int(a.value), int(c.value)

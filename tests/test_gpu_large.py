@@ -221,3 +221,62 @@ def test_paper_shape_at_n2048_values_sampled():
     fc = ((-j) % lay.n) * lay.m + (-l) % lay.m
     assert np.array_equal(s[fr], s[fc])
     plan.close()
+
+
+def test_regulariser_workload_c128_backward_matches_oracle_on_sampled_frequencies():
+    """The regulariser workload at full size (4 x 128->128 on 32x32, k = 3, 5, 3, 5) with its real
+    loss: dsigma = lfa_regulariser_grad (1 at the layer's sigma_max plus 2 lam (sigma - 1)). The GPU
+    backward is restricted to sampled frequencies by zeroing dsigma elsewhere (each sampled
+    half-grid frequency keeps itself and its conjugate; sigma_max's frequency is always sampled),
+    and compared with the oracle's backward over the same frequencies, once with the oracle's own
+    FP64 U, V (sigma simple there) and once with the GPU's U, V. Tolerance 1e-4 relative."""
+    lays = W.layers("reg4_c128_n32")
+    ws = [W.weights(l) for l in lays]
+    plan = LfaPlan([(l.c_out, l.c_in, l.kh, l.kw, l.n, l.m) for l in lays], vectors=True)
+    sig, U, V = plan.svd([torch.from_numpy(w).cuda() for w in ws])
+    dsig, _ = plan.regulariser_grad(sig, 1e-2)
+    torch.cuda.synchronize()
+    st, info = plan.info()
+    assert st == C.LFA_OK, info
+    masks, samples = [], []
+    for i, l in enumerate(lays):
+        half = O.half_grid(l.n, l.m)
+        s = sig[i].cpu().numpy()
+        fmax = int(np.argmax(s) // l.r)
+        hmax = int(np.searchsorted(half, min(fmax, ((-(fmax // l.m)) % l.n) * l.m + (-(fmax % l.m)) % l.m)))
+        pick = np.unique(np.concatenate([[hmax], np.random.default_rng(20 + i).choice(len(half), 8, replace=False)]))
+        f = half[pick]
+        fc = ((-(f // l.m)) % l.n) * l.m + (-(f % l.m)) % l.m
+        keep = np.zeros(l.F, bool)
+        keep[f] = True
+        keep[fc] = True
+        masks.append(torch.from_numpy(keep).cuda())
+        samples.append((pick, f, np.flatnonzero(keep)))
+    g_masked = [d * m[:, None] for d, m in zip(dsig, masks)]
+    dw = plan.backward(g_masked, U, V)
+    for i, (l, w) in enumerate(zip(lays, ws)):
+        pick, f, full_f = samples[i]
+        g = g_masked[i].cpu().numpy().astype(np.float64)
+        assert g[np.argmax(sig[i].cpu().numpy()) // l.r].max() >= 1.0     # the sigma_max term is in the sample
+        s_or, U_or, V_or = O.lfa_svd(w, l.n, l.m, compute_uv=True, freqs=full_f)
+        gaps = np.min(-np.diff(s_or, axis=1)) / s_or.max()
+        assert gaps > 1e-6                                                # simple singular values
+        ref = O.lfa_backward(w, l.n, l.m, g[full_f], U_or, V_or, freqs=full_f)
+        got = dw[i].cpu().numpy().astype(np.float64)
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err <= 1e-4, (i, err)
+        # the same sum with the GPU's factors (conjugate frequencies take conj(U), conj(V))
+        half = O.half_grid(l.n, l.m)
+        hpos = {int(h): k for k, h in enumerate(half)}
+        Ug, Vg = U[i].cpu().numpy().astype(np.complex128), V[i].cpu().numpy().astype(np.complex128)
+        Uf = np.empty((len(full_f), l.c_out, l.r), np.complex128)
+        Vf = np.empty((len(full_f), l.c_in, l.r), np.complex128)
+        for k, ff in enumerate(full_f):
+            fcc = ((-(ff // l.m)) % l.n) * l.m + (-(ff % l.m)) % l.m
+            if ff in hpos:
+                Uf[k], Vf[k] = Ug[hpos[ff]], Vg[hpos[ff]]
+            else:
+                Uf[k], Vf[k] = np.conj(Ug[hpos[fcc]]), np.conj(Vg[hpos[fcc]])
+        ref_g = O.lfa_backward(w, l.n, l.m, g[full_f], Uf, Vf, freqs=full_f)
+        assert np.linalg.norm(got - ref_g) / np.linalg.norm(ref_g) <= 1e-4
+    plan.close()
