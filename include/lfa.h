@@ -66,7 +66,8 @@ typedef enum lfa_status {
   LFA_ERR_CUDA = 4,          /* a CUDA runtime call failed; see lfa_last_cuda_error() */
   LFA_ERR_NOT_CONVERGED = 5, /* returned by lfa_get_info() when a symbol hit max_sweeps */
   LFA_ERR_NONFINITE = 6,     /* returned by lfa_get_info() when a symbol had NaN/Inf */
-  LFA_ERR_TIMEOUT = 7        /* reserved: a bounded device wait ran out */
+  LFA_ERR_TIMEOUT = 7        /* returned by lfa_get_info() when a bounded device wait (the
+                                tensor-core route's MMA completion) ran out */
 } lfa_status_t;
 
 /* One periodic convolution layer (Sec. III "Convolutional Mappings"):
@@ -131,6 +132,12 @@ typedef struct lfa_options {
 } lfa_options_t;
 
 #define LFA_VARIANT_LOGGED 0x10000
+/* options.variant value selecting the blocked Jacobi route for every layer it can serve
+ * (M, N <= 512; not with LFA_PLAIN): one-sided Jacobi over blocks of 32 columns whose Gram
+ * matrices and block rotations run on the tcgen05 tensor cores with TF32 operands split in
+ * three (hi*hi + hi*lo + lo*hi, FP32 accumulation), one thread-block cluster per symbol.
+ * lfa_layer_query reports it as this value. */
+#define LFA_VARIANT_BLOCKED 0x20000
 
 typedef struct lfa_plan_s* lfa_plan_t;
 
@@ -281,8 +288,9 @@ lfa_status_t lfa_svd_backward_noalloc(const lfa_layer_desc_t* layer, uint32_t fl
 lfa_status_t lfa_destroy(lfa_plan_t plan);
 
 /* Copies the counters of the last lfa_svd into *info (synchronises the plan's
- * last stream). Returns LFA_ERR_NONFINITE if a symbol had NaN/Inf, else
- * LFA_ERR_NOT_CONVERGED if a symbol hit max_sweeps, else LFA_OK. */
+ * last stream). Returns LFA_ERR_TIMEOUT if a bounded device wait ran out, else
+ * LFA_ERR_NONFINITE if a symbol had NaN/Inf, else LFA_ERR_NOT_CONVERGED if a symbol
+ * hit max_sweeps, else LFA_OK. */
 lfa_status_t lfa_get_info(lfa_plan_t plan, lfa_info_t* info);
 
 /* Per-layer queries: half-grid size F_h, r, the kernel variant chosen (with

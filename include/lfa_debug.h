@@ -55,6 +55,20 @@ int32_t lfa_debug_logged_ok(int32_t v, int32_t M, int32_t N);
 int64_t lfa_debug_shard_range(int32_t n, int32_t m, int32_t rank, int32_t count_shards, int64_t* first,
                               int64_t* count);
 
+/* The two tensor-core contractions of the blocked Jacobi route (tcgen05, TF32 operands split into
+ * hi + lo, three products, FP32 accumulation), run by one CTA on caller data; they let tests check
+ * the MMA operand layouts and the 3xTF32 accuracy apart from the Jacobi iteration.
+ * lfa_debug_tc_gram: H = Y^* Y (complex64 [64][64] to D) for Y = the 64 columns cols[] (device
+ *   int32) of the column-major planes (Xr, Xi) (leading dimension ld, a multiple of 4, >= Mp),
+ *   rows [0, Mp), Mp a multiple of 32.
+ * lfa_debug_tc_update: (Or, Oi)[cols] = Y Q over rows [0, rows) (a multiple of 128), Y the columns
+ *   cols[] of (Pr, Pi), Q device complex64 [64][64] row-major.
+ * Both return 0, -1 on invalid arguments, or a CUDA error code; asynchronous on `stream`. */
+int32_t lfa_debug_tc_gram(const float* Xr, const float* Xi, int32_t ld, int32_t Mp, const int32_t* cols, float* D,
+                          void* stream);
+int32_t lfa_debug_tc_update(const float* Pr, const float* Pi, float* Or, float* Oi, int32_t ld, int32_t rows,
+                            const int32_t* cols, const float* Q, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -194,6 +194,7 @@ int tuned_variant(const char* path, int M, int N, bool vec) {
   }
   std::fclose(fh);
   if (log) return vec && logged_ok(found, M, N) ? (found | LFA_VARIANT_LOGGED) : -1;
+  if (found == LFA_VARIANT_BLOCKED) return bj_supported(M, N) ? LFA_VARIANT_BLOCKED : -1;
   return variant_fits(found, M, N, vec) ? found : -1;
 }
 
@@ -220,6 +221,10 @@ struct lfa_plan_s {
   // layers whose W does not fit registers: values-mode forward with a rotation log + replay
   struct Logged { int layer; int variant; int grid; int batch; int log_cap; int sweeps_cap; };
   std::vector<Logged> logged;
+  // layers on the blocked tensor-core route: one cluster launch each
+  struct Blocked { int layer; int clusters; };
+  std::vector<Blocked> blocked;
+  float* bj_ws = nullptr;
   float4* log_ws = nullptr;
   int32_t* rounds_ws = nullptr;
   float2* xraw_ws = nullptr;
@@ -334,6 +339,32 @@ lfa_status_t enqueue_forward(lfa_plan_s* p, const float* const* w, float* const*
       for (int k = 0; k < P.nlayers; ++k)
         LFA_CUDA_TRY(launch_complete(P.L[k], P.L[k].wide ? P.L[k].V : P.L[k].U, P.L[k].F_h, s));
   }
+  // blocked layers: one cluster launch each (queue slot 14), then the completion of zero columns
+  for (const auto& bl : p->blocked) {
+    BJLaunch A{};
+    A.L = p->args[bl.layer];
+    A.L.w = w[bl.layer];
+    A.L.sigma = sigma[bl.layer];
+    A.L.U = p->vec ? reinterpret_cast<float2*>(U[bl.layer]) : nullptr;
+    A.L.V = p->vec ? reinterpret_cast<float2*>(V[bl.layer]) : nullptr;
+    A.L.item_begin = 0;
+    int Mp = 0, Np = 0;
+    bj_dims(A.L.M, A.L.N, &Mp, &Np);
+    A.Mp = Mp;
+    A.Np = Np;
+    A.ldx = Mp;
+    A.ldw = Np;
+    A.ws = p->bj_ws;
+    A.slot_floats = bj_slot_floats(A.L.M, A.L.N, p->vec);
+    A.total_items = A.L.F_h;
+    A.max_sweeps = p->max_sweeps;
+    A.half_output = p->half_output;
+    A.queue_slot = 14;
+    A.counters = p->counters;
+    LFA_CUDA_TRY(cudaMemsetAsync(&p->counters->queue[14], 0, sizeof(unsigned), s));
+    LFA_CUDA_TRY(launch_bj(A, bl.clusters, p->vec, s));
+    if (p->vec) LFA_CUDA_TRY(launch_complete(A.L, A.L.wide ? A.L.V : A.L.U, A.L.F_h, s));
+  }
   // logged layers: per batch of symbols, the values-mode forward that logs its rotations and
   // writes sigma and the X-side vectors, then the replay that builds W
   for (const auto& lg : p->logged) {
@@ -395,6 +426,7 @@ int64_t logged_launches(const lfa_plan_s* p) {
     for (const auto& g : p->groups)
       if (kVariants[g.variant].CS > 1)
         for (int l : g.layers) n += (p->args[l].F_h + 65534) / 65535;
+  for (const auto& bl : p->blocked) n += 1 + (p->vec ? (p->args[bl.layer].F_h + 65534) / 65535 : 0);
   return n;
 }
 
@@ -452,7 +484,7 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
   size_t bytes = align256(sizeof(Counters));
   std::vector<size_t> off_half(nlayers), off_twn(nlayers), off_twm(nlayers);
   size_t sym_bytes = 0, g_need = 0, part_bytes = 0, log_bytes = 0, ranks_bytes = 0, rounds_bytes = 0;
-  size_t wraw_bytes = 0;
+  size_t wraw_bytes = 0, bj_bytes = 0;
   for (int l = 0; l < nlayers; ++l) {
     const lfa_layer_desc_t& d = layers[l];
     LayerArgs& La = p->args[l];
@@ -474,24 +506,36 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
     const bool can_log = p->vec && !p->plain;
     // a requested (option, then autotuner cache) variant, possibly with the rotation-log route
     const int requested[2] = {opt ? opt->variant : -1, tuned_variant(opt ? opt->tune_cache : nullptr, La.M, La.N, p->vec)};
+    bool blocked = false;
     for (int rq : requested) {
-      if (v >= 0 || rq < 0) continue;
-      if (rq & LFA_VARIANT_LOGGED) {
+      if (v >= 0 || blocked || rq < 0) continue;
+      if (rq == LFA_VARIANT_BLOCKED) {
+        if (!p->plain && bj_supported(La.M, La.N)) blocked = true;
+      } else if (rq & LFA_VARIANT_LOGGED) {
         const int id = rq & (LFA_VARIANT_LOGGED - 1);
         if (can_log && id < kNumVariants && logged_ok(id, La.M, La.N)) { v = id; logged = true; }
       } else if (variant_fits(rq, La.M, La.N, p->vec)) {
         v = rq;
       }
     }
-    if (v < 0) v = choose_variant(La.M, La.N, p->vec);
-    if (v < 0 && can_log) {
+    if (blocked) {
+      int clusters = 0;
+      cudaError_t be = bj_max_clusters(La.M, La.N, p->vec, prop.multiProcessorCount, &clusters);
+      if (be != cudaSuccess || clusters < 1) { free_plan(p); return be != cudaSuccess ? from_cuda(be) : LFA_ERR_UNSUPPORTED; }
+      clusters = std::min(clusters, std::max(1, La.F_h));
+      p->blocked.push_back({l, clusters});
+      bj_bytes = std::max(bj_bytes, (size_t)clusters * bj_slot_floats(La.M, La.N, p->vec) * sizeof(float));
+      p->variant[l] = -1;
+    }
+    if (!blocked && v < 0) v = choose_variant(La.M, La.N, p->vec);
+    if (!blocked && v < 0 && can_log) {
       // W does not fit registers next to X: values-mode variant + rotation log + replay
       v = choose_variant(La.M, La.N, false);
       if (v >= 0 && logged_ok(v, La.M, La.N)) logged = true;
       else v = -1;
     }
-    if (v < 0) { free_plan(p); return LFA_ERR_UNSUPPORTED; }
-    p->variant[l] = v;
+    if (!blocked && v < 0) { free_plan(p); return LFA_ERR_UNSUPPORTED; }
+    if (!blocked) p->variant[l] = v;
     if (logged) {
       lfa_plan_s::Logged lg;
       lg.layer = l;
@@ -551,6 +595,7 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
   const size_t off_ranks = bytes; bytes += align256(ranks_bytes);
   const size_t off_rounds = bytes; bytes += align256(rounds_bytes);
   const size_t off_wraw = bytes; bytes += align256(wraw_bytes);
+  const size_t off_bj = bytes; bytes += align256(bj_bytes);
 
   cudaError_t e = cudaMalloc(&p->dmem, bytes);
   if (e != cudaSuccess) { free_plan(p); return from_cuda(e); }
@@ -567,6 +612,7 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
   p->xraw_ws = ranks_bytes ? reinterpret_cast<float2*>(base + off_ranks) : nullptr;
   p->rounds_ws = rounds_bytes ? reinterpret_cast<int32_t*>(base + off_rounds) : nullptr;
   p->wraw_ws = wraw_bytes ? reinterpret_cast<float2*>(base + off_wraw) : nullptr;
+  p->bj_ws = bj_bytes ? reinterpret_cast<float*>(base + off_bj) : nullptr;
 
   // ---- upload tables (synchronous, plan time only)
   std::vector<float2> tw;
@@ -598,7 +644,9 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
     g.variant = v;
     g.items = 0;
     for (int l = 0; l < nlayers; ++l)
-      if (p->variant[l] == v && std::none_of(p->logged.begin(), p->logged.end(),
+      if (p->variant[l] == v && std::none_of(p->blocked.begin(), p->blocked.end(),
+                                              [l](const lfa_plan_s::Blocked& q) { return q.layer == l; }) &&
+          std::none_of(p->logged.begin(), p->logged.end(),
                                               [l](const lfa_plan_s::Logged& q) { return q.layer == l; })) {
         g.layers.push_back(l);
         g.items += (p->args[l].F_h + variant_spu(v) - 1) / variant_spu(v);
@@ -628,7 +676,7 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
     if (e == cudaSuccess) e = jacobi_val_log_grid(lg.variant, p->sms, &lg.grid);
     if (e == cudaSuccess && lg.grid < 1) e = cudaErrorInvalidConfiguration;
   }
-  if (e == cudaSuccess && p->groups.size() > 15) e = cudaErrorInvalidValue;   // slot 15: logged layers
+  if (e == cudaSuccess && p->groups.size() > 14) e = cudaErrorInvalidValue;   // 14: blocked, 15: logged layers
   if (e == cudaSuccess && p->use_graph) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) { free_plan(p); return from_cuda(e); }
   *plan = p;
@@ -803,6 +851,7 @@ lfa_status_t lfa_get_info(lfa_plan_t p, lfa_info_t* info) {
   info->nlayers = p->nlayers;
   info->max_sweeps = p->max_sweeps;
   info->tol = p->tol_opt > 0.f ? p->tol_opt : default_tol(p->args[0].M, p->args[0].wide != 0);
+  if (c.timeouts) return LFA_ERR_TIMEOUT;
   if (c.nonfinite) return LFA_ERR_NONFINITE;
   if (c.unconverged) return LFA_ERR_NOT_CONVERGED;
   return LFA_OK;
@@ -816,7 +865,9 @@ lfa_status_t lfa_layer_query(lfa_plan_t p, int32_t layer, int64_t* F_h, int32_t*
   if (variant) {
     const bool logged = std::any_of(p->logged.begin(), p->logged.end(),
                                     [layer](const lfa_plan_s::Logged& q) { return q.layer == layer; });
-    *variant = p->variant[layer] | (logged ? LFA_VARIANT_LOGGED : 0);
+    const bool blocked = std::any_of(p->blocked.begin(), p->blocked.end(),
+                                     [layer](const lfa_plan_s::Blocked& q) { return q.layer == layer; });
+    *variant = blocked ? LFA_VARIANT_BLOCKED : (p->variant[layer] | (logged ? LFA_VARIANT_LOGGED : 0));
   }
   if (half_grid) std::memcpy(half_grid, p->half_host[layer].data(), p->half_host[layer].size() * 4);
   return LFA_OK;
@@ -837,6 +888,7 @@ const char* lfa_status_string(lfa_status_t s) {
 }
 
 const char* lfa_variant_name(int32_t v) {
+  if (v == LFA_VARIANT_BLOCKED) return "blocked_tc_b32";
   static const std::vector<std::string> logged_names = [] {
     std::vector<std::string> out;
     for (int i = 0; i < kNumVariants; ++i) out.push_back(std::string(kVariantNames[i]) + "_log");

@@ -25,6 +25,7 @@ LFA_VECTORS = 0x2
 LFA_HALF_OUTPUT = 0x4
 LFA_PLAIN = 0x8
 LFA_VARIANT_LOGGED = 0x10000   # options.variant flag: values variant + rotation log + W replay
+LFA_VARIANT_BLOCKED = 0x20000  # options.variant value: blocked Jacobi on the tensor cores
 
 # spectral editing modes
 LFA_EDIT_CLIP = 0
@@ -51,7 +52,7 @@ EXPORTS = [
     "lfa_last_cuda_error", "lfa_kernel_launches", "lfa_version",
     "lfa_debug_schedule", "lfa_debug_half_grid", "lfa_debug_choose_variant", "lfa_debug_variant_count",
     "lfa_debug_tuned_variant", "lfa_debug_variant_fits", "lfa_debug_logged_ok", "lfa_debug_half_position",
-    "lfa_debug_shard_range",
+    "lfa_debug_shard_range", "lfa_debug_tc_gram", "lfa_debug_tc_update",
 ]
 
 
@@ -138,6 +139,9 @@ def lib():
         "lfa_debug_logged_ok": (c_int32, [c_int32, c_int32, c_int32]),
         "lfa_debug_half_position": (c_int64, [c_int32, c_int32, c_int32]),
         "lfa_debug_shard_range": (c_int64, [c_int32, c_int32, c_int32, c_int32, POINTER(c_int64), POINTER(c_int64)]),
+        "lfa_debug_tc_gram": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p]),
+        "lfa_debug_tc_update": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p,
+                                          c_void_p, c_void_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -232,10 +236,11 @@ def lfa_destroy(plan: int) -> None:
 
 
 def lfa_get_info(plan: int):
-    """Returns (status, info dict); status is LFA_OK, LFA_ERR_NOT_CONVERGED or LFA_ERR_NONFINITE."""
+    """Returns (status, info dict); status is LFA_OK, LFA_ERR_NOT_CONVERGED, LFA_ERR_NONFINITE or
+    LFA_ERR_TIMEOUT."""
     info = Info()
     st = lib().lfa_get_info(c_void_p(plan), ctypes.byref(info))
-    if st not in (LFA_OK, LFA_ERR_NOT_CONVERGED, LFA_ERR_NONFINITE):
+    if st not in (LFA_OK, LFA_ERR_NOT_CONVERGED, LFA_ERR_NONFINITE, LFA_ERR_TIMEOUT):
         raise LfaError(st, "lfa_get_info")
     return st, info.as_dict()
 
@@ -323,3 +328,16 @@ def lfa_debug_shard_range(n: int, m: int, rank: int, count: int):
     a, c = c_int64(0), c_int64(0)
     F_h = lib().lfa_debug_shard_range(n, m, rank, count, ctypes.byref(a), ctypes.byref(c))
     return int(F_h), int(a.value), int(c.value)
+
+
+def lfa_debug_tc_gram(Xr: int, Xi: int, ld: int, Mp: int, cols: int, D: int, stream=None) -> int:
+    """Tensor-core Gram of one block pair (see include/lfa_debug.h); returns the status code."""
+    return int(lib().lfa_debug_tc_gram(c_void_p(Xr), c_void_p(Xi), ld, Mp, c_void_p(cols), c_void_p(D),
+                                       _stream(stream)))
+
+
+def lfa_debug_tc_update(Pr: int, Pi: int, Or: int, Oi: int, ld: int, rows: int, cols: int, Q: int,
+                        stream=None) -> int:
+    """Tensor-core update Y Q of one block pair (see include/lfa_debug.h); returns the status code."""
+    return int(lib().lfa_debug_tc_update(c_void_p(Pr), c_void_p(Pi), c_void_p(Or), c_void_p(Oi), ld, rows,
+                                         c_void_p(cols), c_void_p(Q), _stream(stream)))

@@ -97,7 +97,7 @@ def check_factors(S, s, U, V):
         "U orthonormality": np.max(np.abs(np.einsum("hos,hot->hst", np.conj(U), U) - eye)),
         "V orthonormality": np.max(np.abs(np.einsum("hos,hot->hst", np.conj(V), V) - eye)),
     }
-    assert all(v <= VEC_TOL for v in errs.values()), errs
+    assert all(v <= VEC_TOL for v in errs.values()), "; ".join(f"{k} {v:.2e}" for k, v in errs.items())
 
 
 SHAPES = [
