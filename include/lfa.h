@@ -133,9 +133,10 @@ typedef struct lfa_options {
 
 #define LFA_VARIANT_LOGGED 0x10000
 /* options.variant value selecting the blocked Jacobi route for every layer it can serve
- * (M, N <= 512; not with LFA_PLAIN): one-sided Jacobi over blocks of 32 columns whose Gram
- * matrices and block rotations run on the tcgen05 tensor cores with TF32 operands split in
- * three (hi*hi + hi*lo + lo*hi, FP32 accumulation), one thread-block cluster per symbol.
+ * (128 <= N <= 512 columns, M <= 512 rows; not with LFA_PLAIN): one-sided Jacobi over blocks of
+ * 32 columns whose Gram matrices and block rotations run on the tcgen05 tensor cores with TF32
+ * operands split in three (hi*hi + hi*lo + lo*hi, FP32 accumulation), one CTA per symbol. It is
+ * also the built-in choice for tall or square symbols (c_out >= c_in) of 256 columns or more.
  * lfa_layer_query reports it as this value. */
 #define LFA_VARIANT_BLOCKED 0x20000
 

@@ -21,8 +21,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def candidates(M: int, N: int, vectors: bool) -> List[int]:
     """Variant ids that can hold an M x N problem, by the library's own rules: register-resident
-    variants (with W when vectors), and with vectors also the values-mode variants that can run
-    the rotation log and the W replay (flagged LFA_VARIANT_LOGGED)."""
+    variants (with W when vectors), with vectors also the values-mode variants that can run the
+    rotation log and the W replay (flagged LFA_VARIANT_LOGGED), and for 128 to 512 columns the
+    blocked tensor-core route (LFA_VARIANT_BLOCKED)."""
     from . import lfa as C
     out = []
     for v in range(C.lfa_debug_variant_count()):
@@ -30,6 +31,8 @@ def candidates(M: int, N: int, vectors: bool) -> List[int]:
             out.append(v)
         if vectors and C.lfa_debug_logged_ok(v, M, N):
             out.append(v | C.LFA_VARIANT_LOGGED)
+    if M <= 512 and 128 <= N <= 512:
+        out.append(C.LFA_VARIANT_BLOCKED)   # the blocked tensor-core route
     return out
 
 
@@ -98,7 +101,12 @@ def write_cache(path: str, best: Dict[Tuple[int, int, int], Tuple[int, float]]):
             if len(parts) in (4, 5):
                 old[tuple(int(x) for x in parts[:3])] = line.rstrip("\n")
     for (M, N, vec), (v, ms) in best.items():
-        route = f"{v & (C.LFA_VARIANT_LOGGED - 1)} log" if v & C.LFA_VARIANT_LOGGED else f"{v}"
+        if v == C.LFA_VARIANT_BLOCKED:
+            route = "0 blocked"
+        elif v & C.LFA_VARIANT_LOGGED:
+            route = f"{v & (C.LFA_VARIANT_LOGGED - 1)} log"
+        else:
+            route = f"{v}"
         old[(M, N, vec)] = f"{M} {N} {vec} {route}  # {C.lfa_variant_name(v)} {ms:.3f} ms"
     with open(path, "w") as fh:
         fh.write("# LFA Jacobi variant cache: M N vectors variant  (written by paper_2506_05617_gb300.autotune)\n")

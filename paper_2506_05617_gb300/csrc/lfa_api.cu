@@ -173,15 +173,16 @@ bool logged_ok(int v, int M, int N) {
          kVariants[v].NP * kVariants[v].L / kVariants[v].CS >= 32 && N <= 512;
 }
 
-// Optional autotuner cache: text lines "M N vec variant [log]" (first match wins); "log" marks
-// the rotation-log route (returned as variant | LFA_VARIANT_LOGGED).
+// Optional autotuner cache: text lines "M N vec variant [log|blocked]" (first match wins); "log"
+// marks the rotation-log route (returned as variant | LFA_VARIANT_LOGGED), "blocked" the blocked
+// tensor-core route (returned as LFA_VARIANT_BLOCKED).
 int tuned_variant(const char* path, int M, int N, bool vec) {
   if (path == nullptr || path[0] == 0) return -1;
   FILE* fh = std::fopen(path, "r");
   if (!fh) return -1;
   int m, n, v, id, found = -1;
   char line[256], word[16];
-  bool log = false;
+  bool log = false, blk = false;
   while (std::fgets(line, sizeof line, fh)) {
     if (line[0] == '#') continue;
     word[0] = 0;
@@ -189,12 +190,13 @@ int tuned_variant(const char* path, int M, int N, bool vec) {
     if (got >= 4 && m == M && n == N && (v != 0) == vec) {
       found = id;
       log = got == 5 && std::strcmp(word, "log") == 0;
+      blk = got == 5 && std::strcmp(word, "blocked") == 0;
       break;
     }
   }
   std::fclose(fh);
   if (log) return vec && logged_ok(found, M, N) ? (found | LFA_VARIANT_LOGGED) : -1;
-  if (found == LFA_VARIANT_BLOCKED) return bj_supported(M, N) ? LFA_VARIANT_BLOCKED : -1;
+  if (blk || found == LFA_VARIANT_BLOCKED) return bj_supported(M, N) ? LFA_VARIANT_BLOCKED : -1;
   return variant_fits(found, M, N, vec) ? found : -1;
 }
 
@@ -221,8 +223,8 @@ struct lfa_plan_s {
   // layers whose W does not fit registers: values-mode forward with a rotation log + replay
   struct Logged { int layer; int variant; int grid; int batch; int log_cap; int sweeps_cap; };
   std::vector<Logged> logged;
-  // layers on the blocked tensor-core route: one cluster launch each
-  struct Blocked { int layer; int clusters; };
+  // layers on the blocked tensor-core route: one persistent launch each
+  struct Blocked { int layer; int ctas; };
   std::vector<Blocked> blocked;
   float* bj_ws = nullptr;
   float4* log_ws = nullptr;
@@ -339,7 +341,7 @@ lfa_status_t enqueue_forward(lfa_plan_s* p, const float* const* w, float* const*
       for (int k = 0; k < P.nlayers; ++k)
         LFA_CUDA_TRY(launch_complete(P.L[k], P.L[k].wide ? P.L[k].V : P.L[k].U, P.L[k].F_h, s));
   }
-  // blocked layers: one cluster launch each (queue slot 14), then the completion of zero columns
+  // blocked layers: one persistent launch each (queue slot 14), then the completion of zero columns
   for (const auto& bl : p->blocked) {
     BJLaunch A{};
     A.L = p->args[bl.layer];
@@ -362,7 +364,7 @@ lfa_status_t enqueue_forward(lfa_plan_s* p, const float* const* w, float* const*
     A.queue_slot = 14;
     A.counters = p->counters;
     LFA_CUDA_TRY(cudaMemsetAsync(&p->counters->queue[14], 0, sizeof(unsigned), s));
-    LFA_CUDA_TRY(launch_bj(A, bl.clusters, p->vec, s));
+    LFA_CUDA_TRY(launch_bj(A, bl.ctas, p->vec, s));
     if (p->vec) LFA_CUDA_TRY(launch_complete(A.L, A.L.wide ? A.L.V : A.L.U, A.L.F_h, s));
   }
   // logged layers: per batch of symbols, the values-mode forward that logs its rotations and
@@ -518,13 +520,16 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
         v = rq;
       }
     }
+    // built-in choice: the blocked tensor-core route for tall or square symbols of 256 columns and
+    // more (measured faster than the element-wise kernels there, with and without vectors)
+    if (v < 0 && !blocked && !p->plain && !La.wide && La.N >= 256 && bj_supported(La.M, La.N)) blocked = true;
     if (blocked) {
-      int clusters = 0;
-      cudaError_t be = bj_max_clusters(La.M, La.N, p->vec, prop.multiProcessorCount, &clusters);
-      if (be != cudaSuccess || clusters < 1) { free_plan(p); return be != cudaSuccess ? from_cuda(be) : LFA_ERR_UNSUPPORTED; }
-      clusters = std::min(clusters, std::max(1, La.F_h));
-      p->blocked.push_back({l, clusters});
-      bj_bytes = std::max(bj_bytes, (size_t)clusters * bj_slot_floats(La.M, La.N, p->vec) * sizeof(float));
+      int ctas = 0;
+      cudaError_t be = bj_max_ctas(p->vec, prop.multiProcessorCount, &ctas);
+      if (be != cudaSuccess || ctas < 1) { free_plan(p); return be != cudaSuccess ? from_cuda(be) : LFA_ERR_UNSUPPORTED; }
+      ctas = std::min(ctas, std::max(1, La.F_h));
+      p->blocked.push_back({l, ctas});
+      bj_bytes = std::max(bj_bytes, (size_t)ctas * bj_slot_floats(La.M, La.N, p->vec) * sizeof(float));
       p->variant[l] = -1;
     }
     if (!blocked && v < 0) v = choose_variant(La.M, La.N, p->vec);

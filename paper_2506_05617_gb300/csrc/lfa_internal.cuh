@@ -140,13 +140,13 @@ cudaError_t launch_replay(int NP, const ReplayArgs& R, int symbols, cudaStream_t
 cudaError_t prepare_replay(int NP);   // kernel attributes, once per plan
 bool replay_supported(int NP);        // a replay configuration exists for NP pairs
 
-// Blocked one-sided Jacobi on the tensor cores (blocked.cu): one thread-block cluster per symbol,
-// X and W in a per-cluster workspace slot (column-major real / imaginary planes).
+// Blocked one-sided Jacobi on the tensor cores (blocked.cu): one CTA per symbol, X and W in a
+// per-CTA workspace slot (column-major real / imaginary planes).
 struct BJLaunch {
   LayerArgs L;
   int32_t Mp, Np;           // padded rows of X (multiple of 128) and columns (multiple of 128)
   int32_t ldx, ldw;         // leading dimensions of the X and W planes
-  float* ws;                // slots of slot_floats floats, one per cluster of the grid
+  float* ws;                // slots of slot_floats floats, one per CTA of the grid
   size_t slot_floats;
   int32_t total_items;      // symbols of the launch
   int32_t max_sweeps;
@@ -157,8 +157,8 @@ struct BJLaunch {
 bool bj_supported(int M, int N);
 void bj_dims(int M, int N, int* Mp, int* Np);
 size_t bj_slot_floats(int M, int N, bool vec);
-cudaError_t bj_max_clusters(int M, int N, bool vec, int sms, int* clusters);   // co-resident clusters
-cudaError_t launch_bj(const BJLaunch& A, int clusters, bool vec, cudaStream_t s);
+cudaError_t bj_max_ctas(bool vec, int sms, int* ctas);   // co-resident CTAs (kernel attributes set)
+cudaError_t launch_bj(const BJLaunch& A, int ctas, bool vec, cudaStream_t s);
 cudaError_t launch_bj_gram_test(const float* Xr, const float* Xi, int ld, int Mp, const int* cols, float* D,
                                 Counters* ctr, cudaStream_t s);
 cudaError_t launch_bj_update_test(const float* Pr, const float* Pi, float* Or, float* Oi, int ld, int rows,

@@ -32,7 +32,8 @@ BLOCKED = [
     (200, 200, 1, 2, 3, True),
     (400, 130, 3, 2, 1, True),
     (384, 384, 3, 2, 2, True),     # cluster of 6
-    (512, 512, 3, 4, 4, True),     # 10 symbols over the clusters
+    (512, 512, 3, 4, 4, True),     # 10 symbols over the CTAs
+    (200, 300, 3, 2, 2, True),     # wide: X = A^*, threshold capped at 2^-20
 ]
 
 
@@ -54,3 +55,17 @@ def test_blocked_route_matches_oracle(spec):
         check_factors(O.symbols(w, n, m)[half], s[half], U[0].cpu().numpy(), V[0].cpu().numpy())
     print(f"{spec}: sweeps/symbol {info['sweeps'] / info['symbols']:.1f}, rotations {info['rotations']}")
     plan.close()
+
+
+def test_blocked_route_is_the_default_for_wide_channel_layers():
+    """Tall or square symbols of 256 to 512 columns take the blocked route by default (and with the
+    committed autotuner cache); 128 columns and wide symbols keep the element-wise kernels."""
+    import os
+    cache = os.path.join(os.path.dirname(os.path.dirname(__file__)), "paper_2506_05617_gb300", "tune_gb300.txt")
+    for spec, vec, blocked in [((512, 512, 3, 3, 4, 4), True, True), ((512, 512, 3, 3, 4, 4), False, True),
+                               ((256, 256, 3, 3, 4, 4), True, True), ((300, 256, 3, 3, 4, 4), True, True),
+                               ((128, 128, 3, 3, 4, 4), True, False), ((256, 512, 3, 3, 4, 4), True, False)]:
+        for tc in (None, cache):
+            plan = LfaPlan([spec], vectors=vec, tune_cache=tc)
+            assert (plan.meta[0]["variant"] == C.LFA_VARIANT_BLOCKED) == blocked, (spec, vec, tc)
+            plan.close()

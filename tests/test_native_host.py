@@ -157,6 +157,13 @@ def test_tune_cache_parsing_and_rotation_log_routes(tmp_path):
     assert C.lfa_debug_tuned_variant(str(cache), 512, 512, True) == 16 | LOG
     assert C.lfa_debug_tuned_variant(str(cache), 100, 100, True) == -1
     assert C.lfa_debug_tuned_variant(str(tmp_path / "missing.txt"), 64, 64, True) == -1
+    # the blocked tensor-core route by keyword, for the sizes it serves
+    blk = tmp_path / "blk.txt"
+    blk.write_text("512 512 1 0 blocked\n600 64 1 0 blocked\n256 256 0 0 blocked\n")
+    assert C.lfa_debug_tuned_variant(str(blk), 512, 512, True) == C.LFA_VARIANT_BLOCKED
+    assert C.lfa_debug_tuned_variant(str(blk), 256, 256, False) == C.LFA_VARIANT_BLOCKED
+    assert C.lfa_debug_tuned_variant(str(blk), 600, 64, True) == -1          # more than 512 rows
+    assert C.lfa_variant_name(C.LFA_VARIANT_BLOCKED) == "blocked_tc_b32"
     assert C.lfa_variant_name(12 | LOG).endswith("_log")
     # the route exists exactly where a replay configuration serves the variant's pairs
     for v in range(C.lfa_debug_variant_count()):
@@ -175,7 +182,11 @@ def test_committed_tune_cache_parses_for_every_entry():
         M, N, vec = (int(x) for x in parts[:3])
         got = C.lfa_debug_tuned_variant(path, M, N, bool(vec))
         assert got >= 0, line
-        assert (got & C.LFA_VARIANT_LOGGED) == (C.LFA_VARIANT_LOGGED if len(parts) == 5 else 0), line
+        word = parts[4] if len(parts) == 5 else ""
+        if word == "blocked":
+            assert got == C.LFA_VARIANT_BLOCKED, line
+        else:
+            assert (got & C.LFA_VARIANT_LOGGED) == (C.LFA_VARIANT_LOGGED if word == "log" else 0), line
 
 
 @pytest.mark.parametrize("n,m", [(1, 1), (1, 7), (6, 1), (2, 2), (3, 3), (4, 5), (5, 4), (8, 8), (7, 9), (32, 32), (9, 16)])
@@ -220,21 +231,24 @@ AUTOTUNE_SHAPES = [(4, 4), (9, 3), (33, 17), (64, 12), (64, 64), (100, 77), (128
 
 def test_autotuner_candidates_are_exactly_what_a_cache_line_can_select(tmp_path):
     """Every route the autotuner times is one that a cache line can select for that problem, and
-    every route a cache line can select is timed (register variants, and rotation-log routes)."""
+    every route a cache line can select is timed (register variants, rotation-log routes and the
+    blocked tensor-core route)."""
     from paper_2506_05617_gb300 import autotune as A
     cache = str(tmp_path / "tune.txt")
     nv = C.lfa_debug_variant_count()
     for M, N in AUTOTUNE_SHAPES:
         for vec in (False, True):
             accepted = set()
+            routes = [("0 blocked", C.LFA_VARIANT_BLOCKED)]
             for v in range(nv):
-                for route, want in [(f"{v}", v), (f"{v} log", v | C.LFA_VARIANT_LOGGED)]:
-                    if route.endswith("log") and not vec:
-                        continue
-                    with open(cache, "w") as fh:
-                        fh.write(f"{M} {N} {int(vec)} {route}\n")
-                    if C.lfa_debug_tuned_variant(cache, M, N, vec) == want:
-                        accepted.add(want)
+                routes += [(f"{v}", v), (f"{v} log", v | C.LFA_VARIANT_LOGGED)]
+            for route, want in routes:
+                if route.endswith("log") and not vec:
+                    continue
+                with open(cache, "w") as fh:
+                    fh.write(f"{M} {N} {int(vec)} {route}\n")
+                if C.lfa_debug_tuned_variant(cache, M, N, vec) == want:
+                    accepted.add(want)
             cands = A.candidates(M, N, vec)
             assert len(cands) == len(set(cands))
             assert set(cands) == accepted, (M, N, vec, sorted(set(cands) ^ accepted))
