@@ -77,7 +77,7 @@ def executed_flops(layers, info, vectors: bool) -> float:
 def kernel_sha16() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("jacobi.cuh", "jacobi_variants.cuh", "lfa_internal.cuh"):
+    for f in ("jacobi.cuh", "jacobi_variants.cuh", "lfa_internal.cuh", "blocked.cu", "tc_ptx.cuh"):
         with open(os.path.join(ROOT, "paper_2506_05617_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -130,6 +130,29 @@ def lift_pairs(l: W.Layer, target_bytes: int = 512 << 20) -> int:
 
 def fp32_peak_tflops() -> float:
     return SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+# nominal dense tensor-core rates of GB300: TF32 1.1 and BF16 2.25 PFLOP/s
+TF32_PER_BF16 = 1.1 / 2.25
+
+
+def tf32_peak_tflops(peaks: dict):
+    """TF32 tensor peak: the measured sustained cuBLAS BF16 rate (the kernel runs for seconds inside
+    a step) times the nominal TF32 / BF16 ratio; the fallback figure when nothing was measured."""
+    bf16 = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
+    if bf16:
+        return float(bf16) * TF32_PER_BF16, "measured sustained bf16 x nominal TF32/BF16 ratio (1.1/2.25)"
+    return 1700.0 * TF32_PER_BF16, "fallback sustained bf16 (1.7 PFLOP/s) x nominal TF32/BF16 ratio (1.1/2.25)"
+
+
+def blocked_tensor_flops(l: W.Layer, grams: int, updates: int, vectors: bool) -> float:
+    """Tensor-core flops the blocked route issued, from its device counters: a block-pair Gram is the
+    real 128 x 128 product over Mp rows and an update the real product of every 128-row tile of X
+    (and W) with the 128 x 128 real form of Q - I, each as three TF32 products."""
+    M, N = max(l.c_out, l.cols), min(l.c_out, l.cols)
+    Mp, Np = -(-M // 128) * 128, -(-N // 128) * 128
+    per_row = 3 * 2 * 128 * 128
+    return grams * per_row * Mp + updates * per_row * (Mp + (Np if vectors else 0))
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -408,6 +431,47 @@ def run_lfa(args, rank: int, world: int, local_rank: int):
     barrier()
     plain_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in pev]))
 
+    # ---- the FFT route, the paper's comparison system (Table II), on the same GPU: the symbols of
+    # every channel pair from one batched cuFFT transform, then the plain path's Jacobi; timed as a
+    # forward, and its symbol stage alone against the direct tap sums of the plain path
+    fft_leg = None
+    if not args.no_fft_route and all((l.sh, l.sw) == (1, 1) for l in layers):
+        fplan = LfaPlan(specs, vectors=False, fft_route=True, tune_cache=args.tune_cache)
+        fsig, _, _ = fplan.alloc(dev)
+        fp = [x.data_ptr() for x in fsig]
+        for _ in range(2):
+            C.lfa_svd(fplan.handle, pw, fp, None, None, sptr)
+        barrier()
+        fev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(reps_aux)]
+        for e in fev:
+            flush.fill_(4)
+            e[0].record(stream)
+            C.lfa_svd(fplan.handle, pw, fp, None, None, sptr)
+            e[1].record(stream)
+        barrier()
+        fft_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in fev]))
+        l0 = layers[0]
+        symb = torch.empty((plain.meta[0]["F_h"], l0.c_out, l0.cols), dtype=torch.complex64, device=dev)
+        stage = {}
+        for name, call in (("fft_symbols_ms", lambda: C.lfa_fft_symbols(fplan.handle, 0, pw[0], symb.data_ptr(), sptr)),
+                           ("assembly_symbols_ms", lambda: C.lfa_symbols(plain.handle, 0, pw[0], symb.data_ptr(), sptr))):
+            call()
+            barrier()
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.fill_(5)
+            a_.record(stream)
+            for _ in range(5):
+                call()
+            b_.record(stream)
+            barrier()
+            stage[name] = a_.elapsed_time(b_) / 5
+        fft_leg = {"forward_values_ms": fft_ms, "layers_per_s": len(layers) / (fft_ms / 1e3), **stage,
+                   "layer0_symbols": f"{plain.meta[0]['F_h']} half-grid symbols of {l0.c_out}x{l0.cols}",
+                   "route": "cuFFT batched R2C of the zero-padded kernel per channel pair + gather, then the "
+                            "plain path's Jacobi (values)"}
+        del symb
+        fplan.close()
+
     peaks = {}
     if os.path.exists(PEAKS_FILE):
         try:
@@ -509,6 +573,47 @@ def run_lfa(args, rank: int, world: int, local_rank: int):
     peak = fp32_peak_tflops()
     achieved = flops / (fwd_mean / 1e3) / 1e12
     traffic = measured_traffic(args.workload)
+    routes = [m["variant"] for m in plan.meta]
+    if routes[0] == C.LFA_VARIANT_BLOCKED:
+        # the dominant kernel is the blocked Jacobi on the tensor cores (all layers of the workload
+        # on that route): roofline against the TF32 tensor peak
+        tpeak, tsrc = tf32_peak_tflops(peaks)
+        executed = blocked_tensor_flops(layers[0], info["tc_grams"], info["tc_updates"], vectors)
+        roofline = {
+            "kernel": "bj_kernel (blocked one-sided Jacobi, tcgen05 3xTF32 Gram and block updates, %s)" % (
+                "values+vectors" if vectors else "values"),
+            "bound": "tensor",
+            "achieved": achieved,
+            "peak": tpeak,
+            "unit": "TFLOP/s",
+            "frac": achieved / tpeak,
+            "traffic": traffic,
+            "peak_source": tsrc,
+            "flops_model": "nominal Golub-Van Loan complex SVD counts (x4) + symbol assembly, per half-grid symbol",
+            "executed_sweeps_per_symbol": info["sweeps"] / max(1, info["symbols"]),
+            "tensor_grams": info["tc_grams"],
+            "tensor_updates": info["tc_updates"],
+            "executed_tflops": executed / (fwd_mean / 1e3) / 1e12,
+            "executed_frac": executed / (fwd_mean / 1e3) / 1e12 / tpeak,
+            "executed_model": "tensor flops issued: 3 TF32 products per real block product (Gram and update)",
+        }
+    else:
+        roofline = {
+            "kernel": "jacobi_kernel (fused symbol assembly + one-sided Jacobi, %s)" % (
+                "values+vectors" if vectors else "values"),
+            "bound": "alu",
+            "achieved": achieved,
+            "peak": peak,
+            "unit": "TFLOP/s",
+            "frac": achieved / peak,
+            "traffic": traffic,
+            "peak_source": f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz",
+            "flops_model": "nominal Golub-Van Loan complex SVD counts (x4) + symbol assembly, per half-grid symbol",
+            "executed_sweeps_per_symbol": info["sweeps"] / max(1, info["symbols"]),
+            "rotations": info["rotations"],
+            "executed_tflops": executed_flops(layers, info, vectors) / (fwd_mean / 1e3) / 1e12,
+            "executed_frac": executed_flops(layers, info, vectors) / (fwd_mean / 1e3) / 1e12 / peak,
+        }
 
     out = {
         "metric": METRIC,
@@ -538,22 +643,9 @@ def run_lfa(args, rank: int, world: int, local_rank: int):
         "fwd_ms": fwd_mean,
         "plain_fwd_values_ms": plain_ms,
         "plain_layers_per_s": len(layers) / (plain_ms / 1e3),
-        "roofline": {
-            "kernel": "jacobi_kernel (fused symbol assembly + one-sided Jacobi, %s)" % (
-                "values+vectors" if vectors else "values"),
-            "bound": "alu",
-            "achieved": achieved,
-            "peak": peak,
-            "unit": "TFLOP/s",
-            "frac": achieved / peak,
-            "traffic": traffic,
-            "peak_source": f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz",
-            "flops_model": "nominal Golub-Van Loan complex SVD counts (x4) + symbol assembly, per half-grid symbol",
-            "executed_sweeps_per_symbol": info["sweeps"] / max(1, info["symbols"]),
-            "rotations": info["rotations"],
-            "executed_tflops": executed_flops(layers, info, vectors) / (fwd_mean / 1e3) / 1e12,
-            "executed_frac": executed_flops(layers, info, vectors) / (fwd_mean / 1e3) / 1e12 / peak,
-        },
+        "fft_route": fft_leg,
+        "roofline": roofline,
+        "routes": [C.lfa_variant_name(v) for v in routes],
         "clocks": clocks,
         "gpu_launches": int(launches),
         "accuracy": {"unconverged": info["unconverged"], "nonfinite": info["nonfinite"]},
@@ -671,8 +763,8 @@ def run_sweep(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["lfa", "reference"], default="lfa")
     ap.add_argument("--workload", default="conv512_k3_n64", choices=sorted(W.WORKLOADS))
     ap.add_argument("--flush-mb", type=int, default=256)
@@ -681,6 +773,7 @@ def main():
                     help="oracle frequencies per sample step (default: 64, or 2 for 512-channel layers)")
     ap.add_argument("--cpu-leg", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fft-route", action="store_true", help="skip the GPU FFT-route (comparison) leg")
     ap.add_argument("--values-only", action="store_true", help="values only (no vectors, backward, lifting)")
     ap.add_argument("--tune-cache", default=DEFAULT_TUNE if os.path.exists(DEFAULT_TUNE) else None,
                     help="autotuner cache file read by lfa_plan")

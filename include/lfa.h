@@ -100,6 +100,10 @@ typedef struct lfa_layer_desc {
 #define LFA_PLAIN        0x8u  /* plain per-layer path: materialised symbols, one launch per layer
                                   and stage, no graph (the baseline the batched path is measured
                                   against) */
+#define LFA_FFT_ROUTE    0x10u /* the plain path with the symbols from the FFT route, the paper's
+                                  comparison system (Sec. II, Sec. IV Table II): a batched cuFFT
+                                  transform of the zero-padded kernel per channel pair instead of
+                                  the tap sums (stride-1 layers, values only; implies LFA_PLAIN) */
 
 /* Options (nullable pointer: defaults). */
 typedef struct lfa_options {
@@ -154,6 +158,8 @@ typedef struct lfa_info {
   int32_t nlayers;
   int32_t max_sweeps;
   float tol;
+  int64_t tc_grams;         /* blocked tensor-core route: block-pair Gram matrices formed */
+  int64_t tc_updates;       /* blocked tensor-core route: block-pair rotations applied to X (and W) */
 } lfa_info_t;
 
 /* Creates a plan for nlayers layers (Algorithm 1's "SVD with LFA(A, m, n)",
@@ -186,6 +192,13 @@ lfa_status_t lfa_svd(lfa_plan_t plan, const float* const* w, float* const* sigma
  * for all half-grid frequencies: out = device complex64 [F_h][c_out][c_in].
  * Asynchronous. Errors: LFA_ERR_INVALID_ARG. */
 lfa_status_t lfa_symbols(lfa_plan_t plan, int32_t layer, const float* w, float* out, void* stream);
+
+/* The same symbols through the FFT route (plan created with LFA_FFT_ROUTE): the kernel of every
+ * channel pair placed on the n x m grid at its tap offsets (aliasing taps added) and transformed
+ * by cuFFT's batched real-to-complex transform, F = conj(A_k), gathered into
+ * out = device complex64 [F_h][c_out][c_in]. Asynchronous. Errors: LFA_ERR_INVALID_ARG (plan
+ * without LFA_FFT_ROUTE, NULL pointers), LFA_ERR_CUDA. */
+lfa_status_t lfa_fft_symbols(lfa_plan_t plan, int32_t layer, const float* w, float* out, void* stream);
 
 /* Global singular vectors (Sec. III, U^_k = F_k^out U_k, V^_k = F_k^in V_k) of one
  * layer for the flat indices q in [first, first + count), q = f*r + s over the

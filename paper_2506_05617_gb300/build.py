@@ -79,7 +79,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in sources()]
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + ".tmp"
-        cmd = [nv] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs
+        cmd = [nv] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + ["-lcufft"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")

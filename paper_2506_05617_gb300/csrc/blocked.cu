@@ -571,7 +571,7 @@ __global__ void __launch_bounds__(bj::THREADS, 1) bj_kernel(const __grid_constan
     __threadfence_block();
     __syncthreads();
     // ---- sweeps
-    int sweeps = 0, nrot = 0;
+    int sweeps = 0, nrot = 0, ngram = 0, nupd = 0;
     bool converged = false;
     for (;;) {
       int rotated_sweep = 0;
@@ -584,10 +584,12 @@ __global__ void __launch_bounds__(bj::THREADS, 1) bj_kernel(const __grid_constan
           __syncthreads();
           gram_pair(sm, Xr, Xi, ldx, Mp, scols, ctr, ph);
           gram_to_h(sm, La.tol2);
+          ++ngram;
           if (ms->any) {                      // else no pair of the block pair rotates: skip the rest
             nrot += inner_sweep(sm, La.tol2);
             if (ms->rotated) {
               rotated_sweep = 1;
+              ++nupd;
               q_to_operands(sm);
               update_pair(sm, Mat{Xr, Xi, ldx, Mp / RT}, Mat{Wr, Wi, ldw, VEC ? Np / RT : 0}, scols, ctr, ph);
             }
@@ -601,6 +603,8 @@ __global__ void __launch_bounds__(bj::THREADS, 1) bj_kernel(const __grid_constan
     }
     if (threadIdx.x == 0) {
       atomicAdd(&ctr->sweeps, (unsigned long long)sweeps);
+      atomicAdd(&ctr->tc_grams, (unsigned long long)ngram);
+      atomicAdd(&ctr->tc_updates, (unsigned long long)nupd);
       if (!converged) atomicAdd(&ctr->unconverged, 1ull);
     }
     if (threadIdx.x < 32 && nrot) atomicAdd(&ctr->rotations, (unsigned long long)nrot);

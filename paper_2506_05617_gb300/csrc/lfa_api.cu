@@ -206,7 +206,7 @@ int tuned_variant(const char* path, int M, int N, bool vec) {
 struct lfa_plan_s {
   int nlayers = 0;
   uint32_t flags = 0;
-  bool vec = false, half_output = false, plain = false, use_graph = true;
+  bool vec = false, half_output = false, plain = false, use_graph = true, fft = false;
   int max_sweeps = 30;
   float tol_opt = 0.f;
   int device = 0, sms = 0;
@@ -242,6 +242,10 @@ struct lfa_plan_s {
   float* edit_ws = nullptr;                 // phi(sigma) / (n m) of one layer (spectral editing)
   float* reg_ws = nullptr;                  // per-CTA partials of the regulariser
   std::vector<int> bw_chunks;      // per layer
+  // FFT route: a batched cuFFT plan per layer and one workspace for the real grids and spectra
+  std::vector<void*> fft_plans;
+  std::vector<int> fft_pairs;
+  void* fft_ws = nullptr;
   // graph cache
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t graph = nullptr;
@@ -276,6 +280,8 @@ float default_tol(int M, bool wide) {
 
 void free_plan(lfa_plan_s* p) {
   if (!p) return;
+  for (void* h : p->fft_plans)
+    if (h) fft_destroy_plan(h);
   if (p->exec) cudaGraphExecDestroy(p->exec);
   if (p->graph) cudaGraphDestroy(p->graph);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
@@ -296,8 +302,14 @@ lfa_status_t enqueue_forward(lfa_plan_s* p, const float* const* w, float* const*
       La.sigma = sigma[l];
       La.symbols = p->sym_ws;
       La.item_begin = 0;
-      LFA_CUDA_TRY(launch_symbols(La, p->sym_ws, s));
-      g_launches += 1;
+      if (p->fft) {
+        int nk = 0;
+        LFA_CUDA_TRY(launch_fft_symbols(La, p->fft_plans[l], p->fft_pairs[l], p->fft_ws, p->sym_ws, s, &nk));
+        g_launches += nk;
+      } else {
+        LFA_CUDA_TRY(launch_symbols(La, p->sym_ws, s));
+        g_launches += 1;
+      }
       JacobiLaunch P{};
       P.L[0] = La;
       P.nlayers = 1;
@@ -441,7 +453,13 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
   if (plan == nullptr) return LFA_ERR_INVALID_ARG;
   *plan = nullptr;
   if (layers == nullptr || nlayers < 1 || nlayers > kMaxLayers) return LFA_ERR_INVALID_ARG;
-  if (flags & ~(uint32_t)(LFA_VALUES | LFA_VECTORS | LFA_HALF_OUTPUT | LFA_PLAIN)) return LFA_ERR_INVALID_ARG;
+  if (flags & ~(uint32_t)(LFA_VALUES | LFA_VECTORS | LFA_HALF_OUTPUT | LFA_PLAIN | LFA_FFT_ROUTE))
+    return LFA_ERR_INVALID_ARG;
+  if (flags & LFA_FFT_ROUTE) {
+    flags |= LFA_PLAIN;
+    for (int l = 0; l < nlayers; ++l)
+      if ((layers[l].stride_h > 1) || (layers[l].stride_w > 1)) return LFA_ERR_UNSUPPORTED;
+  }
   if ((flags & LFA_PLAIN) && (flags & LFA_VECTORS)) return LFA_ERR_INVALID_ARG;  // plain = values only
   for (int l = 0; l < nlayers; ++l) {
     lfa_status_t st = validate_layer(layers[l]);
@@ -466,6 +484,7 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
   p->vec = (flags & LFA_VECTORS) != 0;
   p->half_output = (flags & LFA_HALF_OUTPUT) != 0;
   p->plain = (flags & LFA_PLAIN) != 0;
+  p->fft = (flags & LFA_FFT_ROUTE) != 0;
   p->max_sweeps = (opt && opt->max_sweeps > 0) ? opt->max_sweeps : 30;
   if (fault("nonconverge")) p->max_sweeps = 1;
   p->tol_opt = opt ? opt->tol : 0.f;
@@ -601,6 +620,19 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
   const size_t off_rounds = bytes; bytes += align256(rounds_bytes);
   const size_t off_wraw = bytes; bytes += align256(wraw_bytes);
   const size_t off_bj = bytes; bytes += align256(bj_bytes);
+  // FFT route: transform batches of channel pairs within 512 MB of real grids and spectra
+  size_t fft_bytes = 0;
+  if (p->fft) {
+    p->fft_pairs.assign(nlayers, 0);
+    p->fft_plans.assign(nlayers, nullptr);
+    for (int l = 0; l < nlayers; ++l) {
+      const LayerArgs& La = p->args[l];
+      const int pairs = std::max(1, fft_chunk_pairs(La, (size_t)512 << 20));
+      p->fft_pairs[l] = pairs;
+      fft_bytes = std::max(fft_bytes, (size_t)pairs * ((size_t)La.n * La.m * 4 + (size_t)La.n * (La.m / 2 + 1) * 8));
+    }
+  }
+  const size_t off_fft = bytes; bytes += align256(fft_bytes);
 
   cudaError_t e = cudaMalloc(&p->dmem, bytes);
   if (e != cudaSuccess) { free_plan(p); return from_cuda(e); }
@@ -618,6 +650,9 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
   p->rounds_ws = rounds_bytes ? reinterpret_cast<int32_t*>(base + off_rounds) : nullptr;
   p->wraw_ws = wraw_bytes ? reinterpret_cast<float2*>(base + off_wraw) : nullptr;
   p->bj_ws = bj_bytes ? reinterpret_cast<float*>(base + off_bj) : nullptr;
+  p->fft_ws = fft_bytes ? static_cast<void*>(base + off_fft) : nullptr;
+  for (int l = 0; l < nlayers && p->fft && e == cudaSuccess; ++l)
+    e = fft_make_plan(p->args[l], p->fft_pairs[l], &p->fft_plans[l]);
 
   // ---- upload tables (synchronous, plan time only)
   std::vector<float2> tw;
@@ -740,6 +775,19 @@ lfa_status_t lfa_symbols(lfa_plan_t p, int32_t layer, const float* w, float* out
   return from_cuda(launch_symbols(La, reinterpret_cast<float2*>(out), static_cast<cudaStream_t>(stream)));
 }
 
+lfa_status_t lfa_fft_symbols(lfa_plan_t p, int32_t layer, const float* w, float* out, void* stream) {
+  if (p == nullptr || !p->fft || w == nullptr || out == nullptr || layer < 0 || layer >= p->nlayers)
+    return LFA_ERR_INVALID_ARG;
+  LayerArgs La = p->args[layer];
+  La.w = w;
+  int nk = 0;
+  const lfa_status_t st = from_cuda(launch_fft_symbols(La, p->fft_plans[layer], p->fft_pairs[layer], p->fft_ws,
+                                                        reinterpret_cast<float2*>(out), static_cast<cudaStream_t>(stream),
+                                                        &nk));
+  g_launches += nk;
+  return st;
+}
+
 lfa_status_t lfa_expand(lfa_plan_t p, int32_t layer, const float* U, const float* V, int64_t first,
                         int64_t count, float* u_hat, float* v_hat, void* stream) {
   if (p == nullptr || layer < 0 || layer >= p->nlayers || !p->vec) return LFA_ERR_INVALID_ARG;
@@ -856,6 +904,8 @@ lfa_status_t lfa_get_info(lfa_plan_t p, lfa_info_t* info) {
   info->nlayers = p->nlayers;
   info->max_sweeps = p->max_sweeps;
   info->tol = p->tol_opt > 0.f ? p->tol_opt : default_tol(p->args[0].M, p->args[0].wide != 0);
+  info->tc_grams = (int64_t)c.tc_grams;
+  info->tc_updates = (int64_t)c.tc_updates;
   if (c.timeouts) return LFA_ERR_TIMEOUT;
   if (c.nonfinite) return LFA_ERR_NONFINITE;
   if (c.unconverged) return LFA_ERR_NOT_CONVERGED;

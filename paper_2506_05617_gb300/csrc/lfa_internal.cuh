@@ -17,6 +17,8 @@ struct Counters {
   unsigned long long sweeps;
   unsigned long long rotations;
   unsigned long long timeouts;   // bounded device waits that ran out (tensor-core route)
+  unsigned long long tc_grams;   // block-pair Gram matrices formed on the tensor cores
+  unsigned long long tc_updates; // block-pair rotations applied on the tensor cores
   unsigned int queue[16];        // work-queue tickets, one per launch of a call
 };
 
@@ -163,6 +165,13 @@ cudaError_t launch_bj_gram_test(const float* Xr, const float* Xi, int ld, int Mp
                                 Counters* ctr, cudaStream_t s);
 cudaError_t launch_bj_update_test(const float* Pr, const float* Pi, float* Or, float* Oi, int ld, int rows,
                                   const int* cols, const float2* Q, Counters* ctr, cudaStream_t s);
+
+// The FFT route to the symbols (fft_route.cu, cuFFT): the paper's comparison system.
+int fft_chunk_pairs(const LayerArgs& La, size_t bytes);                 // channel pairs per transform batch
+cudaError_t fft_make_plan(const LayerArgs& La, int pairs, void** handle);
+void fft_destroy_plan(void* handle);
+cudaError_t launch_fft_symbols(const LayerArgs& La, void* handle, int pairs, void* ws, float2* out, cudaStream_t s,
+                               int* nk);
 
 // Auxiliary kernels (aux_kernels.cu).
 cudaError_t launch_symbols(const LayerArgs& La, float2* out, cudaStream_t s);

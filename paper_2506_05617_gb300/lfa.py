@@ -24,6 +24,7 @@ LFA_VALUES = 0x1
 LFA_VECTORS = 0x2
 LFA_HALF_OUTPUT = 0x4
 LFA_PLAIN = 0x8
+LFA_FFT_ROUTE = 0x10
 LFA_VARIANT_LOGGED = 0x10000   # options.variant flag: values variant + rotation log + W replay
 LFA_VARIANT_BLOCKED = 0x20000  # options.variant value: blocked Jacobi on the tensor cores
 
@@ -46,7 +47,7 @@ LFA_ERR_TIMEOUT = 7
 
 # every symbol include/lfa.h and include/lfa_debug.h declare
 EXPORTS = [
-    "lfa_plan", "lfa_svd", "lfa_symbols", "lfa_expand", "lfa_svd_backward", "lfa_svd_backward_noalloc",
+    "lfa_plan", "lfa_svd", "lfa_symbols", "lfa_fft_symbols", "lfa_expand", "lfa_svd_backward", "lfa_svd_backward_noalloc",
     "lfa_regulariser_grad", "lfa_spectral_edit",
     "lfa_destroy", "lfa_get_info", "lfa_layer_query", "lfa_status_string", "lfa_variant_name",
     "lfa_last_cuda_error", "lfa_kernel_launches", "lfa_version",
@@ -83,7 +84,7 @@ class Info(ctypes.Structure):
     _fields_ = [("symbols", c_int64), ("singular_values", c_int64), ("unconverged", c_int64),
                 ("nonfinite", c_int64), ("sweeps", c_int64), ("rotations", c_int64),
                 ("plan_device_bytes", c_int64), ("nlayers", c_int32), ("max_sweeps", c_int32),
-                ("tol", c_float)]
+                ("tol", c_float), ("tc_grams", c_int64), ("tc_updates", c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -116,6 +117,7 @@ def lib():
         "lfa_plan": (c_int32, [POINTER(c_void_p), POINTER(LayerDesc), c_int32, c_uint32, POINTER(Options)]),
         "lfa_svd": (c_int32, [P, PP, PP, PP, PP, P]),
         "lfa_symbols": (c_int32, [P, c_int32, P, P, P]),
+        "lfa_fft_symbols": (c_int32, [P, c_int32, P, P, P]),
         "lfa_expand": (c_int32, [P, c_int32, P, P, c_int64, c_int64, P, P, P]),
         "lfa_svd_backward": (c_int32, [P, PP, PP, PP, PP, P]),
         "lfa_svd_backward_noalloc": (c_int32, [POINTER(LayerDesc), c_uint32, P, P, P, P, P]),
@@ -195,6 +197,11 @@ def lfa_svd(plan: int, w: Sequence[int], sigma: Sequence[int], U: Optional[Seque
 
 def lfa_symbols(plan: int, layer: int, w: int, out: int, stream=None) -> None:
     _check(lib().lfa_symbols(c_void_p(plan), layer, c_void_p(w), c_void_p(out), _stream(stream)), "lfa_symbols")
+
+
+def lfa_fft_symbols(plan: int, layer: int, w: int, out: int, stream=None) -> None:
+    _check(lib().lfa_fft_symbols(c_void_p(plan), layer, c_void_p(w), c_void_p(out), _stream(stream)),
+           "lfa_fft_symbols")
 
 
 def lfa_expand(plan: int, layer: int, U: int, V: int, first: int, count: int, u_hat: int, v_hat: int,
