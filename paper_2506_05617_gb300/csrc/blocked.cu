@@ -296,12 +296,20 @@ __device__ int inner_sweep(unsigned char* sm, float tol2) {
       if (j.w != 0.f) {
         const int a = pa[qi], b = pb[qi];
         const float cm = j.x, er = j.y, ei = j.z;
+        // every row's pair of entries first, then the rotated values (loads not held up by stores)
+        float2 qa[P / QW], qb[P / QW];
+#pragma unroll
+        for (int k = 0; k < P / QW; ++k) {
+          qa[k] = Q[(qx + QW * k) * P + a];
+          qb[k] = Q[(qx + QW * k) * P + b];
+        }
 #pragma unroll
         for (int k = 0; k < P / QW; ++k) {
           const int x = qx + QW * k;
-          const float2 qa = Q[x * P + a], qb = Q[x * P + b];
-          Q[x * P + a] = make_float2(fmaf(cm, qa.x, qa.x) - (qb.x * er + qb.y * ei), fmaf(cm, qa.y, qa.y) - (qb.y * er - qb.x * ei));
-          Q[x * P + b] = make_float2(fmaf(cm, qb.x, qb.x) + (qa.x * er - qa.y * ei), fmaf(cm, qb.y, qb.y) + (qa.x * ei + qa.y * er));
+          Q[x * P + a] = make_float2(fmaf(cm, qa[k].x, qa[k].x) - (qb[k].x * er + qb[k].y * ei),
+                                     fmaf(cm, qa[k].y, qa[k].y) - (qb[k].y * er - qb[k].x * ei));
+          Q[x * P + b] = make_float2(fmaf(cm, qb[k].x, qb[k].x) + (qa[k].x * er - qa[k].y * ei),
+                                     fmaf(cm, qb[k].y, qb[k].y) + (qa[k].x * ei + qa[k].y * er));
         }
       }
     }
@@ -398,14 +406,17 @@ __device__ void update_pair(unsigned char* sm, Mat m0, Mat m1, const int* cols, 
     float* Y = (part >> 1) ? (first ? m0.im : m1.im) : (first ? m0.re : m1.re);
     const size_t ld = (size_t)(first ? m0.ld : m1.ld);
     const size_t r = (size_t)(first ? T : T - m0.tiles) * RT + orow;
-    float v[32];
-    tc::tmem_ld16(ta, v);
-    tc::tmem_ld16(ta + 16, v + 16);
-    tc::tmem_ld_wait();
+    // all loads of Y first, then the stores: a store between loads to addresses the compiler cannot
+    // tell apart would serialise the 32 L2 round trips
 #pragma unroll
-    for (int q = 0; q < 32; ++q) {
-      const size_t e = (size_t)cols[cq + q] * ld + r;
-      Y[e] = __ldcg(Y + e) + v[q];
+    for (int h = 0; h < 2; ++h) {
+      float v[16], y[16];
+      tc::tmem_ld16(ta + 16 * h, v);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) y[q] = __ldcg(Y + (size_t)cols[cq + 16 * h + q] * ld + r);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int q = 0; q < 16; ++q) Y[(size_t)cols[cq + 16 * h + q] * ld + r] = y[q] + v[q];
     }
     tc::fence_before_sync();
   };
