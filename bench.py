@@ -721,6 +721,26 @@ def run_reference(args):
     }
 
 
+def run_forward_once(args):
+    """One forward of the workload on cuda:0 through the public API (no graph), for profiling."""
+    import torch
+    from paper_2506_05617_gb300 import build as B
+    from paper_2506_05617_gb300.torch_api import LfaPlan
+    B.build()
+    layers = W.layers(args.workload)
+    vectors = not (args.values_only or args.workload in VALUES_ONLY)
+    plan = LfaPlan([l.desc() for l in layers], vectors=vectors, use_graph=0, tune_cache=args.tune_cache)
+    ws = [torch.from_numpy(W.weights(l)).cuda() for l in layers]
+    plan.svd(ws)
+    torch.cuda.synchronize()
+    st, info = plan.info()
+    print(json.dumps({"workload": args.workload, "routes": [m["variant_name"] for m in plan.meta], "status": st,
+                      "sweeps_per_symbol": info["sweeps"] / max(1, info["symbols"]),
+                      "tc_grams": info["tc_grams"], "tc_updates": info["tc_updates"]}))
+    plan.close()
+    return 0 if st == 0 else 1
+
+
 def run_sweep(args):
     """O(N) study: the 64->64 3x3 layer at each torus size n (values + vectors forward), one JSON
     line per n. The time per symbol stays flat once the GPU is full, so the time grows with the
@@ -774,6 +794,9 @@ def main():
     ap.add_argument("--cpu-leg", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fft-route", action="store_true", help="skip the GPU FFT-route (comparison) leg")
+    ap.add_argument("--forward-once", action="store_true",
+                    help="build the workload's plan, run one forward (values + vectors unless values-only) and "
+                         "exit: the small launch a profiler captures")
     ap.add_argument("--values-only", action="store_true", help="values only (no vectors, backward, lifting)")
     ap.add_argument("--tune-cache", default=DEFAULT_TUNE if os.path.exists(DEFAULT_TUNE) else None,
                     help="autotuner cache file read by lfa_plan")
@@ -799,6 +822,8 @@ def main():
         return 0
     if args.sweep_n:
         return run_sweep(args)
+    if args.forward_once:
+        return run_forward_once(args)
     if args.impl == "reference":
         if rank != 0:
             return 0

@@ -60,7 +60,7 @@ int64_t lfa_debug_shard_range(int32_t n, int32_t m, int32_t rank, int32_t count_
  * the MMA operand layouts and the 3xTF32 accuracy apart from the Jacobi iteration.
  * lfa_debug_tc_gram: H = Y^* Y (complex64 [64][64] to D) for Y = the 64 columns cols[] (device
  *   int32) of the column-major planes (Xr, Xi) (leading dimension ld, a multiple of 4, >= Mp),
- *   rows [0, Mp), Mp a multiple of 32.
+ *   rows [0, Mp), Mp a multiple of 64.
  * lfa_debug_tc_update: (Or, Oi)[cols] = Y Q over rows [0, rows) (a multiple of 128), Y the columns
  *   cols[] of (Pr, Pi), Q device complex64 [64][64] row-major.
  * Both return 0, -1 on invalid arguments, or a CUDA error code; asynchronous on `stream`. */

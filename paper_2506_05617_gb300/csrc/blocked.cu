@@ -43,17 +43,17 @@ namespace bj {
 constexpr int B = 32;            // columns per block
 constexpr int P = 2 * B;         // columns of a block pair
 constexpr int THREADS = 512;
-constexpr int KC = 32;           // rows of X per Gram chunk (K of the Gram)
+constexpr int KC = 64;           // rows of X per Gram chunk (K of the Gram)
 constexpr int RT = 128;          // rows of X (or W) per update tile (M of the update)
-constexpr int KU = 8;            // columns of Y per update chunk (K of one MMA)
+constexpr int KU = 16;           // columns of Y per update chunk (K of two MMAs)
 constexpr uint32_t TMEM_COLS = 256;   // Gram D (128 columns), or two update accumulators
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
 constexpr int HS = P + 1;        // row stride of H (float2): a column of H spreads over the banks
 
-// shared memory (bytes)
-//  stage: Gram chunk buffer 0 (32 KB) | two update chunk buffers (16 KB each) | H (64 x 65 float2)
-//  R1:    Gram chunk buffer 1 (32 KB) | Q in fp32 (32 KB) | the update's Q operands (64 KB)
-constexpr int STAGE_BYTES = 33792;
+// shared memory (bytes); one CTA per SM, so chunks are large (fewer barriers and MMA round trips)
+//  stage: Gram chunk buffer 0 (64 KB) | H (64 x 65 float2) | two update chunk buffers (32 KB each)
+//  R1:    Gram chunk buffer 1 (64 KB) | Q in fp32 (32 KB) | the update's Q operands (64 KB)
+constexpr int STAGE_BYTES = 65536;
 constexpr int R1_BYTES = 65536;
 constexpr int OFF_STAGE = 0;
 constexpr int OFF_R1 = OFF_STAGE + STAGE_BYTES;
@@ -98,23 +98,24 @@ __device__ __forceinline__ void wait_buf(unsigned char* sm, Counters* ctr, int b
 // D (TMEM columns [0, 128), 128 x 128 fp32) = Z^T Z over rows [0, Mp) of the 64 columns cols[] of
 // the planes (Xr, Xi): Z column p < 64 is Re x_{cols[p]}, p >= 64 is Im x_{cols[p-64]}. Planes are
 // column-major with leading dimension ld (a multiple of 4); Mp is a multiple of KC.
-// A chunk of KC rows is staged as TF32 hi | lo, core matrix (kc, pg) = (rows 4kc..4kc+3, Z columns
-// 8pg..8pg+7) at byte ((kc * 16 + pg) * 8) * 16: LBO (along K) = 2048 B, SBO (along M/N) = 128 B.
+// A chunk of KC = 64 rows is staged as TF32 hi | lo (32 KB each), core matrix (kc, pg) = (rows
+// 4kc..4kc+3, Z columns 8pg..8pg+7) at byte ((kc * 16 + pg) * 8) * 16: LBO (along K) = 2048 B, SBO
+// (along M/N) = 128 B.
 // Two chunk buffers alternate; each thread loads its next chunk into registers while the tensor
 // core works on the current one.
 __device__ void gram_pair(unsigned char* sm, const float* Xr, const float* Xi, int ld, int Mp, const int* cols,
                           Counters* ctr, uint32_t& ph) {
   Misc* ms = misc(sm);
-  constexpr uint32_t LBO = 2048, SBO = 128, LO = 16384;
+  constexpr uint32_t LBO = 2048, SBO = 128, LO = 32768;
   constexpr uint32_t ID = tc::idesc_tf32(128, 128);
   const uint32_t base0 = tc::smem_u32(sm + OFF_STAGE), base1 = tc::smem_u32(sm + OFF_R1);
-  constexpr int NIT = 1024 / THREADS;             // float4 per thread and chunk
+  constexpr int NIT = KC * 2 * P / 4 / THREADS;   // float4 per thread and chunk
   const float* src[NIT];
   int off[NIT];
 #pragma unroll
   for (int it = 0; it < NIT; ++it) {
-    const int e = threadIdx.x + THREADS * it;       // 1024 float4 per chunk
-    const int plo = e & 7, kc = (e >> 3) & 7, pg = e >> 6;
+    const int e = threadIdx.x + THREADS * it;       // KC * 128 / 4 float4 per chunk
+    const int plo = e & 7, kc = (e >> 3) & (KC / 4 - 1), pg = e / (8 * KC / 4);
     const int p = pg * 8 + plo;
     src[it] = (p < P ? Xr + (size_t)cols[p] * ld : Xi + (size_t)cols[p - P] * ld) + 4 * kc;
     off[it] = ((kc * 16 + pg) * 8 + plo) * 4;
@@ -362,13 +363,13 @@ struct Mat {
 // For every row tile of m0 and then of m1 (m1.tiles may be 0), the 64 columns cols[] of the tile
 // become Y Q = Y + Y (Q - I): Y (Q - I) = [Re Y Re(Q - I) - Im Y Im Q, Re Y Im Q + Im Y Re(Q - I)]
 // on the tensor cores (the R1 operands are those of Q - I), Y added on the CUDA cores.
-// The work is a flat sequence of steps (tile, chunk of KU = 8 columns of Y): a chunk is staged
-// as Re Y hi | lo | Im Y hi | lo (4 KB each, core matrix (kc, rg) = (columns 4kc..4kc+3, rows
+// The work is a flat sequence of steps (tile, chunk of KU = 16 columns of Y): a chunk is staged
+// as Re Y hi | lo | Im Y hi | lo (8 KB each, core matrix (kc, rg) = (columns 4kc..4kc+3, rows
 // 8rg..8rg+7) at byte ((kc * 16 + rg) * 8) * 16: LBO = 2048 B, SBO = 128 B) in one of two buffers,
 // while the next chunk's loads are in flight. Tile T accumulates in TMEM columns 128 (T & 1) +
 // [0, 64) (Re) and + [64, 128) (Im); its epilogue runs while the next tile's MMAs execute.
 __device__ void update_pair(unsigned char* sm, Mat m0, Mat m1, const int* cols, Counters* ctr, uint32_t& ph) {
-  static_assert(THREADS == 512, "the staging map below gives each thread 4 entries of one plane");
+  static_assert(THREADS == 512 && KU == 16, "the staging map below gives each thread a row's column quad");
   Misc* ms = misc(sm);
   float* const stage = reinterpret_cast<float*>(sm + OFF_STAGE);
   const uint32_t s_base = tc::smem_u32(sm + OFF_STAGE);
@@ -378,22 +379,36 @@ __device__ void update_pair(unsigned char* sm, Mat m0, Mat m1, const int* cols, 
   constexpr uint32_t ID_NEG = tc::idesc_tf32(128, 64, false, true);
   constexpr int CH = P / KU;                            // chunks per tile
   const int row = threadIdx.x & (RT - 1);
-  const int kc = (threadIdx.x >> 7) & 1;                // this thread's column quad within a chunk
-  const int pl = threadIdx.x >> 8;                      // its plane: 0 real, 1 imaginary
+  const int kc = threadIdx.x >> 7;                      // this thread's column quad within a chunk
   const int S = (m0.tiles + m1.tiles) * CH;
-  const int soff = ((kc * 16 + (row >> 3)) * 8 + (row & 7)) * 4 + pl * 2048;
-  float4 pre0, pre1;                                    // loads of steps s and s + 1 in flight
-  auto prefetch = [&](int s, float4& v) {
+  const int soff = ((kc * 16 + (row >> 3)) * 8 + (row & 7)) * 4;
+  // real and imaginary quads of steps s and s + 1 in flight
+  float4 pr0, pi0, pr1, pi1;
+  auto prefetch = [&](int s, float4& vr, float4& vi) {
     const int T = s / CH, u = s % CH;
     const bool first = T < m0.tiles;
-    const float* src = pl ? (first ? m0.im : m1.im) : (first ? m0.re : m1.re);
+    const float* re = first ? m0.re : m1.re;
+    const float* im = first ? m0.im : m1.im;
     const size_t ld = (size_t)(first ? m0.ld : m1.ld);
     const size_t r = (size_t)(first ? T : T - m0.tiles) * RT + row;
     const int c0 = u * KU + 4 * kc;
-    v.x = __ldcg(src + (size_t)cols[c0] * ld + r);
-    v.y = __ldcg(src + (size_t)cols[c0 + 1] * ld + r);
-    v.z = __ldcg(src + (size_t)cols[c0 + 2] * ld + r);
-    v.w = __ldcg(src + (size_t)cols[c0 + 3] * ld + r);
+    vr.x = __ldcg(re + (size_t)cols[c0] * ld + r);
+    vr.y = __ldcg(re + (size_t)cols[c0 + 1] * ld + r);
+    vr.z = __ldcg(re + (size_t)cols[c0 + 2] * ld + r);
+    vr.w = __ldcg(re + (size_t)cols[c0 + 3] * ld + r);
+    vi.x = __ldcg(im + (size_t)cols[c0] * ld + r);
+    vi.y = __ldcg(im + (size_t)cols[c0 + 1] * ld + r);
+    vi.z = __ldcg(im + (size_t)cols[c0 + 2] * ld + r);
+    vi.w = __ldcg(im + (size_t)cols[c0 + 3] * ld + r);
+  };
+  auto stage_quad = [&](float* st, float4 v) {     // hi at st, lo 8 KB further
+    float4 h, l;
+    tc::split_tf32(v.x, h.x, l.x);
+    tc::split_tf32(v.y, h.y, l.y);
+    tc::split_tf32(v.z, h.z, l.z);
+    tc::split_tf32(v.w, h.w, l.w);
+    *reinterpret_cast<float4*>(st + soff) = h;
+    *reinterpret_cast<float4*>(st + 2048 + soff) = l;
   };
   // epilogue of tile T: warp w takes TMEM lanes 32 (w % 4) .. (its rows) and 32 columns: part
   // w / 4 = 0, 1 real columns 0-31, 32-63; 2, 3 imaginary
@@ -420,57 +435,52 @@ __device__ void update_pair(unsigned char* sm, Mat m0, Mat m1, const int* cols, 
     }
     tc::fence_before_sync();
   };
-  prefetch(0, pre0);
-  if (S > 1) prefetch(1, pre1);
+  prefetch(0, pr0, pi0);
+  if (S > 1) prefetch(1, pr1, pi1);
   for (int s = 0; s < S; ++s) {
     const int b = s & 1;
-    float* st = stage + b * 4096;                       // 16 KB buffer b
-    {
-      const float4 v = b ? pre1 : pre0;
-      float4 h, l;
-      tc::split_tf32(v.x, h.x, l.x);
-      tc::split_tf32(v.y, h.y, l.y);
-      tc::split_tf32(v.z, h.z, l.z);
-      tc::split_tf32(v.w, h.w, l.w);
-      *reinterpret_cast<float4*>(st + soff) = h;
-      *reinterpret_cast<float4*>(st + 1024 + soff) = l;
-    }
+    float* st = stage + b * 8192;                       // 32 KB buffer b
+    stage_quad(st, b ? pr1 : pr0);
+    stage_quad(st + 4096, b ? pi1 : pi0);
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     if (s + 2 < S) {
-      if (b) prefetch(s + 2, pre1);
-      else prefetch(s + 2, pre0);
+      if (b) prefetch(s + 2, pr1, pi1);
+      else prefetch(s + 2, pr0, pi0);
     }
     if (threadIdx.x == 0 && !ms->failed) {
       tc::fence_after_sync();
       const int T = s / CH, u = s % CH;
-      const uint32_t a0 = s_base + (uint32_t)b * 16384;
-      const uint64_t yrh = tc::smem_desc_kmajor(a0, LBO, SBO);
-      const uint64_t yrl = tc::smem_desc_kmajor(a0 + 4096, LBO, SBO);
-      const uint64_t yih = tc::smem_desc_kmajor(a0 + 8192, LBO, SBO);
-      const uint64_t yil = tc::smem_desc_kmajor(a0 + 12288, LBO, SBO);
-      const uint32_t qo = (uint32_t)(u * KU / 4) * QLBO;
-      const uint64_t qrh = tc::smem_desc_kmajor(q_base + qo, QLBO, QSBO);
-      const uint64_t qrl = tc::smem_desc_kmajor(q_base + 16384 + qo, QLBO, QSBO);
-      const uint64_t qih = tc::smem_desc_kmajor(q_base + 32768 + qo, QLBO, QSBO);
-      const uint64_t qil = tc::smem_desc_kmajor(q_base + 49152 + qo, QLBO, QSBO);
-      const uint32_t acc0 = u > 0 ? 1u : 0u;
       const uint32_t dr = ms->tmem + (uint32_t)(128 * (T & 1)), di = dr + 64;
-      // Re Y' = Re Y Re(Q - I) - Im Y Im Q
-      tc::mma_tf32(dr, yrh, qrh, ID, acc0);
-      tc::mma_tf32(dr, yrh, qrl, ID, 1u);
-      tc::mma_tf32(dr, yrl, qrh, ID, 1u);
-      tc::mma_tf32(dr, yih, qih, ID_NEG, 1u);
-      tc::mma_tf32(dr, yih, qil, ID_NEG, 1u);
-      tc::mma_tf32(dr, yil, qih, ID_NEG, 1u);
-      // Im Y' = Re Y Im Q + Im Y Re(Q - I)
-      tc::mma_tf32(di, yrh, qih, ID, acc0);
-      tc::mma_tf32(di, yrh, qil, ID, 1u);
-      tc::mma_tf32(di, yrl, qih, ID, 1u);
-      tc::mma_tf32(di, yih, qrh, ID, 1u);
-      tc::mma_tf32(di, yih, qrl, ID, 1u);
-      tc::mma_tf32(di, yil, qrh, ID, 1u);
+#pragma unroll
+      for (int k = 0; k < KU / 8; ++k) {
+        const uint32_t a0 = s_base + (uint32_t)b * 32768 + (uint32_t)k * 2 * LBO;
+        const uint64_t yrh = tc::smem_desc_kmajor(a0, LBO, SBO);
+        const uint64_t yrl = tc::smem_desc_kmajor(a0 + 8192, LBO, SBO);
+        const uint64_t yih = tc::smem_desc_kmajor(a0 + 16384, LBO, SBO);
+        const uint64_t yil = tc::smem_desc_kmajor(a0 + 24576, LBO, SBO);
+        const uint32_t qo = (uint32_t)((u * KU + 8 * k) / 4) * QLBO;
+        const uint64_t qrh = tc::smem_desc_kmajor(q_base + qo, QLBO, QSBO);
+        const uint64_t qrl = tc::smem_desc_kmajor(q_base + 16384 + qo, QLBO, QSBO);
+        const uint64_t qih = tc::smem_desc_kmajor(q_base + 32768 + qo, QLBO, QSBO);
+        const uint64_t qil = tc::smem_desc_kmajor(q_base + 49152 + qo, QLBO, QSBO);
+        const uint32_t acc0 = (u > 0 || k > 0) ? 1u : 0u;
+        // Re Y' = Re Y Re(Q - I) - Im Y Im Q
+        tc::mma_tf32(dr, yrh, qrh, ID, acc0);
+        tc::mma_tf32(dr, yrh, qrl, ID, 1u);
+        tc::mma_tf32(dr, yrl, qrh, ID, 1u);
+        tc::mma_tf32(dr, yih, qih, ID_NEG, 1u);
+        tc::mma_tf32(dr, yih, qil, ID_NEG, 1u);
+        tc::mma_tf32(dr, yil, qih, ID_NEG, 1u);
+        // Im Y' = Re Y Im Q + Im Y Re(Q - I)
+        tc::mma_tf32(di, yrh, qih, ID, acc0);
+        tc::mma_tf32(di, yrh, qil, ID, 1u);
+        tc::mma_tf32(di, yrl, qih, ID, 1u);
+        tc::mma_tf32(di, yih, qrh, ID, 1u);
+        tc::mma_tf32(di, yih, qrl, ID, 1u);
+        tc::mma_tf32(di, yil, qrh, ID, 1u);
+      }
       tc::mma_commit(&ms->mbar[b]);
     }
     if (s >= 1) {
@@ -824,10 +834,10 @@ extern "C" {
 
 // The tensor-core Gram of one block pair: H = Y^* Y for the 64 columns cols[] (device int32) of
 // the column-major planes (Xr, Xi) with leading dimension ld over rows [0, Mp) (Mp a multiple of
-// 32, ld a multiple of 4); H written to D as complex64 [64][64]. Returns 0, or the CUDA error.
+// 64, ld a multiple of 4); H written to D as complex64 [64][64]. Returns 0, or the CUDA error.
 int32_t lfa_debug_tc_gram(const float* Xr, const float* Xi, int32_t ld, int32_t Mp, const int32_t* cols, float* D,
                           void* stream) {
-  if (!Xr || !Xi || !cols || !D || ld < Mp || (ld & 3) || Mp < 32 || (Mp & 31)) return -1;
+  if (!Xr || !Xi || !cols || !D || ld < Mp || (ld & 3) || Mp < lfa::bj::KC || (Mp % lfa::bj::KC)) return -1;
   const cudaError_t e = lfa::launch_bj_gram_test(Xr, Xi, ld, Mp, cols, D, nullptr, static_cast<cudaStream_t>(stream));
   return (int32_t)e;
 }

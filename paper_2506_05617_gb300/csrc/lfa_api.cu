@@ -2,6 +2,7 @@
 // convolutions, arXiv 2506.05617). Plans own tables, counters and workspace; all
 // per-call buffers belong to the caller.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <atomic>
@@ -23,6 +24,13 @@
 using namespace lfa;
 
 namespace {
+
+// NVTX range around an entry point (shows the host side of each call on a profiler timeline; a no-op
+// unless a profiler has injected its NVTX library).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 thread_local int32_t g_last_cuda_error = 0;
 std::atomic<int64_t> g_launches{0};
@@ -450,6 +458,7 @@ extern "C" {
 
 lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t nlayers,
                       uint32_t flags, const lfa_options_t* opt) {
+  NvtxRange nvtx_range("lfa_plan");
   if (plan == nullptr) return LFA_ERR_INVALID_ARG;
   *plan = nullptr;
   if (layers == nullptr || nlayers < 1 || nlayers > kMaxLayers) return LFA_ERR_INVALID_ARG;
@@ -725,6 +734,7 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
 
 lfa_status_t lfa_svd(lfa_plan_t p, const float* const* w, float* const* sigma, float* const* U,
                      float* const* V, void* stream) {
+  NvtxRange nvtx_range("lfa_svd");
   if (p == nullptr || w == nullptr || sigma == nullptr) return LFA_ERR_INVALID_ARG;
   if (p->vec && (U == nullptr || V == nullptr)) return LFA_ERR_INVALID_ARG;
   for (int l = 0; l < p->nlayers; ++l) {
@@ -790,6 +800,7 @@ lfa_status_t lfa_fft_symbols(lfa_plan_t p, int32_t layer, const float* w, float*
 
 lfa_status_t lfa_expand(lfa_plan_t p, int32_t layer, const float* U, const float* V, int64_t first,
                         int64_t count, float* u_hat, float* v_hat, void* stream) {
+  NvtxRange nvtx_range("lfa_expand");
   if (p == nullptr || layer < 0 || layer >= p->nlayers || !p->vec) return LFA_ERR_INVALID_ARG;
   if (p->shard_count > 1) return LFA_ERR_UNSUPPORTED;
   const LayerArgs& La = p->args[layer];
@@ -805,6 +816,7 @@ lfa_status_t lfa_expand(lfa_plan_t p, int32_t layer, const float* U, const float
 
 lfa_status_t lfa_svd_backward(lfa_plan_t p, const float* const* dsigma, const float* const* U,
                               const float* const* V, float* const* dw, void* stream) {
+  NvtxRange nvtx_range("lfa_svd_backward");
   if (p == nullptr || !p->vec || dsigma == nullptr || U == nullptr || V == nullptr || dw == nullptr)
     return LFA_ERR_INVALID_ARG;
   for (int l = 0; l < p->nlayers; ++l)
