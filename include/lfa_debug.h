@@ -60,7 +60,7 @@ int64_t lfa_debug_shard_range(int32_t n, int32_t m, int32_t rank, int32_t count_
  * the MMA operand layouts and the 3xTF32 accuracy apart from the Jacobi iteration.
  * lfa_debug_tc_gram: H = Y^* Y (complex64 [64][64] to D) for Y = the 64 columns cols[] (device
  *   int32) of the column-major planes (Xr, Xi) (leading dimension ld, a multiple of 4, >= Mp),
- *   rows [0, Mp), Mp a multiple of 64.
+ *   rows [0, Mp), Mp a multiple of 32.
  * lfa_debug_tc_update: (Or, Oi)[cols] = Y Q over rows [0, rows) (a multiple of 128), Y the columns
  *   cols[] of (Pr, Pi), Q device complex64 [64][64] row-major.
  * Both return 0, -1 on invalid arguments, or a CUDA error code; asynchronous on `stream`. */
@@ -68,6 +68,21 @@ int32_t lfa_debug_tc_gram(const float* Xr, const float* Xi, int32_t ld, int32_t 
                           void* stream);
 int32_t lfa_debug_tc_update(const float* Pr, const float* Pi, float* Or, float* Oi, int32_t ld, int32_t rows,
                             const int32_t* cols, const float* Q, void* stream);
+
+/* Phase profile of the blocked tensor-core route in the last lfa_svd call of a plan (waits for the
+ * plan's last stream): out[0..5] = clock cycles summed over the route's CTAs (thread 0 of each) in
+ * block-pair Grams, inner sweeps, updates, symbol assembly, output, and whole symbols; *ctas = the
+ * CTAs of the route's launch for the plan's first blocked layer (0 when no layer takes the route).
+ * plan is an lfa_plan_t. Returns an lfa_status_t (0 on success, 1 on a NULL argument). */
+int32_t lfa_debug_bj_profile(void* plan, uint64_t* out, int32_t* ctas);
+/* Co-resident CTAs per SM of the blocked route in plans created afterwards: 0 restores the
+ * kernel's own choice (two), 1 launches one per SM. For launch-shape measurements. */
+void lfa_debug_set_bj_ctas_per_sm(int32_t n);
+/* Resources of the blocked route's kernel (values-only or with vectors): out[0] = CTAs per SM the
+ * occupancy calculator admits, out[1] = registers per thread, out[2] = static and out[3] = dynamic
+ * shared memory per CTA in bytes, out[4] = CTAs per SM with 32 KB of dynamic shared memory instead.
+ * Returns an lfa_status_t. */
+int32_t lfa_debug_bj_occupancy(int32_t vectors, int32_t* out);
 
 #ifdef __cplusplus
 }

@@ -128,6 +128,8 @@ WORKLOADS = {
     # the same layer on the 7x7 torus of a ResNet-18's last stage (25 half-grid symbols): the small
     # case of the 512-channel kernels for profiling
     "conv512_k3_n7": [Layer(512, 512, 3, 3, 7, 7, "uniform", 0.0, 51)],
+    # the same layer on 16x16 (130 half-grid symbols: one wave of one symbol per SM)
+    "conv512_k3_n16": [Layer(512, 512, 3, 3, 16, 16, "uniform", 0.0, 51)],
     # stem: 3->64 7x7 on 224x224 (tall 64x3 symbols)
     "stem3to64_k7_n224": [Layer(64, 3, 7, 7, 224, 224, "uniform", 0.0, 52)],
     # stride-2 layers (crystals with 4 polyphase components per coarse cell)

@@ -23,12 +23,13 @@
 //    TF32 pairs) in K-major core-matrix layout; one thread issues the MMAs and an mbarrier
 //    reports their completion.
 //  * The inner 64 x 64 problem runs on the CUDA cores from shared memory.
-//  * One CTA of 512 threads per SM works on one symbol (X and W, 4 MB at 512 x 512, in its
-//    workspace slot), taking the block pairs of each round in turn; CTAs pull symbols from an
-//    atomic work queue. The occupancy calculator admits one CTA of this kernel per SM (measured:
-//    launching two per SM ran no faster), so the CTA is as wide as the register file allows.
-//    (One thread-block cluster per symbol, one block pair per CTA and round, was measured first:
-//    120 CTAs for 512-column symbols, and the rounds waited on the cluster barrier.)
+//  * One CTA of 256 threads works on one symbol (X and W, 4 MB at 512 x 512, in its workspace
+//    slot), taking the block pairs of each round in turn; CTAs pull symbols from an atomic work
+//    queue. Two CTAs share an SM (each ~100 KB of shared memory and half of the tensor memory):
+//    a block pair's phases are chains of barriers and dependent loads, and the other CTA's
+//    symbol fills those gaps. (One 512-thread CTA per SM was measured first: 2.82 s for the
+//    512 -> 512 layer on 64 x 64; one thread-block cluster per symbol, one block pair per CTA and
+//    round, before that: the rounds waited on the cluster barrier.)
 #include <algorithm>
 
 #include "jacobi.cuh"
@@ -42,29 +43,39 @@ namespace bj {
 
 constexpr int B = 32;            // columns per block
 constexpr int P = 2 * B;         // columns of a block pair
-constexpr int THREADS = 512;
-constexpr int KC = 64;           // rows of X per Gram chunk (K of the Gram)
+constexpr int THREADS = 256;
+constexpr int CTAS_PER_SM = 2;   // two symbols per SM: one CTA's barriers and loads hide the other's
+constexpr int MAX_REGS = 120;    // registers per thread: two CTAs of 256 threads fit the register file
+                                 // (at 128 the occupancy calculator admits one)
+constexpr int KC = 32;           // rows of X per Gram chunk (K of the Gram)
 constexpr int RT = 128;          // rows of X (or W) per update tile (M of the update)
-constexpr int KU = 16;           // columns of Y per update chunk (K of two MMAs)
+constexpr int KU = 8;            // columns of Y per update chunk (K of one MMA)
 constexpr uint32_t TMEM_COLS = 256;   // Gram D (128 columns), or two update accumulators
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
 constexpr int HS = P + 1;        // row stride of H (float2): a column of H spreads over the banks
 
-// shared memory (bytes); one CTA per SM, so chunks are large (fewer barriers and MMA round trips)
-//  stage: Gram chunk buffer 0 (64 KB) | H (64 x 65 float2) | two update chunk buffers (32 KB each)
-//  R1:    Gram chunk buffer 1 (64 KB) | Q in fp32 (32 KB) | the update's Q operands (64 KB)
-constexpr int STAGE_BYTES = 65536;
-constexpr int R1_BYTES = 65536;
-constexpr int OFF_STAGE = 0;
-constexpr int OFF_R1 = OFF_STAGE + STAGE_BYTES;
-constexpr int OFF_PRM = OFF_R1 + R1_BYTES;           // float4 [32] rotation parameters of a round
+// Shared memory (bytes). Two CTAs share an SM, so each phase of a block pair reuses one 97 KB
+// region (the phases of one CTA never overlap):
+//  Gram:          chunk buffer 0 [0, 32K) | chunk buffer 1 [32K, 64K)   (TF32 hi | lo, 16 KB each)
+//  inner sweep:   Q in fp32 [0, 32K) | H (64 x 65 float2) [32K, 32K + 33280)
+//  update:        Q operands [0, 64K) | two update chunk buffers [65K, 97K) (16 KB each)
+constexpr int OFF_STAGE = 0;               // Gram buffer 0, Q, Q operands
+constexpr int OFF_R1 = 32768;              // Gram buffer 1, H
+constexpr int OFF_UPD = 66560;             // update chunk buffers (after H)
+constexpr int REGION_BYTES = OFF_UPD + 32768;
+constexpr int OFF_PRM = REGION_BYTES;                // float4 [32] rotation parameters of a round
 constexpr int OFF_PAB = OFF_PRM + 32 * 16;           // int32 [2][32] the round's pairs (a, b)
 constexpr int OFF_TRI = OFF_PAB + 256;               // uint16 [528] pair-block (P, P') table
 constexpr int OFF_PHS = OFF_TRI + 1088;              // float2 [256] phases of the symbol
 constexpr int OFF_MISC = OFF_PHS + kMaxTaps * 8;     // mbarriers, tmem base, flags
 constexpr int SMEM = OFF_MISC + 64;
-static_assert(P * HS * 8 <= STAGE_BYTES, "H fits the staging area");
-static_assert(OFF_R1 % 1024 == 0 && OFF_PRM % 16 == 0 && OFF_PHS % 16 == 0 && OFF_MISC % 16 == 0, "alignment");
+static_assert(OFF_R1 + P * HS * 8 <= OFF_UPD, "H ends before the update buffers");
+static_assert(P * P * 8 <= OFF_R1, "Q (fp32) ends before H");
+static_assert(2 * KC * 2 * P * 4 <= OFF_R1 && 4 * P * P * 4 <= OFF_UPD && OFF_UPD + 2 * 4 * RT * KU * 4 <= REGION_BYTES,
+              "Gram buffers, Q operands and update buffers fit their places");
+static_assert(OFF_R1 % 1024 == 0 && OFF_UPD % 1024 == 0 && OFF_PRM % 16 == 0 && OFF_PHS % 16 == 0 &&
+              OFF_MISC % 16 == 0, "alignment");
+static_assert(CTAS_PER_SM * (SMEM + 2048) <= 233472, "two CTAs per SM");
 
 struct Misc {
   uint64_t mbar[2];     // MMA completion, one per operand buffer
@@ -98,7 +109,7 @@ __device__ __forceinline__ void wait_buf(unsigned char* sm, Counters* ctr, int b
 // D (TMEM columns [0, 128), 128 x 128 fp32) = Z^T Z over rows [0, Mp) of the 64 columns cols[] of
 // the planes (Xr, Xi): Z column p < 64 is Re x_{cols[p]}, p >= 64 is Im x_{cols[p-64]}. Planes are
 // column-major with leading dimension ld (a multiple of 4); Mp is a multiple of KC.
-// A chunk of KC = 64 rows is staged as TF32 hi | lo (32 KB each), core matrix (kc, pg) = (rows
+// A chunk of KC = 32 rows is staged as TF32 hi | lo (16 KB each), core matrix (kc, pg) = (rows
 // 4kc..4kc+3, Z columns 8pg..8pg+7) at byte ((kc * 16 + pg) * 8) * 16: LBO (along K) = 2048 B, SBO
 // (along M/N) = 128 B.
 // Two chunk buffers alternate; each thread loads its next chunk into registers while the tensor
@@ -106,7 +117,7 @@ __device__ __forceinline__ void wait_buf(unsigned char* sm, Counters* ctr, int b
 __device__ void gram_pair(unsigned char* sm, const float* Xr, const float* Xi, int ld, int Mp, const int* cols,
                           Counters* ctr, uint32_t& ph) {
   Misc* ms = misc(sm);
-  constexpr uint32_t LBO = 2048, SBO = 128, LO = 32768;
+  constexpr uint32_t LBO = 2048, SBO = 128, LO = KC * 2 * P * 4;
   constexpr uint32_t ID = tc::idesc_tf32(128, 128);
   const uint32_t base0 = tc::smem_u32(sm + OFF_STAGE), base1 = tc::smem_u32(sm + OFF_R1);
   constexpr int NIT = KC * 2 * P / 4 / THREADS;   // float4 per thread and chunk
@@ -166,23 +177,25 @@ __device__ void gram_pair(unsigned char* sm, const float* Xr, const float* Xi, i
   wait_buf(sm, ctr, (n - 1) & 1, ph);
 }
 
-// H (64 x 64 complex, row-major with row stride HS in the staging area) from the Gram
+// H (64 x 64 complex, row-major with row stride HS at OFF_R1) from the Gram
 // D = [[A, Bm], [Bm^T, C]]: Re H = A + C, Im H = Bm - Bm^T (H = Y^* Y). Warp w reads TMEM lanes
-// 32 (w % 4) .. + 31 (rows of D) and the 32 columns 32 (w / 4) .. + 31. Then every pair (p, q) is tested
-// with the rotation rule: misc->any = 0 means the inner sweep would not rotate at all.
-__device__ void gram_to_h(unsigned char* sm, float tol2) {
+// 32 (w % 4) .. + 31 (rows of D) and, in turn, the column groups g = w / 4, w / 4 + THREADS / 128, ...
+// of D (group g: columns 64 (g / 2) + 32 (g % 2) .. + 31). Then every pair (p, q) the inner sweep
+// visits (all pairs when `full`, else the pairs across the two blocks) is tested with the rotation
+// rule: misc->any = 0 means the inner sweep would not rotate at all.
+__device__ void gram_to_h(unsigned char* sm, float tol2, bool full) {
   Misc* ms = misc(sm);
-  float2* H = reinterpret_cast<float2*>(sm + OFF_STAGE);
+  float2* H = reinterpret_cast<float2*>(sm + OFF_R1);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = 32 * (w & 3) + lane;                  // row of D
-  const int half = (w >> 2) >> 1;                      // D columns [64 half, 64 half + 64) ...
-  const int q0 = ((w >> 2) & 1) * 32;                   // ... of which [q0, q0 + 32)
-  const uint32_t ta = ms->tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(64 * half + q0);
   if (threadIdx.x == 0) ms->any = 0;
   // pass 1: rows < 64 write A (real part) or Bm (imaginary part); pass 2: rows >= 64 add C (real)
   // and subtract Bm^T (imaginary). 32 columns of D per TMEM load.
   for (int pass = 0; pass < 2; ++pass) {
-    {
+    for (int g = w >> 2; g < 4; g += THREADS / 128) {
+      const int half = g >> 1;                          // D columns [64 half, 64 half + 64) ...
+      const int q0 = (g & 1) * 32;                      // ... of which [q0, q0 + 32)
+      const uint32_t ta = ms->tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(64 * half + q0);
       float v[32];
       tc::tmem_ld16(ta, v);
       tc::tmem_ld16(ta + 16, v + 16);
@@ -203,11 +216,11 @@ __device__ void gram_to_h(unsigned char* sm, float tol2) {
     __syncthreads();
   }
   tc::fence_before_sync();
-  // the rotation test on all 2016 pairs of the initial H
+  // the rotation test on the pairs of the initial H that the inner sweep visits
   bool any = false;
   for (int e = threadIdx.x; e < P * P; e += THREADS) {
     const int p = e >> 6, q = e & 63;
-    if (p >= q) continue;
+    if (p >= q || (!full && q < B) || (!full && p >= B)) continue;
     float al = H[p * HS + p].x, be = H[q * HS + q].x;
     const float2 g = H[p * HS + q];
     float gr = g.x, gi = g.y;
@@ -218,20 +231,26 @@ __device__ void gram_to_h(unsigned char* sm, float tol2) {
 }
 
 // ---------------------------------------------------------------------------------- inner sweep
-// Circle-method pair i of round t over 64 indices: (t, 63) for i = 0, else (c(t+i), c(t-i)),
-// c(x) = x mod 63.
-__device__ __forceinline__ void inner_pair(int t, int i, int& a, int& b) {
-  if (i == 0) { a = t; b = P - 1; }
+// Pair i of round t of the inner sweep over the 64 columns of a block pair. A full sweep (63 rounds)
+// takes the circle method over all 64 indices: (t, 63) for i = 0, else (c(t+i), c(t-i)),
+// c(x) = x mod 63. A cross sweep (32 rounds) visits only the 32 x 32 pairs across the two blocks:
+// (i, 32 + (i + t) mod 32). The outer sweep gives every block pair of its first round a full inner
+// sweep (each block occurs once in that round, so every pair inside a block is visited once per
+// outer sweep) and the block pairs of the other rounds a cross sweep: every pair of columns is
+// still rotated at least once per outer sweep, at about half the inner rounds.
+__device__ __forceinline__ void inner_pair(int t, int i, bool full, int& a, int& b) {
+  if (!full) { a = i; b = B + ((i + t) & (B - 1)); }
+  else if (i == 0) { a = t; b = P - 1; }
   else { a = (t + i) % (P - 1); b = (t - i + (P - 1)) % (P - 1); }
 }
 
-// One cyclic two-sided Jacobi sweep on H (staging area) accumulating Q (R1, fp32, starts as I):
+// One cyclic two-sided Jacobi sweep on H (OFF_R1) accumulating Q (OFF_STAGE, fp32, starts as I):
 // per round, 32 threads choose the rotations of the round's 32 disjoint pairs; then
 // H <- J^* H J by 2 x 2 blocks (P <= P') and Q <- Q J, J = [[1 + cm1, es], [-conj(es), 1 + cm1]]
 // per pair. Returns this thread's count of rotations.
-__device__ int inner_sweep(unsigned char* sm, float tol2) {
-  float2* H = reinterpret_cast<float2*>(sm + OFF_STAGE);
-  float2* Q = reinterpret_cast<float2*>(sm + OFF_R1);
+__device__ int inner_sweep(unsigned char* sm, float tol2, bool full) {
+  float2* H = reinterpret_cast<float2*>(sm + OFF_R1);
+  float2* Q = reinterpret_cast<float2*>(sm + OFF_STAGE);
   float4* prm = reinterpret_cast<float4*>(sm + OFF_PRM);
   int* pa = reinterpret_cast<int*>(sm + OFF_PAB);
   int* pb = pa + 32;
@@ -243,10 +262,11 @@ __device__ int inner_sweep(unsigned char* sm, float tol2) {
   constexpr int QW = THREADS / 32;                          // rows of Q per pass
   const int qi = threadIdx.x & 31, qx = threadIdx.x >> 5;   // Q: pair qi, rows qx + QW k
   __syncthreads();
-  for (int t = 0; t < P - 1; ++t) {
+  const int rounds = full ? P - 1 : B;
+  for (int t = 0; t < rounds; ++t) {
     if (threadIdx.x < 32) {
       int a, b;
-      inner_pair(t, threadIdx.x, a, b);
+      inner_pair(t, threadIdx.x, full, a, b);
       float al = H[a * HS + a].x, be = H[b * HS + b].x;
       const float2 g = H[a * HS + b];
       float gr = g.x, gi = g.y;
@@ -319,15 +339,16 @@ __device__ int inner_sweep(unsigned char* sm, float tol2) {
   return nrot;
 }
 
-// Q (R1, fp32 complex, Q[k][n] at k * 64 + n) -> the B operands of the update in R1: Re (Q - I)^T
+// Q (OFF_STAGE, fp32 complex, Q[k][n] at k * 64 + n) -> the B operands of the update in its place
+// (OFF_STAGE, 64 KB, over Q and the first half of H, both dead by then): Re (Q - I)^T
 // and Im Q^T (N = 64 output columns x K = 64), each split into TF32 hi and lo (16 KB each),
 // K-major core matrices (kc, ng) at byte ((kc * 8 + ng) * 8) * 16: LBO = 1024 B, SBO = 128 B.
 // Layout: [Re hi | Re lo | Im hi | Im lo]. The update forms Y (Q - I) on the tensor cores and adds
 // Y exactly on the CUDA cores: the 3xTF32 error (a few fp32 units of each product) then scales
 // with the rotation, which is small once the sweeps near convergence, instead of with Y.
 __device__ void q_to_operands(unsigned char* sm) {
-  float2* Q = reinterpret_cast<float2*>(sm + OFF_R1);
-  float* R = reinterpret_cast<float*>(sm + OFF_R1);
+  float2* Q = reinterpret_cast<float2*>(sm + OFF_STAGE);
+  float* R = reinterpret_cast<float*>(sm + OFF_STAGE);
   constexpr int NQ = P * P / THREADS;
   float2 q[NQ];
 #pragma unroll
@@ -362,19 +383,22 @@ struct Mat {
 
 // For every row tile of m0 and then of m1 (m1.tiles may be 0), the 64 columns cols[] of the tile
 // become Y Q = Y + Y (Q - I): Y (Q - I) = [Re Y Re(Q - I) - Im Y Im Q, Re Y Im Q + Im Y Re(Q - I)]
-// on the tensor cores (the R1 operands are those of Q - I), Y added on the CUDA cores.
-// The work is a flat sequence of steps (tile, chunk of KU = 16 columns of Y): a chunk is staged
-// as Re Y hi | lo | Im Y hi | lo (8 KB each, core matrix (kc, rg) = (columns 4kc..4kc+3, rows
+// on the tensor cores (the operands at OFF_STAGE are those of Q - I), Y added on the CUDA cores.
+// The work is a flat sequence of steps (tile, chunk of KU = 8 columns of Y): a chunk is staged
+// as Re Y hi | lo | Im Y hi | lo (4 KB each, core matrix (kc, rg) = (columns 4kc..4kc+3, rows
 // 8rg..8rg+7) at byte ((kc * 16 + rg) * 8) * 16: LBO = 2048 B, SBO = 128 B) in one of two buffers,
-// while the next chunk's loads are in flight. Tile T accumulates in TMEM columns 128 (T & 1) +
-// [0, 64) (Re) and + [64, 128) (Im); its epilogue runs while the next tile's MMAs execute.
+// while the loads of the next PD chunks are in flight. Tile T accumulates in TMEM columns
+// 128 (T & 1) + [0, 64) (Re) and + [64, 128) (Im); its epilogue runs while the next tile's MMAs
+// execute.
 __device__ void update_pair(unsigned char* sm, Mat m0, Mat m1, const int* cols, Counters* ctr, uint32_t& ph) {
-  static_assert(THREADS == 512 && KU == 16, "the staging map below gives each thread a row's column quad");
+  static_assert(THREADS == 256 && KU == 8, "the staging map below gives each thread a row's column quad");
+  constexpr int PD = 4;                                 // chunks whose loads are in flight
   Misc* ms = misc(sm);
-  float* const stage = reinterpret_cast<float*>(sm + OFF_STAGE);
-  const uint32_t s_base = tc::smem_u32(sm + OFF_STAGE);
-  const uint32_t q_base = tc::smem_u32(sm + OFF_R1);
+  float* const stage = reinterpret_cast<float*>(sm + OFF_UPD);
+  const uint32_t s_base = tc::smem_u32(sm + OFF_UPD);
+  const uint32_t q_base = tc::smem_u32(sm + OFF_STAGE);
   constexpr uint32_t LBO = 2048, SBO = 128, QLBO = 1024, QSBO = 128;
+  constexpr uint32_t PART = RT * KU * 4;                // bytes of one plane part (hi or lo, Re or Im)
   constexpr uint32_t ID = tc::idesc_tf32(128, 64);
   constexpr uint32_t ID_NEG = tc::idesc_tf32(128, 64, false, true);
   constexpr int CH = P / KU;                            // chunks per tile
@@ -382,8 +406,6 @@ __device__ void update_pair(unsigned char* sm, Mat m0, Mat m1, const int* cols, 
   const int kc = threadIdx.x >> 7;                      // this thread's column quad within a chunk
   const int S = (m0.tiles + m1.tiles) * CH;
   const int soff = ((kc * 16 + (row >> 3)) * 8 + (row & 7)) * 4;
-  // real and imaginary quads of steps s and s + 1 in flight
-  float4 pr0, pi0, pr1, pi1;
   auto prefetch = [&](int s, float4& vr, float4& vi) {
     const int T = s / CH, u = s % CH;
     const bool first = T < m0.tiles;
@@ -401,71 +423,76 @@ __device__ void update_pair(unsigned char* sm, Mat m0, Mat m1, const int* cols, 
     vi.z = __ldcg(im + (size_t)cols[c0 + 2] * ld + r);
     vi.w = __ldcg(im + (size_t)cols[c0 + 3] * ld + r);
   };
-  auto stage_quad = [&](float* st, float4 v) {     // hi at st, lo 8 KB further
+  auto stage_quad = [&](float* st, float4 v) {     // hi at st, lo one part further
     float4 h, l;
     tc::split_tf32(v.x, h.x, l.x);
     tc::split_tf32(v.y, h.y, l.y);
     tc::split_tf32(v.z, h.z, l.z);
     tc::split_tf32(v.w, h.w, l.w);
     *reinterpret_cast<float4*>(st + soff) = h;
-    *reinterpret_cast<float4*>(st + 2048 + soff) = l;
+    *reinterpret_cast<float4*>(st + PART / 4 + soff) = l;
   };
-  // epilogue of tile T: warp w takes TMEM lanes 32 (w % 4) .. (its rows) and 32 columns: part
-  // w / 4 = 0, 1 real columns 0-31, 32-63; 2, 3 imaginary
+  // epilogue of tile T: warp w takes TMEM lanes 32 (w % 4) .. (its rows) and, in turn, the parts
+  // w / 4, w / 4 + THREADS / 128, ... of 32 columns: parts 0, 1 real columns 0-31, 32-63; 2, 3
+  // imaginary
   auto epilogue = [&](int T) {
     const bool first = T < m0.tiles;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, part = w >> 2;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int orow = 32 * (w & 3) + lane;
-    const int cq = (part & 1) * 32;
-    const uint32_t ta = ms->tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(128 * (T & 1) + 64 * (part >> 1) + cq);
-    float* Y = (part >> 1) ? (first ? m0.im : m1.im) : (first ? m0.re : m1.re);
     const size_t ld = (size_t)(first ? m0.ld : m1.ld);
     const size_t r = (size_t)(first ? T : T - m0.tiles) * RT + orow;
-    // all loads of Y first, then the stores: a store between loads to addresses the compiler cannot
-    // tell apart would serialise the 32 L2 round trips
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      float v[16], y[16];
-      tc::tmem_ld16(ta + 16 * h, v);
+    for (int part = w >> 2; part < 4; part += THREADS / 128) {
+      const int cq = (part & 1) * 32;
+      const uint32_t ta = ms->tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(128 * (T & 1) + 64 * (part >> 1) + cq);
+      float* Y = (part >> 1) ? (first ? m0.im : m1.im) : (first ? m0.re : m1.re);
+      // all loads of Y first, then the stores: a store between loads to addresses the compiler
+      // cannot tell apart would serialise the 32 L2 round trips
 #pragma unroll
-      for (int q = 0; q < 16; ++q) y[q] = __ldcg(Y + (size_t)cols[cq + 16 * h + q] * ld + r);
-      tc::tmem_ld_wait();
+      for (int h = 0; h < 2; ++h) {
+        float v[16], y[16];
+        tc::tmem_ld16(ta + 16 * h, v);
 #pragma unroll
-      for (int q = 0; q < 16; ++q) Y[(size_t)cols[cq + 16 * h + q] * ld + r] = y[q] + v[q];
+        for (int q = 0; q < 16; ++q) y[q] = __ldcg(Y + (size_t)cols[cq + 16 * h + q] * ld + r);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int q = 0; q < 16; ++q) Y[(size_t)cols[cq + 16 * h + q] * ld + r] = y[q] + v[q];
+      }
     }
     tc::fence_before_sync();
   };
-  prefetch(0, pr0, pi0);
-  if (S > 1) prefetch(1, pr1, pi1);
-  for (int s = 0; s < S; ++s) {
-    const int b = s & 1;
-    float* st = stage + b * 8192;                       // 32 KB buffer b
-    stage_quad(st, b ? pr1 : pr0);
-    stage_quad(st + 4096, b ? pi1 : pi0);
-    tc::fence_proxy_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    if (s + 2 < S) {
-      if (b) prefetch(s + 2, pr1, pi1);
-      else prefetch(s + 2, pr0, pi0);
-    }
-    if (threadIdx.x == 0 && !ms->failed) {
-      tc::fence_after_sync();
-      const int T = s / CH, u = s % CH;
-      const uint32_t dr = ms->tmem + (uint32_t)(128 * (T & 1)), di = dr + 64;
+  float4 pr[PD], pi[PD];
 #pragma unroll
-      for (int k = 0; k < KU / 8; ++k) {
-        const uint32_t a0 = s_base + (uint32_t)b * 32768 + (uint32_t)k * 2 * LBO;
+  for (int j = 0; j < PD; ++j)
+    if (j < S) prefetch(j, pr[j], pi[j]);
+  for (int s0 = 0; s0 < S; s0 += PD) {
+#pragma unroll
+    for (int j = 0; j < PD; ++j) {
+      const int s = s0 + j;
+      if (s >= S) break;                                // uniform over the CTA
+      const int b = j & 1;                              // = s & 1 (PD even)
+      float* st = stage + b * (4 * PART / 4);           // buffer b: Re hi | Re lo | Im hi | Im lo
+      stage_quad(st, pr[j]);
+      stage_quad(st + 2 * PART / 4, pi[j]);
+      tc::fence_proxy_async_smem();
+      tc::fence_before_sync();
+      __syncthreads();
+      if (s + PD < S) prefetch(s + PD, pr[j], pi[j]);
+      if (threadIdx.x == 0 && !ms->failed) {
+        tc::fence_after_sync();
+        const int T = s / CH, u = s % CH;
+        const uint32_t dr = ms->tmem + (uint32_t)(128 * (T & 1)), di = dr + 64;
+        const uint32_t a0 = s_base + (uint32_t)b * 4 * PART;
         const uint64_t yrh = tc::smem_desc_kmajor(a0, LBO, SBO);
-        const uint64_t yrl = tc::smem_desc_kmajor(a0 + 8192, LBO, SBO);
-        const uint64_t yih = tc::smem_desc_kmajor(a0 + 16384, LBO, SBO);
-        const uint64_t yil = tc::smem_desc_kmajor(a0 + 24576, LBO, SBO);
-        const uint32_t qo = (uint32_t)((u * KU + 8 * k) / 4) * QLBO;
+        const uint64_t yrl = tc::smem_desc_kmajor(a0 + PART, LBO, SBO);
+        const uint64_t yih = tc::smem_desc_kmajor(a0 + 2 * PART, LBO, SBO);
+        const uint64_t yil = tc::smem_desc_kmajor(a0 + 3 * PART, LBO, SBO);
+        const uint32_t qo = (uint32_t)((u * KU) / 4) * QLBO;
         const uint64_t qrh = tc::smem_desc_kmajor(q_base + qo, QLBO, QSBO);
         const uint64_t qrl = tc::smem_desc_kmajor(q_base + 16384 + qo, QLBO, QSBO);
         const uint64_t qih = tc::smem_desc_kmajor(q_base + 32768 + qo, QLBO, QSBO);
         const uint64_t qil = tc::smem_desc_kmajor(q_base + 49152 + qo, QLBO, QSBO);
-        const uint32_t acc0 = (u > 0 || k > 0) ? 1u : 0u;
+        const uint32_t acc0 = u > 0 ? 1u : 0u;
         // Re Y' = Re Y Re(Q - I) - Im Y Im Q
         tc::mma_tf32(dr, yrh, qrh, ID, acc0);
         tc::mma_tf32(dr, yrh, qrl, ID, 1u);
@@ -480,12 +507,12 @@ __device__ void update_pair(unsigned char* sm, Mat m0, Mat m1, const int* cols, 
         tc::mma_tf32(di, yih, qrh, ID, 1u);
         tc::mma_tf32(di, yih, qrl, ID, 1u);
         tc::mma_tf32(di, yil, qrh, ID, 1u);
+        tc::mma_commit(&ms->mbar[b]);
       }
-      tc::mma_commit(&ms->mbar[b]);
-    }
-    if (s >= 1) {
-      wait_buf(sm, ctr, (s - 1) & 1, ph);               // step s - 1 done (its buffer is free)
-      if ((s - 1) % CH == CH - 1) epilogue((s - 1) / CH);
+      if (s >= 1) {
+        wait_buf(sm, ctr, (s - 1) & 1, ph);             // step s - 1 done (its buffer is free)
+        if ((s - 1) % CH == CH - 1) epilogue((s - 1) / CH);
+      }
     }
   }
   wait_buf(sm, ctr, (S - 1) & 1, ph);
@@ -543,7 +570,7 @@ __device__ __forceinline__ void outer_pair(int t, int pos, int nb, int& I, int& 
 // pairs in circle-method order (nb - 1 rounds of nb / 2 pairs); then sigma, ranks and the
 // normalised factors written to the layer's outputs. One CTA of 512 threads per SM.
 template <bool VEC>
-__global__ void __launch_bounds__(bj::THREADS, 1) bj_kernel(const __grid_constant__ BJLaunch A) {
+__global__ void __maxnreg__(bj::MAX_REGS) bj_kernel(const __grid_constant__ BJLaunch A) {
   using namespace bj;
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ int scols[P];
@@ -565,11 +592,14 @@ __global__ void __launch_bounds__(bj::THREADS, 1) bj_kernel(const __grid_constan
   uint32_t ph = 0;   // mbarrier phase parities (see wait_buf)
   unsigned int* queue = &ctr->queue[A.queue_slot];
 
+  // phase clocks of thread 0: Gram, inner sweep, update, assembly, output, whole symbols
+  unsigned long long cyc[6] = {0, 0, 0, 0, 0, 0};
   for (;;) {
     if (threadIdx.x == 0) ms->item = (int)atomicAdd(queue, 1u);
     __syncthreads();
     const int h = ms->item;
     if (h >= A.total_items) break;
+    const long long c_sym = clock64();
     const int f = La.half[h];
     const int jj = f / La.m, ll = f - jj * La.m;
     const int kk = La.kh * La.kw;
@@ -591,6 +621,8 @@ __global__ void __launch_bounds__(bj::THREADS, 1) bj_kernel(const __grid_constan
     }
     __threadfence_block();
     __syncthreads();
+    long long c_ph = clock64();
+    cyc[3] += (unsigned long long)(c_ph - c_sym);
     // ---- sweeps
     int sweeps = 0, nrot = 0, ngram = 0, nupd = 0;
     bool converged = false;
@@ -604,10 +636,17 @@ __global__ void __launch_bounds__(bj::THREADS, 1) bj_kernel(const __grid_constan
           if (threadIdx.x == 0) ms->rotated = 0;
           __syncthreads();
           gram_pair(sm, Xr, Xi, ldx, Mp, scols, ctr, ph);
-          gram_to_h(sm, La.tol2);
+          const bool full = (t == 0);         // the first round of the sweep: intra-block pairs too
+          gram_to_h(sm, La.tol2, full);
           ++ngram;
+          long long c1 = clock64();
+          cyc[0] += (unsigned long long)(c1 - c_ph);
+          c_ph = c1;
           if (ms->any) {                      // else no pair of the block pair rotates: skip the rest
-            nrot += inner_sweep(sm, La.tol2);
+            nrot += inner_sweep(sm, La.tol2, full);
+            c1 = clock64();
+            cyc[1] += (unsigned long long)(c1 - c_ph);
+            c_ph = c1;
             if (ms->rotated) {
               rotated_sweep = 1;
               ++nupd;
@@ -616,6 +655,9 @@ __global__ void __launch_bounds__(bj::THREADS, 1) bj_kernel(const __grid_constan
             }
           }
           __syncthreads();
+          c1 = clock64();
+          cyc[2] += (unsigned long long)(c1 - c_ph);
+          c_ph = c1;
         }
       }
       ++sweeps;
@@ -721,9 +763,16 @@ __global__ void __launch_bounds__(bj::THREADS, 1) bj_kernel(const __grid_constan
       __syncthreads();
     }
     __syncthreads();   // the slot is reused by the CTA's next symbol
+    const long long c_end = clock64();
+    cyc[4] += (unsigned long long)(c_end - c_ph);
+    cyc[5] += (unsigned long long)(c_end - c_sym);
   }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 6; ++k) atomicAdd(&ctr->bj_cycles[k], cyc[k]);
   cta_teardown(sm);
 }
+
+int g_bj_ctas_per_sm = 0;
 
 template <bool VEC>
 static cudaError_t bj_prepare_t(int sms, int* max_ctas) {
@@ -734,8 +783,9 @@ static cudaError_t bj_prepare_t(int sms, int* max_ctas) {
   int b = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, bj_kernel<VEC>, bj::THREADS, bj::SMEM);
   if (e != cudaSuccess) return e;
-  // one CTA of 512 threads per SM (it holds TMEM_COLS of the SM's 512 tensor-memory columns)
-  *max_ctas = std::min(b, 1) * sms;
+  // two CTAs of 256 threads per SM (each holds TMEM_COLS of the SM's 512 tensor-memory columns)
+  const int per_sm = g_bj_ctas_per_sm > 0 ? std::min(g_bj_ctas_per_sm, bj::CTAS_PER_SM) : bj::CTAS_PER_SM;
+  *max_ctas = (b >= 1 ? per_sm : 0) * sms;
   return cudaSuccess;
 }
 
@@ -745,6 +795,27 @@ bool bj_supported(int M, int N) { return N >= 128 && M <= 512 && N <= 512; }
 void bj_dims(int M, int N, int* Mp, int* Np) {
   *Mp = (M + bj::RT - 1) / bj::RT * bj::RT;
   *Np = (N + 127) / 128 * 128;
+}
+
+template <bool VEC>
+static cudaError_t bj_occupancy_t(int* blocks, int* regs, int* smem_static, int* smem_dyn) {
+  cudaError_t e = bj_prepare_t<VEC>(0, nullptr);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, bj_kernel<VEC>);
+  if (e != cudaSuccess) return e;
+  *regs = fa.numRegs;
+  *smem_static = (int)fa.sharedSizeBytes;
+  *smem_dyn = bj::SMEM;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, bj_kernel<VEC>, bj::THREADS, bj::SMEM);
+  if (e != cudaSuccess) return e;
+  // the same with 32 KB of dynamic shared memory: tells a shared-memory limit from a register limit
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks + 1, bj_kernel<VEC>, bj::THREADS, 32768);
+}
+
+cudaError_t bj_occupancy(bool vec, int* blocks, int* regs, int* smem_static, int* smem_dyn) {
+  return vec ? bj_occupancy_t<true>(blocks, regs, smem_static, smem_dyn)
+             : bj_occupancy_t<false>(blocks, regs, smem_static, smem_dyn);
 }
 
 cudaError_t bj_max_ctas(bool vec, int sms, int* ctas) {
@@ -775,8 +846,8 @@ bj_gram_test_kernel(const float* Xr, const float* Xi, int ld, int Mp, const int*
   bj::cta_setup(sm);
   uint32_t ph = 0;
   bj::gram_pair(sm, Xr, Xi, ld, Mp, scol, ctr, ph);
-  bj::gram_to_h(sm, 0.f);
-  const float2* H = reinterpret_cast<const float2*>(sm + bj::OFF_STAGE);
+  bj::gram_to_h(sm, 0.f, true);
+  const float2* H = reinterpret_cast<const float2*>(sm + bj::OFF_R1);
   for (int e = threadIdx.x; e < bj::P * bj::P; e += bj::THREADS) {
     const float2 v = H[(e / bj::P) * bj::HS + e % bj::P];
     D[2 * e] = v.x;
@@ -794,7 +865,7 @@ bj_update_test_kernel(const float* Pr, const float* Pi, float* Or, float* Oi, in
   __shared__ int scol[bj::P];
   if (threadIdx.x < bj::P) scol[threadIdx.x] = cols[threadIdx.x];
   bj::cta_setup(sm);
-  float2* Q = reinterpret_cast<float2*>(sm + bj::OFF_R1);
+  float2* Q = reinterpret_cast<float2*>(sm + bj::OFF_STAGE);
   for (int e = threadIdx.x; e < bj::P * bj::P; e += bj::THREADS) Q[e] = Qin[e];
   __syncthreads();
   bj::q_to_operands(sm);

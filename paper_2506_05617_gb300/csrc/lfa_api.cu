@@ -1026,6 +1026,31 @@ int64_t lfa_debug_shard_range(int32_t n, int32_t m, int32_t rank, int32_t count_
   return F_h;
 }
 
+int32_t lfa_debug_bj_profile(void* plan, uint64_t* out, int32_t* ctas) {
+  lfa_plan_s* p = static_cast<lfa_plan_s*>(plan);
+  if (p == nullptr || out == nullptr || ctas == nullptr) return LFA_ERR_INVALID_ARG;
+  LFA_CUDA_TRY(cudaStreamSynchronize(p->last_stream));
+  Counters c;
+  LFA_CUDA_TRY(cudaMemcpy(&c, p->counters, sizeof c, cudaMemcpyDeviceToHost));
+  for (int k = 0; k < 6; ++k) out[k] = (uint64_t)c.bj_cycles[k];
+  *ctas = p->blocked.empty() ? 0 : p->blocked[0].ctas;
+  return LFA_OK;
+}
+
+void lfa_debug_set_bj_ctas_per_sm(int32_t n) { g_bj_ctas_per_sm = n < 0 ? 0 : n; }
+
+int32_t lfa_debug_bj_occupancy(int32_t vectors, int32_t* out) {
+  if (out == nullptr) return LFA_ERR_INVALID_ARG;
+  int b[2] = {0, 0}, r = 0, ss = 0, sd = 0;
+  LFA_CUDA_TRY(bj_occupancy(vectors != 0, b, &r, &ss, &sd));
+  out[0] = b[0];
+  out[1] = r;
+  out[2] = ss;
+  out[3] = sd;
+  out[4] = b[1];
+  return LFA_OK;
+}
+
 int32_t lfa_debug_logged_ok(int32_t v, int32_t M, int32_t N) {
   return v >= 0 && v < kNumVariants && logged_ok(v, M, N) ? 1 : 0;
 }

@@ -19,6 +19,9 @@ struct Counters {
   unsigned long long timeouts;   // bounded device waits that ran out (tensor-core route)
   unsigned long long tc_grams;   // block-pair Gram matrices formed on the tensor cores
   unsigned long long tc_updates; // block-pair rotations applied on the tensor cores
+  // tensor-core route, summed over CTAs (clock64 of each CTA's thread 0): Gram, inner sweep,
+  // update, assembly, output, whole symbols
+  unsigned long long bj_cycles[6];
   unsigned int queue[16];        // work-queue tickets, one per launch of a call
 };
 
@@ -160,6 +163,8 @@ bool bj_supported(int M, int N);
 void bj_dims(int M, int N, int* Mp, int* Np);
 size_t bj_slot_floats(int M, int N, bool vec);
 cudaError_t bj_max_ctas(bool vec, int sms, int* ctas);   // co-resident CTAs (kernel attributes set)
+extern int g_bj_ctas_per_sm;                             // 0: the kernel's own choice (debug hook)
+cudaError_t bj_occupancy(bool vec, int* blocks, int* regs, int* smem_static, int* smem_dyn);
 cudaError_t launch_bj(const BJLaunch& A, int ctas, bool vec, cudaStream_t s);
 cudaError_t launch_bj_gram_test(const float* Xr, const float* Xi, int ld, int Mp, const int* cols, float* D,
                                 Counters* ctr, cudaStream_t s);

@@ -217,11 +217,19 @@ extern "C" lfa_status_t lfa_svd_backward_noalloc(const lfa_layer_desc_t* layer, 
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int nm_max = d.n > d.m ? d.n : d.m;
-  twiddle_kernel<<<(nm_max + 255) / 256, 256, 0, s>>>(tw_n, d.n, tw_m, d.m);
-  e = cudaGetLastError();
+  // cudaLaunchKernel returns the status of this launch alone (cudaGetLastError would also report,
+  // and clear, an error left behind by unrelated earlier work)
+  {
+    int n_ = d.n, m_ = d.m;
+    void* args[] = {&tw_n, &n_, &tw_m, &m_};
+    e = cudaLaunchKernel(reinterpret_cast<const void*>(twiddle_kernel), dim3((nm_max + 255) / 256), dim3(256), args,
+                         0, s);
+  }
   if (e == cudaSuccess) {
-    half_grid_kernel<<<(La.F_h + 255) / 256, 256, 0, s>>>(half, d.n, d.m, La.F_h);
-    e = cudaGetLastError();
+    int n_ = d.n, m_ = d.m, fh = La.F_h;
+    void* args[] = {&half, &n_, &m_, &fh};
+    e = cudaLaunchKernel(reinterpret_cast<const void*>(half_grid_kernel), dim3((La.F_h + 255) / 256), dim3(256),
+                         args, 0, s);
   }
   if (e == cudaSuccess) {
     int nk = 0;

@@ -53,7 +53,8 @@ EXPORTS = [
     "lfa_last_cuda_error", "lfa_kernel_launches", "lfa_version",
     "lfa_debug_schedule", "lfa_debug_half_grid", "lfa_debug_choose_variant", "lfa_debug_variant_count",
     "lfa_debug_tuned_variant", "lfa_debug_variant_fits", "lfa_debug_logged_ok", "lfa_debug_half_position",
-    "lfa_debug_shard_range", "lfa_debug_tc_gram", "lfa_debug_tc_update",
+    "lfa_debug_shard_range", "lfa_debug_tc_gram", "lfa_debug_tc_update", "lfa_debug_bj_profile",
+    "lfa_debug_set_bj_ctas_per_sm", "lfa_debug_bj_occupancy",
 ]
 
 
@@ -144,6 +145,9 @@ def lib():
         "lfa_debug_tc_gram": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p]),
         "lfa_debug_tc_update": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p,
                                           c_void_p, c_void_p]),
+        "lfa_debug_bj_profile": (c_int32, [P, POINTER(ctypes.c_uint64), POINTER(c_int32)]),
+        "lfa_debug_set_bj_ctas_per_sm": (None, [c_int32]),
+        "lfa_debug_bj_occupancy": (c_int32, [c_int32, POINTER(c_int32)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -348,3 +352,32 @@ def lfa_debug_tc_update(Pr: int, Pi: int, Or: int, Oi: int, ld: int, rows: int, 
     """Tensor-core update Y Q of one block pair (see include/lfa_debug.h); returns the status code."""
     return int(lib().lfa_debug_tc_update(c_void_p(Pr), c_void_p(Pi), c_void_p(Or), c_void_p(Oi), ld, rows,
                                          c_void_p(cols), c_void_p(Q), _stream(stream)))
+
+
+BJ_PHASES = ("gram", "inner", "update", "assembly", "output", "symbol")
+
+
+def lfa_debug_bj_profile(plan: int):
+    """Phase clock cycles of the blocked route in the plan's last forward (summed over its CTAs) and
+    the CTA count of its launch: (dict phase -> cycles, ctas)."""
+    out = (ctypes.c_uint64 * 6)()
+    ctas = c_int32(0)
+    st = lib().lfa_debug_bj_profile(c_void_p(plan), out, ctypes.byref(ctas))
+    if st != LFA_OK:
+        raise LfaError(st, "lfa_debug_bj_profile")
+    return {k: int(v) for k, v in zip(BJ_PHASES, out)}, int(ctas.value)
+
+
+def lfa_debug_set_bj_ctas_per_sm(n: int) -> None:
+    """CTAs per SM of the blocked route in plans created afterwards (0: the kernel's choice)."""
+    lib().lfa_debug_set_bj_ctas_per_sm(int(n))
+
+
+def lfa_debug_bj_occupancy(vectors: bool):
+    """(CTAs per SM, registers per thread, static shared bytes, dynamic shared bytes, CTAs per SM with
+    32 KB of dynamic shared memory) of the blocked route's kernel."""
+    out = (c_int32 * 5)()
+    st = lib().lfa_debug_bj_occupancy(1 if vectors else 0, out)
+    if st != LFA_OK:
+        raise LfaError(st, "lfa_debug_bj_occupancy")
+    return tuple(int(v) for v in out)
