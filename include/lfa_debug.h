@@ -69,6 +69,12 @@ int32_t lfa_debug_tc_gram(const float* Xr, const float* Xi, int32_t ld, int32_t 
 int32_t lfa_debug_tc_update(const float* Pr, const float* Pi, float* Or, float* Oi, int32_t ld, int32_t rows,
                             const int32_t* cols, const float* Q, void* stream);
 
+/* The backward route a layer takes in lfa_svd_backward: 2 the tensor-core G product (stride 1,
+ * c_out and c_in >= 128, at most 25 taps), 1 the fused CUDA-core kernel (stride 1, at most 25 taps),
+ * 0 the CUDA-core G product and tap projection; -1 for an invalid layer. */
+int32_t lfa_debug_backward_route(int32_t c_out, int32_t c_in, int32_t kh, int32_t kw, int32_t stride_h,
+                                 int32_t stride_w);
+
 /* Phase profile of the blocked tensor-core route in the last lfa_svd call of a plan (waits for the
  * plan's last stream): out[0..5] = clock cycles summed over the route's CTAs (thread 0 of each) in
  * block-pair Grams, inner sweeps, updates, symbol assembly, output, and whole symbols; *ctas = the

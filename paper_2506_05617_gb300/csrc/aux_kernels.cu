@@ -559,15 +559,24 @@ __global__ void __launch_bounds__(256) backward_reduce_kernel(const float* parti
   dw[e] = s;
 }
 
+cudaError_t launch_backward_reduce(const float* partial, int chunks, int64_t total, float* dw, cudaStream_t s) {
+  backward_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(partial, chunks, total, dw);
+  return cudaGetLastError();
+}
+
 // G holds g_cap symbols' G_h; the half grid is processed in blocks of whole chunks that fit.
 cudaError_t launch_backward(const LayerArgs& La, const float* dsigma, int half_output,
                             const float2* U, const float2* V, float2* G, int64_t g_cap, float* partial,
-                            int chunks, float* dw, cudaStream_t s, int* nkernels) {
+                            int chunks, float* dw, cudaStream_t s, int* nkernels, unsigned int* queue,
+                            Counters* ctr, int sms) {
   *nkernels = 0;
   const int CW = La.c_out * La.c_w;
   const int kk = La.kh * La.kw;
   // no frequencies (an empty shard of the half grid): the contribution is zero
   if (La.F_h <= 0) return cudaMemsetAsync(dw, 0, (size_t)CW * kk * sizeof(float), s);
+  if (queue && ctr && G && g_cap >= 1 && sms > 0 && tc_backward_parts(La) > 0)
+    return launch_backward_tc(La, dsigma, half_output, U, V, G, g_cap, partial, chunks, queue, ctr, dw, sms, s,
+                              nkernels);
   if (La.sh == 1 && La.sw == 1 && kk <= 25 && chunks <= 65535) {
     // fused: G never leaves registers
     const int chunk = (La.F_h + chunks - 1) / chunks;

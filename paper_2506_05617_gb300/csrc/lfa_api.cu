@@ -610,6 +610,8 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
       g_bytes = std::max(g_bytes, (size_t)(chunk * CC * 8));
       const int fused = fused_backward_chunks(La);   // the fused backward picks its own chunking
       if (fused > 0) chunks = fused;
+      const int tc_parts = tc_backward_parts(La);     // the tensor-core backward: its partial slabs
+      if (tc_parts > 0) chunks = tc_parts;
       p->bw_chunks[l] = (int)chunks;
       part_bytes = std::max(part_bytes, (size_t)(chunks * CC * La.kh * La.kw * 4));
     }
@@ -829,7 +831,7 @@ lfa_status_t lfa_svd_backward(lfa_plan_t p, const float* const* dsigma, const fl
     int nk = 0;
     LFA_CUDA_TRY(launch_backward(La, dsigma[l], p->half_output, reinterpret_cast<const float2*>(U[l]),
                                  reinterpret_cast<const float2*>(V[l]), p->g_ws, g_cap, p->partial_ws,
-                                 p->bw_chunks[l], dw[l], s, &nk));
+                                 p->bw_chunks[l], dw[l], s, &nk, p->counters->bw_queue, p->counters, p->sms));
     g_launches += nk;
   }
   return LFA_OK;
@@ -862,7 +864,7 @@ lfa_status_t lfa_spectral_edit(lfa_plan_t p, const float* const* sigma, const fl
     const int64_t g_cap = p->g_cap_bytes / (CC * 8);
     int nk = 0;
     LFA_CUDA_TRY(launch_backward(La, p->edit_ws, p->half_output, Ul, Vl, p->g_ws, g_cap, p->partial_ws,
-                                 p->bw_chunks[l], w_out[l], s, &nk));
+                                 p->bw_chunks[l], w_out[l], s, &nk, p->counters->bw_queue, p->counters, p->sms));
     g_launches += 1 + nk;
   }
   return LFA_OK;
@@ -1024,6 +1026,16 @@ int64_t lfa_debug_shard_range(int32_t n, int32_t m, int32_t rank, int32_t count_
   const int64_t F_h = ((int64_t)n * m + s) / 2;
   shard_range(F_h, rank, count_shards, first, count);
   return F_h;
+}
+
+int32_t lfa_debug_backward_route(int32_t c_out, int32_t c_in, int32_t kh, int32_t kw, int32_t stride_h,
+                                 int32_t stride_w) {
+  LayerArgs La;
+  std::memset(&La, 0, sizeof La);
+  if (!set_geometry(La, c_out, c_in, kh, kw, 8, 8, -1, -1, stride_h, stride_w)) return -1;
+  La.F_h = 1;
+  if (tc_backward_parts(La) > 0) return 2;
+  return fused_backward_chunks(La) > 0 ? 1 : 0;
 }
 
 int32_t lfa_debug_bj_profile(void* plan, uint64_t* out, int32_t* ctas) {

@@ -23,6 +23,7 @@ struct Counters {
   // update, assembly, output, whole symbols
   unsigned long long bj_cycles[6];
   unsigned int queue[16];        // work-queue tickets, one per launch of a call
+  unsigned int bw_queue[2];      // work-queue tickets of the tensor-core backward's launches
 };
 
 // One layer as a kernel sees it. The Jacobi problem of a symbol is X (M x N), with
@@ -186,9 +187,21 @@ int fused_backward_chunks(const LayerArgs& La);
 cudaError_t launch_complete(const LayerArgs& La, float2* X, int symbols, cudaStream_t s);
 cudaError_t launch_expand(const LayerArgs& La, const float2* U, const float2* V, int64_t first,
                           int64_t count, float2* u_hat, float2* v_hat, cudaStream_t s);
+// The backward of one layer. With `queue` (two device counters) and `ctr` given, stride-1 layers of
+// 128 channels and more (tc_backward_parts > 0) take the tensor-core route (backward_tc.cu), with
+// `chunks` partial slabs; otherwise the CUDA-core kernels.
 cudaError_t launch_backward(const LayerArgs& La, const float* dsigma, int half_output,
                             const float2* U, const float2* V, float2* G, int64_t g_cap,
-                            float* partial, int chunks, float* dw, cudaStream_t s, int* nkernels);
+                            float* partial, int chunks, float* dw, cudaStream_t s, int* nkernels,
+                            unsigned int* queue = nullptr, Counters* ctr = nullptr, int sms = 0);
+// partial slabs of the tensor-core backward for a layer, 0 when the route does not apply
+int tc_backward_parts(const LayerArgs& La);
+cudaError_t launch_backward_tc(const LayerArgs& La, const float* dsigma, int half_output, const float2* U,
+                               const float2* V, float2* G, int64_t g_cap, float* partial, int parts,
+                               unsigned int* queue, Counters* ctr, float* dw, int sms, cudaStream_t s,
+                               int* nkernels);
+// dw = sum over `chunks` partial slabs of `total` floats, in slab order
+cudaError_t launch_backward_reduce(const float* partial, int chunks, int64_t total, float* dw, cudaStream_t s);
 cudaError_t launch_edit_values(const LayerArgs& La, int half_output, const float* sigma, int mode, float a,
                                float b, float* g, cudaStream_t s);
 // scratch: kRegScratchBytes of device memory for the per-CTA partials (plan-owned)

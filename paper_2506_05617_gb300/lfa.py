@@ -54,7 +54,7 @@ EXPORTS = [
     "lfa_debug_schedule", "lfa_debug_half_grid", "lfa_debug_choose_variant", "lfa_debug_variant_count",
     "lfa_debug_tuned_variant", "lfa_debug_variant_fits", "lfa_debug_logged_ok", "lfa_debug_half_position",
     "lfa_debug_shard_range", "lfa_debug_tc_gram", "lfa_debug_tc_update", "lfa_debug_bj_profile",
-    "lfa_debug_set_bj_ctas_per_sm", "lfa_debug_bj_occupancy",
+    "lfa_debug_set_bj_ctas_per_sm", "lfa_debug_bj_occupancy", "lfa_debug_backward_route",
 ]
 
 
@@ -148,6 +148,7 @@ def lib():
         "lfa_debug_bj_profile": (c_int32, [P, POINTER(ctypes.c_uint64), POINTER(c_int32)]),
         "lfa_debug_set_bj_ctas_per_sm": (None, [c_int32]),
         "lfa_debug_bj_occupancy": (c_int32, [c_int32, POINTER(c_int32)]),
+        "lfa_debug_backward_route": (c_int32, [c_int32] * 6),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -381,3 +382,11 @@ def lfa_debug_bj_occupancy(vectors: bool):
     if st != LFA_OK:
         raise LfaError(st, "lfa_debug_bj_occupancy")
     return tuple(int(v) for v in out)
+
+
+BACKWARD_ROUTES = {2: "tensor-core", 1: "fused", 0: "cuda-core"}
+
+
+def lfa_debug_backward_route(c_out: int, c_in: int, kh: int, kw: int, stride_h: int = 1, stride_w: int = 1) -> int:
+    """The backward route of a layer: 2 tensor-core G product, 1 fused CUDA-core, 0 CUDA-core G + taps."""
+    return int(lib().lfa_debug_backward_route(c_out, c_in, kh, kw, stride_h, stride_w))

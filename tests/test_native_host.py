@@ -287,3 +287,17 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     from paper_2506_05617_gb300.torch_api import LfaPlan
     with pytest.raises(RuntimeError, match="not built"):
         LfaPlan([(4, 4, 3, 3, 8, 8)])
+
+
+def test_backward_route_choice():
+    """Stride-1 layers with 128 channels and more on both sides and at most 25 taps take the
+    tensor-core backward; other stride-1 layers with at most 25 taps the fused CUDA-core kernel; the
+    rest the CUDA-core G product and tap projection."""
+    assert C.lfa_debug_backward_route(512, 512, 3, 3) == 2
+    assert C.lfa_debug_backward_route(128, 128, 5, 5) == 2
+    assert C.lfa_debug_backward_route(130, 140, 1, 1) == 2
+    assert C.lfa_debug_backward_route(128, 96, 3, 3) == 1
+    assert C.lfa_debug_backward_route(64, 64, 3, 3) == 1
+    assert C.lfa_debug_backward_route(256, 256, 7, 7) == 0
+    assert C.lfa_debug_backward_route(256, 128, 3, 3, 2, 2) == 0
+    assert C.lfa_debug_backward_route(0, 128, 3, 3) == -1
