@@ -722,7 +722,8 @@ def run_reference(args):
 
 
 def run_forward_once(args):
-    """One forward of the workload on cuda:0 through the public API (no graph), for profiling."""
+    """One forward of the workload on cuda:0 through the public API (no graph), for profiling; with
+    --with-backward (and vectors) also the regulariser gradient and the backward of that step."""
     import torch
     from paper_2506_05617_gb300 import build as B
     from paper_2506_05617_gb300.torch_api import LfaPlan
@@ -731,7 +732,10 @@ def run_forward_once(args):
     vectors = not (args.values_only or args.workload in VALUES_ONLY)
     plan = LfaPlan([l.desc() for l in layers], vectors=vectors, use_graph=0, tune_cache=args.tune_cache)
     ws = [torch.from_numpy(W.weights(l)).cuda() for l in layers]
-    plan.svd(ws)
+    sig, U, V = plan.svd(ws)
+    if args.with_backward and vectors:
+        dsig, _ = plan.regulariser_grad(sig, LAM)
+        plan.backward(dsig, U, V)
     torch.cuda.synchronize()
     st, info = plan.info()
     print(json.dumps({"workload": args.workload, "routes": [m["variant_name"] for m in plan.meta], "status": st,
@@ -797,6 +801,8 @@ def main():
     ap.add_argument("--forward-once", action="store_true",
                     help="build the workload's plan, run one forward (values + vectors unless values-only) and "
                          "exit: the small launch a profiler captures")
+    ap.add_argument("--with-backward", action="store_true",
+                    help="with --forward-once: also the regulariser gradient and the backward")
     ap.add_argument("--values-only", action="store_true", help="values only (no vectors, backward, lifting)")
     ap.add_argument("--tune-cache", default=DEFAULT_TUNE if os.path.exists(DEFAULT_TUNE) else None,
                     help="autotuner cache file read by lfa_plan")

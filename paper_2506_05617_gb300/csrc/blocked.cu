@@ -77,13 +77,13 @@ static_assert(OFF_R1 % 1024 == 0 && OFF_UPD % 1024 == 0 && OFF_PRM % 16 == 0 && 
               OFF_MISC % 16 == 0, "alignment");
 static_assert(CTAS_PER_SM * (SMEM + 2048) <= 233472, "two CTAs per SM");
 
+constexpr int MB_TILE = 2;       // mbarrier of a finished update tile
 struct Misc {
-  uint64_t mbar[2];     // MMA completion, one per operand buffer
+  uint64_t mbar[3];     // [0], [1]: MMA completion, one per operand buffer; [MB_TILE]: an update tile
   uint32_t tmem;        // TMEM base column address
   int32_t rotated;      // the block pair rotated in its inner sweep
   int32_t failed;       // a bounded wait ran out: no further tensor work in this CTA
   int32_t item;         // work item
-  int32_t vote[2];      // unused
   int32_t any;          // some pair of the block pair passes the rotation test
   int32_t pad[5];
 };
@@ -339,13 +339,13 @@ __device__ int inner_sweep(unsigned char* sm, float tol2, bool full) {
   return nrot;
 }
 
-// Q (OFF_STAGE, fp32 complex, Q[k][n] at k * 64 + n) -> the B operands of the update in its place
-// (OFF_STAGE, 64 KB, over Q and the first half of H, both dead by then): Re (Q - I)^T
-// and Im Q^T (N = 64 output columns x K = 64), each split into TF32 hi and lo (16 KB each),
-// K-major core matrices (kc, ng) at byte ((kc * 8 + ng) * 8) * 16: LBO = 1024 B, SBO = 128 B.
-// Layout: [Re hi | Re lo | Im hi | Im lo]. The update forms Y (Q - I) on the tensor cores and adds
-// Y exactly on the CUDA cores: the 3xTF32 error (a few fp32 units of each product) then scales
-// with the rotation, which is small once the sweeps near convergence, instead of with Y.
+// Q (OFF_STAGE, fp32 complex, Q[k][n] at k * 64 + n) -> the B operand of the update in its place
+// (OFF_STAGE, 64 KB, over Q and the first half of H, both dead by then): the 128 x 64 (N x K) matrix
+// [Re (Q - I)^T ; Im Q^T], rows n < 64 from Re(Q - I) and n >= 64 from Im Q, split into TF32 hi and lo
+// (32 KB each), K-major core matrices (kc, ng) at byte ((kc * 16 + ng) * 8) * 16: LBO = 2048 B,
+// SBO = 128 B. Layout: [hi | lo]. The update forms Y (Q - I) on the tensor cores and adds Y exactly
+// on the CUDA cores: the 3xTF32 error (a few fp32 units of each product) then scales with the
+// rotation, which is small once the sweeps near convergence, instead of with Y.
 __device__ void q_to_operands(unsigned char* sm) {
   float2* Q = reinterpret_cast<float2*>(sm + OFF_STAGE);
   float* R = reinterpret_cast<float*>(sm + OFF_STAGE);
@@ -358,14 +358,15 @@ __device__ void q_to_operands(unsigned char* sm) {
   for (int j = 0; j < NQ; ++j) {
     const int e = threadIdx.x + THREADS * j;
     const int k = e / P, n = e % P;
-    const int off = ((k / 4 * 8 + n / 8) * 8 + n % 8) * 4 + k % 4;
+    const int off_re = ((k / 4 * 16 + n / 8) * 8 + n % 8) * 4 + k % 4;   // row n of B
+    const int off_im = off_re + (P / 8) * 8 * 4;                          // row n + 64 of B
     float h, l;
     tc::split_tf32(k == n ? q[j].x - 1.f : q[j].x, h, l);
-    R[off] = h;
-    R[4096 + off] = l;
+    R[off_re] = h;
+    R[8192 + off_re] = l;
     tc::split_tf32(q[j].y, h, l);
-    R[8192 + off] = h;
-    R[12288 + off] = l;
+    R[off_im] = h;
+    R[8192 + off_im] = l;
   }
   tc::fence_proxy_async_smem();
   __syncthreads();
@@ -382,142 +383,130 @@ struct Mat {
 };
 
 // For every row tile of m0 and then of m1 (m1.tiles may be 0), the 64 columns cols[] of the tile
-// become Y Q = Y + Y (Q - I): Y (Q - I) = [Re Y Re(Q - I) - Im Y Im Q, Re Y Im Q + Im Y Re(Q - I)]
-// on the tensor cores (the operands at OFF_STAGE are those of Q - I), Y added on the CUDA cores.
-// The work is a flat sequence of steps (tile, chunk of KU = 8 columns of Y): a chunk is staged
-// as Re Y hi | lo | Im Y hi | lo (4 KB each, core matrix (kc, rg) = (columns 4kc..4kc+3, rows
-// 8rg..8rg+7) at byte ((kc * 16 + rg) * 8) * 16: LBO = 2048 B, SBO = 128 B) in one of two buffers,
-// while the loads of the next PD chunks are in flight. Tile T accumulates in TMEM columns
-// 128 (T & 1) + [0, 64) (Re) and + [64, 128) (Im); its epilogue runs while the next tile's MMAs
-// execute.
+// become Y Q = Y + Y (Q - I). With B = [Re(Q - I) | Im Q] (N = 128), the tensor cores form
+// D1 = Re Y B and D2 = Im Y B (TMEM columns [0, 128) and [128, 256)), and the CUDA cores add
+//   Re Y' = Re Y + D1[:, c] - D2[:, 64 + c],   Im Y' = Im Y + D1[:, 64 + c] + D2[:, c].
+// The work is a flat sequence of steps (tile, chunk of KU = 8 columns of Y): thread (row r, quad kc)
+// loads Re and Im of row r of the chunk's columns 4 kc .. 4 kc + 3, keeps them for the tile's
+// epilogue, and stages them as Re Y hi | lo | Im Y hi | lo (4 KB each, core matrix (kc, rg) at byte
+// ((kc * 16 + rg) * 8) * 16: LBO = 2048 B, SBO = 128 B) in one of two buffers, PD chunks ahead of
+// their loads. After the tile's last chunk each thread reads its 32 output columns' four
+// accumulators out of TMEM (its row is its TMEM lane) and writes Y' with the Y it kept: no reload.
 __device__ void update_pair(unsigned char* sm, Mat m0, Mat m1, const int* cols, Counters* ctr, uint32_t& ph) {
-  static_assert(THREADS == 256 && KU == 8, "the staging map below gives each thread a row's column quad");
-  constexpr int PD = 4;                                 // chunks whose loads are in flight
+  static_assert(THREADS == 256 && KU == 8 && P / KU == 8, "each thread keeps a row's column quad per chunk");
+  constexpr int PD = 2;                                 // chunks whose loads are in flight
+  constexpr int CH = P / KU;                            // chunks per tile
   Misc* ms = misc(sm);
   float* const stage = reinterpret_cast<float*>(sm + OFF_UPD);
   const uint32_t s_base = tc::smem_u32(sm + OFF_UPD);
   const uint32_t q_base = tc::smem_u32(sm + OFF_STAGE);
-  constexpr uint32_t LBO = 2048, SBO = 128, QLBO = 1024, QSBO = 128;
+  constexpr uint32_t LBO = 2048, SBO = 128;
   constexpr uint32_t PART = RT * KU * 4;                // bytes of one plane part (hi or lo, Re or Im)
-  constexpr uint32_t ID = tc::idesc_tf32(128, 64);
-  constexpr uint32_t ID_NEG = tc::idesc_tf32(128, 64, false, true);
-  constexpr int CH = P / KU;                            // chunks per tile
+  constexpr uint32_t ID = tc::idesc_tf32(128, 128);
   const int row = threadIdx.x & (RT - 1);
   const int kc = threadIdx.x >> 7;                      // this thread's column quad within a chunk
-  const int S = (m0.tiles + m1.tiles) * CH;
+  const int tiles = m0.tiles + m1.tiles;
   const int soff = ((kc * 16 + (row >> 3)) * 8 + (row & 7)) * 4;
-  auto prefetch = [&](int s, float4& vr, float4& vi) {
-    const int T = s / CH, u = s % CH;
+  auto load = [&](int T, int u, float* vr, float* vi) {
     const bool first = T < m0.tiles;
     const float* re = first ? m0.re : m1.re;
     const float* im = first ? m0.im : m1.im;
     const size_t ld = (size_t)(first ? m0.ld : m1.ld);
     const size_t r = (size_t)(first ? T : T - m0.tiles) * RT + row;
     const int c0 = u * KU + 4 * kc;
-    vr.x = __ldcg(re + (size_t)cols[c0] * ld + r);
-    vr.y = __ldcg(re + (size_t)cols[c0 + 1] * ld + r);
-    vr.z = __ldcg(re + (size_t)cols[c0 + 2] * ld + r);
-    vr.w = __ldcg(re + (size_t)cols[c0 + 3] * ld + r);
-    vi.x = __ldcg(im + (size_t)cols[c0] * ld + r);
-    vi.y = __ldcg(im + (size_t)cols[c0 + 1] * ld + r);
-    vi.z = __ldcg(im + (size_t)cols[c0 + 2] * ld + r);
-    vi.w = __ldcg(im + (size_t)cols[c0 + 3] * ld + r);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      vr[q] = __ldcg(re + (size_t)cols[c0 + q] * ld + r);
+      vi[q] = __ldcg(im + (size_t)cols[c0 + q] * ld + r);
+    }
   };
-  auto stage_quad = [&](float* st, float4 v) {     // hi at st, lo one part further
+  auto stage_quad = [&](float* st, const float* v) {    // hi at st, lo one part further
     float4 h, l;
-    tc::split_tf32(v.x, h.x, l.x);
-    tc::split_tf32(v.y, h.y, l.y);
-    tc::split_tf32(v.z, h.z, l.z);
-    tc::split_tf32(v.w, h.w, l.w);
+    tc::split_tf32(v[0], h.x, l.x);
+    tc::split_tf32(v[1], h.y, l.y);
+    tc::split_tf32(v[2], h.z, l.z);
+    tc::split_tf32(v[3], h.w, l.w);
     *reinterpret_cast<float4*>(st + soff) = h;
     *reinterpret_cast<float4*>(st + PART / 4 + soff) = l;
   };
-  // epilogue of tile T: warp w takes TMEM lanes 32 (w % 4) .. (its rows) and, in turn, the parts
-  // w / 4, w / 4 + THREADS / 128, ... of 32 columns: parts 0, 1 real columns 0-31, 32-63; 2, 3
-  // imaginary
-  auto epilogue = [&](int T) {
-    const bool first = T < m0.tiles;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int orow = 32 * (w & 3) + lane;
-    const size_t ld = (size_t)(first ? m0.ld : m1.ld);
-    const size_t r = (size_t)(first ? T : T - m0.tiles) * RT + orow;
+  float yr[CH][4], yi[CH][4];                           // this thread's Y of the current tile
+  float nr[PD][4], ni[PD][4];                           // the next tile's first chunks, in flight
 #pragma unroll
-    for (int part = w >> 2; part < 4; part += THREADS / 128) {
-      const int cq = (part & 1) * 32;
-      const uint32_t ta = ms->tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(128 * (T & 1) + 64 * (part >> 1) + cq);
-      float* Y = (part >> 1) ? (first ? m0.im : m1.im) : (first ? m0.re : m1.re);
-      // all loads of Y first, then the stores: a store between loads to addresses the compiler
-      // cannot tell apart would serialise the 32 L2 round trips
+  for (int u = 0; u < PD; ++u) load(0, u, yr[u], yi[u]);
+  int s = 0;
+  for (int T = 0; T < tiles; ++T) {
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        float v[16], y[16];
-        tc::tmem_ld16(ta + 16 * h, v);
-#pragma unroll
-        for (int q = 0; q < 16; ++q) y[q] = __ldcg(Y + (size_t)cols[cq + 16 * h + q] * ld + r);
-        tc::tmem_ld_wait();
-#pragma unroll
-        for (int q = 0; q < 16; ++q) Y[(size_t)cols[cq + 16 * h + q] * ld + r] = y[q] + v[q];
-      }
-    }
-    tc::fence_before_sync();
-  };
-  float4 pr[PD], pi[PD];
-#pragma unroll
-  for (int j = 0; j < PD; ++j)
-    if (j < S) prefetch(j, pr[j], pi[j]);
-  for (int s0 = 0; s0 < S; s0 += PD) {
-#pragma unroll
-    for (int j = 0; j < PD; ++j) {
-      const int s = s0 + j;
-      if (s >= S) break;                                // uniform over the CTA
-      const int b = j & 1;                              // = s & 1 (PD even)
-      float* st = stage + b * (4 * PART / 4);           // buffer b: Re hi | Re lo | Im hi | Im lo
-      stage_quad(st, pr[j]);
-      stage_quad(st + 2 * PART / 4, pi[j]);
+    for (int u = 0; u < CH; ++u, ++s) {
+      if (u + PD < CH) load(T, u + PD, yr[u + PD], yi[u + PD]);
+      else if (T + 1 < tiles) load(T + 1, u + PD - CH, nr[u + PD - CH], ni[u + PD - CH]);
+      const int b = s & 1;
+      if (s >= 2) wait_buf(sm, ctr, b, ph);             // the MMAs of step s - 2 released buffer b
+      float* st = stage + b * (4 * PART / 4);
+      stage_quad(st, yr[u]);
+      stage_quad(st + 2 * PART / 4, yi[u]);
       tc::fence_proxy_async_smem();
       tc::fence_before_sync();
       __syncthreads();
-      if (s + PD < S) prefetch(s + PD, pr[j], pi[j]);
       if (threadIdx.x == 0 && !ms->failed) {
         tc::fence_after_sync();
-        const int T = s / CH, u = s % CH;
-        const uint32_t dr = ms->tmem + (uint32_t)(128 * (T & 1)), di = dr + 64;
+        const uint32_t d1 = ms->tmem, d2 = ms->tmem + 128;
         const uint32_t a0 = s_base + (uint32_t)b * 4 * PART;
         const uint64_t yrh = tc::smem_desc_kmajor(a0, LBO, SBO);
         const uint64_t yrl = tc::smem_desc_kmajor(a0 + PART, LBO, SBO);
         const uint64_t yih = tc::smem_desc_kmajor(a0 + 2 * PART, LBO, SBO);
         const uint64_t yil = tc::smem_desc_kmajor(a0 + 3 * PART, LBO, SBO);
-        const uint32_t qo = (uint32_t)((u * KU) / 4) * QLBO;
-        const uint64_t qrh = tc::smem_desc_kmajor(q_base + qo, QLBO, QSBO);
-        const uint64_t qrl = tc::smem_desc_kmajor(q_base + 16384 + qo, QLBO, QSBO);
-        const uint64_t qih = tc::smem_desc_kmajor(q_base + 32768 + qo, QLBO, QSBO);
-        const uint64_t qil = tc::smem_desc_kmajor(q_base + 49152 + qo, QLBO, QSBO);
+        const uint32_t qo = (uint32_t)(u * KU / 4) * LBO;
+        const uint64_t bh = tc::smem_desc_kmajor(q_base + qo, LBO, SBO);
+        const uint64_t bl = tc::smem_desc_kmajor(q_base + 32768 + qo, LBO, SBO);
         const uint32_t acc0 = u > 0 ? 1u : 0u;
-        // Re Y' = Re Y Re(Q - I) - Im Y Im Q
-        tc::mma_tf32(dr, yrh, qrh, ID, acc0);
-        tc::mma_tf32(dr, yrh, qrl, ID, 1u);
-        tc::mma_tf32(dr, yrl, qrh, ID, 1u);
-        tc::mma_tf32(dr, yih, qih, ID_NEG, 1u);
-        tc::mma_tf32(dr, yih, qil, ID_NEG, 1u);
-        tc::mma_tf32(dr, yil, qih, ID_NEG, 1u);
-        // Im Y' = Re Y Im Q + Im Y Re(Q - I)
-        tc::mma_tf32(di, yrh, qih, ID, acc0);
-        tc::mma_tf32(di, yrh, qil, ID, 1u);
-        tc::mma_tf32(di, yrl, qih, ID, 1u);
-        tc::mma_tf32(di, yih, qrh, ID, 1u);
-        tc::mma_tf32(di, yih, qrl, ID, 1u);
-        tc::mma_tf32(di, yil, qrh, ID, 1u);
+        tc::mma_tf32(d1, yrh, bh, ID, acc0);             // D1 = Re Y B
+        tc::mma_tf32(d1, yrh, bl, ID, 1u);
+        tc::mma_tf32(d1, yrl, bh, ID, 1u);
+        tc::mma_tf32(d2, yih, bh, ID, acc0);             // D2 = Im Y B
+        tc::mma_tf32(d2, yih, bl, ID, 1u);
+        tc::mma_tf32(d2, yil, bh, ID, 1u);
         tc::mma_commit(&ms->mbar[b]);
-      }
-      if (s >= 1) {
-        wait_buf(sm, ctr, (s - 1) & 1, ph);             // step s - 1 done (its buffer is free)
-        if ((s - 1) % CH == CH - 1) epilogue((s - 1) / CH);
+        if (u == CH - 1) tc::mma_commit(&ms->mbar[MB_TILE]);
       }
     }
+    // epilogue of tile T: every MMA of the tile has completed
+    wait_buf(sm, ctr, MB_TILE, ph);
+    {
+      const bool first = T < m0.tiles;
+      float* Yr = first ? m0.re : m1.re;
+      float* Yi = first ? m0.im : m1.im;
+      const size_t ld = (size_t)(first ? m0.ld : m1.ld);
+      const size_t r = (size_t)(first ? T : T - m0.tiles) * RT + row;
+      const uint32_t ta = ms->tmem + ((uint32_t)(32 * ((threadIdx.x >> 5) & 3)) << 16);
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        const uint32_t c = (uint32_t)(u * KU + 4 * kc);
+        float a[4], bq[4], cq[4], dq[4];
+        tc::tmem_ld4(ta + c, a);               // D1[:, c]        Re Y Re(Q - I)
+        tc::tmem_ld4(ta + 64 + c, bq);         // D1[:, 64 + c]   Re Y Im Q
+        tc::tmem_ld4(ta + 128 + c, cq);        // D2[:, c]        Im Y Re(Q - I)
+        tc::tmem_ld4(ta + 192 + c, dq);        // D2[:, 64 + c]   Im Y Im Q
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const size_t o = (size_t)cols[c + q] * ld + r;
+          Yr[o] = yr[u][q] + (a[q] - dq[q]);
+          Yi[o] = yi[u][q] + (bq[q] + cq[q]);
+        }
+      }
+      tc::fence_before_sync();
+      __syncthreads();                                  // the accumulators are free for the next tile
+    }
+#pragma unroll
+    for (int u = 0; u < PD; ++u)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        yr[u][q] = nr[u][q];
+        yi[u][q] = ni[u][q];
+      }
   }
-  wait_buf(sm, ctr, (S - 1) & 1, ph);
-  epilogue(S / CH - 1);
-  __syncthreads();
+  // the operand buffers' last two commits (complete by now): one wait per commit keeps the parities
+  for (int t = s >= 2 ? s - 2 : 0; t < s; ++t) wait_buf(sm, ctr, t & 1, ph);
 }
 
 // ---------------------------------------------------------------------------------- set-up
@@ -531,6 +520,7 @@ __device__ void cta_setup(unsigned char* sm) {
   if (threadIdx.x == 0) {
     tc::mbar_init(&ms->mbar[0], 1);
     tc::mbar_init(&ms->mbar[1], 1);
+    tc::mbar_init(&ms->mbar[MB_TILE], 1);
     tc::fence_mbar_init();
     ms->failed = 0;
     ms->rotated = 0;
