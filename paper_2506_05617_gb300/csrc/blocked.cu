@@ -558,7 +558,7 @@ __device__ __forceinline__ void outer_pair(int t, int pos, int nb, int& I, int& 
 // One symbol per CTA (a persistent grid pulling symbols from an atomic work queue). Per symbol:
 // assembly of X = A_k (or A_k^*) into the CTA's workspace slot and W = I; sweeps over the block
 // pairs in circle-method order (nb - 1 rounds of nb / 2 pairs); then sigma, ranks and the
-// normalised factors written to the layer's outputs. One CTA of 512 threads per SM.
+// normalised factors written to the layer's outputs. CTAs of 256 threads, two per SM.
 template <bool VEC>
 __global__ void __maxnreg__(bj::MAX_REGS) bj_kernel(const __grid_constant__ BJLaunch A) {
   using namespace bj;
@@ -566,10 +566,8 @@ __global__ void __maxnreg__(bj::MAX_REGS) bj_kernel(const __grid_constant__ BJLa
   __shared__ int scols[P];
   __shared__ float sinv[2][P];          // 1/|x_c| (0 for a negligible column), 1/|w_c| of 64 columns
   __shared__ int srank[P];
-  const LayerArgs& La = A.L;
   Counters* ctr = A.counters;
   const int Mp = A.Mp, Np = A.Np, ldx = A.ldx, ldw = A.ldw;
-  const int M = La.M, N = La.N;
   const int nb = Np / B;
   float* Xr = A.ws + (size_t)blockIdx.x * A.slot_floats;
   float* Xi = Xr + (size_t)Np * ldx;
@@ -587,8 +585,13 @@ __global__ void __maxnreg__(bj::MAX_REGS) bj_kernel(const __grid_constant__ BJLa
   for (;;) {
     if (threadIdx.x == 0) ms->item = (int)atomicAdd(queue, 1u);
     __syncthreads();
-    const int h = ms->item;
-    if (h >= A.total_items) break;
+    const int item = ms->item;
+    if (item >= A.total_items) break;
+    int lk = 0;                                         // the item's layer
+    while (lk + 1 < A.nlayers && item >= A.L[lk + 1].item_begin) ++lk;
+    const LayerArgs& La = A.L[lk];
+    const int h = item - La.item_begin;                 // half-grid symbol of that layer
+    const int M = La.M, N = La.N;
     const long long c_sym = clock64();
     const int f = La.half[h];
     const int jj = f / La.m, ll = f - jj * La.m;
@@ -782,6 +785,13 @@ static cudaError_t bj_prepare_t(int sms, int* max_ctas) {
 // The route serves 128 to 512 columns (fewer leave most of the 128-column padding idle) and up
 // to 512 rows.
 bool bj_supported(int M, int N) { return N >= 128 && M <= 512 && N <= 512; }
+
+// The built-in choice takes the blocked route for tall or square symbols of 256-512 columns when a
+// layer has enough symbols to fill the GPU. One symbol per CTA takes ~20 ms at 256 columns, ~55 ms
+// at 384 and ~125 ms at 512 (alone on an SM, values), while the element-wise cluster kernels spread
+// a symbol over up to 16 SMs at ~0.24, ~1.9 and ~1.9 ms of throughput per symbol (GB300): the
+// blocked route is the faster one from about 84, 30 and 68 symbols.
+int bj_min_symbols(int N) { return N <= 256 ? 84 : N <= 384 ? 30 : 68; }
 void bj_dims(int M, int N, int* Mp, int* Np) {
   *Mp = (M + bj::RT - 1) / bj::RT * bj::RT;
   *Np = (N + 127) / 128 * 128;

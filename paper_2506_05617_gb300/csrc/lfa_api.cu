@@ -5,6 +5,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
+#include <memory>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -231,9 +232,12 @@ struct lfa_plan_s {
   // layers whose W does not fit registers: values-mode forward with a rotation log + replay
   struct Logged { int layer; int variant; int grid; int batch; int log_cap; int sweeps_cap; };
   std::vector<Logged> logged;
-  // layers on the blocked tensor-core route: one persistent launch each
+  // layers on the blocked tensor-core route, and their launches: one persistent launch per group of
+  // layers whose symbols pad to the same Mp x Np (indices into `blocked`), with its CTA count
   struct Blocked { int layer; int ctas; };
   std::vector<Blocked> blocked;
+  struct BlockedGroup { std::vector<int> members; int ctas; int Mp, Np; };
+  std::vector<BlockedGroup> bj_groups;
   float* bj_ws = nullptr;
   float4* log_ws = nullptr;
   int32_t* rounds_ws = nullptr;
@@ -361,31 +365,41 @@ lfa_status_t enqueue_forward(lfa_plan_s* p, const float* const* w, float* const*
       for (int k = 0; k < P.nlayers; ++k)
         LFA_CUDA_TRY(launch_complete(P.L[k], P.L[k].wide ? P.L[k].V : P.L[k].U, P.L[k].F_h, s));
   }
-  // blocked layers: one persistent launch each (queue slot 14), then the completion of zero columns
-  for (const auto& bl : p->blocked) {
-    BJLaunch A{};
-    A.L = p->args[bl.layer];
-    A.L.w = w[bl.layer];
-    A.L.sigma = sigma[bl.layer];
-    A.L.U = p->vec ? reinterpret_cast<float2*>(U[bl.layer]) : nullptr;
-    A.L.V = p->vec ? reinterpret_cast<float2*>(V[bl.layer]) : nullptr;
-    A.L.item_begin = 0;
-    int Mp = 0, Np = 0;
-    bj_dims(A.L.M, A.L.N, &Mp, &Np);
-    A.Mp = Mp;
-    A.Np = Np;
-    A.ldx = Mp;
-    A.ldw = Np;
-    A.ws = p->bj_ws;
-    A.slot_floats = bj_slot_floats(A.L.M, A.L.N, p->vec);
-    A.total_items = A.L.F_h;
-    A.max_sweeps = p->max_sweeps;
-    A.half_output = p->half_output;
-    A.queue_slot = 14;
-    A.counters = p->counters;
+  // blocked layers: one persistent launch per group of same-size layers (queue slot 14), then the
+  // completion of zero columns per layer
+  for (const auto& bg : p->bj_groups) {
+    // BJLaunch holds kMaxLayers layers (~10 KB): built on the heap, passed by value at launch
+    std::unique_ptr<BJLaunch> A(new (std::nothrow) BJLaunch());
+    if (!A) return LFA_ERR_OOM;
+    int items = 0;
+    for (size_t k = 0; k < bg.members.size(); ++k) {
+      const int l = p->blocked[bg.members[k]].layer;
+      LayerArgs& La = A->L[k];
+      La = p->args[l];
+      La.w = w[l];
+      La.sigma = sigma[l];
+      La.U = p->vec ? reinterpret_cast<float2*>(U[l]) : nullptr;
+      La.V = p->vec ? reinterpret_cast<float2*>(V[l]) : nullptr;
+      La.item_begin = items;
+      items += La.F_h;
+    }
+    A->nlayers = (int)bg.members.size();
+    A->Mp = bg.Mp;
+    A->Np = bg.Np;
+    A->ldx = bg.Mp;
+    A->ldw = bg.Np;
+    A->ws = p->bj_ws;
+    A->slot_floats = bj_slot_floats(bg.Mp, bg.Np, p->vec);
+    A->total_items = items;
+    A->max_sweeps = p->max_sweeps;
+    A->half_output = p->half_output;
+    A->queue_slot = 14;
+    A->counters = p->counters;
     LFA_CUDA_TRY(cudaMemsetAsync(&p->counters->queue[14], 0, sizeof(unsigned), s));
-    LFA_CUDA_TRY(launch_bj(A, bl.ctas, p->vec, s));
-    if (p->vec) LFA_CUDA_TRY(launch_complete(A.L, A.L.wide ? A.L.V : A.L.U, A.L.F_h, s));
+    LFA_CUDA_TRY(launch_bj(*A, bg.ctas, p->vec, s));
+    if (p->vec)
+      for (int k = 0; k < A->nlayers; ++k)
+        LFA_CUDA_TRY(launch_complete(A->L[k], A->L[k].wide ? A->L[k].V : A->L[k].U, A->L[k].F_h, s));
   }
   // logged layers: per batch of symbols, the values-mode forward that logs its rotations and
   // writes sigma and the X-side vectors, then the replay that builds W
@@ -448,7 +462,8 @@ int64_t logged_launches(const lfa_plan_s* p) {
     for (const auto& g : p->groups)
       if (kVariants[g.variant].CS > 1)
         for (int l : g.layers) n += (p->args[l].F_h + 65534) / 65535;
-  for (const auto& bl : p->blocked) n += 1 + (p->vec ? (p->args[bl.layer].F_h + 65534) / 65535 : 0);
+  n += (int64_t)p->bj_groups.size();
+  for (const auto& bl : p->blocked) n += p->vec ? (p->args[bl.layer].F_h + 65534) / 65535 : 0;
   return n;
 }
 
@@ -537,10 +552,13 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
     // a requested (option, then autotuner cache) variant, possibly with the rotation-log route
     const int requested[2] = {opt ? opt->variant : -1, tuned_variant(opt ? opt->tune_cache : nullptr, La.M, La.N, p->vec)};
     bool blocked = false;
-    for (int rq : requested) {
+    for (int q = 0; q < 2; ++q) {
+      const int rq = requested[q];
       if (v >= 0 || blocked || rq < 0) continue;
       if (rq == LFA_VARIANT_BLOCKED) {
-        if (!p->plain && bj_supported(La.M, La.N)) blocked = true;
+        // an explicit request always takes the route; the autotuner cache's choice (timed on a
+        // layer with many symbols) only when this layer has enough symbols to fill the GPU
+        if (!p->plain && bj_supported(La.M, La.N) && (q == 0 || La.F_h >= bj_min_symbols(La.N))) blocked = true;
       } else if (rq & LFA_VARIANT_LOGGED) {
         const int id = rq & (LFA_VARIANT_LOGGED - 1);
         if (can_log && id < kNumVariants && logged_ok(id, La.M, La.N)) { v = id; logged = true; }
@@ -549,15 +567,16 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
       }
     }
     // built-in choice: the blocked tensor-core route for tall or square symbols of 256 columns and
-    // more (measured faster than the element-wise kernels there, with and without vectors)
-    if (v < 0 && !blocked && !p->plain && !La.wide && La.N >= 256 && bj_supported(La.M, La.N)) blocked = true;
+    // more, in layers with enough symbols to fill the GPU (bj_min_symbols); measured faster than the
+    // element-wise kernels there, with and without vectors
+    if (v < 0 && !blocked && !p->plain && !La.wide && La.N >= 256 && bj_supported(La.M, La.N) &&
+        La.F_h >= bj_min_symbols(La.N))
+      blocked = true;
     if (blocked) {
       int ctas = 0;
       cudaError_t be = bj_max_ctas(p->vec, prop.multiProcessorCount, &ctas);
       if (be != cudaSuccess || ctas < 1) { free_plan(p); return be != cudaSuccess ? from_cuda(be) : LFA_ERR_UNSUPPORTED; }
-      ctas = std::min(ctas, std::max(1, La.F_h));
-      p->blocked.push_back({l, ctas});
-      bj_bytes = std::max(bj_bytes, (size_t)ctas * bj_slot_floats(La.M, La.N, p->vec) * sizeof(float));
+      p->blocked.push_back({l, ctas});   // the CTA count is the launch's, set per group below
       p->variant[l] = -1;
     }
     if (!blocked && v < 0) v = choose_variant(La.M, La.N, p->vec);
@@ -615,6 +634,27 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
       p->bw_chunks[l] = (int)chunks;
       part_bytes = std::max(part_bytes, (size_t)(chunks * CC * La.kh * La.kw * 4));
     }
+  }
+  // blocked launches: layers whose symbols pad to the same Mp x Np share one persistent launch
+  for (int b = 0; b < (int)p->blocked.size(); ++b) {
+    const LayerArgs& La = p->args[p->blocked[b].layer];
+    int Mp = 0, Np = 0;
+    bj_dims(La.M, La.N, &Mp, &Np);
+    auto it = std::find_if(p->bj_groups.begin(), p->bj_groups.end(),
+                           [&](const lfa_plan_s::BlockedGroup& g) { return g.Mp == Mp && g.Np == Np; });
+    if (it == p->bj_groups.end()) {
+      p->bj_groups.push_back({{b}, 0, Mp, Np});
+      it = p->bj_groups.end() - 1;
+    } else {
+      it->members.push_back(b);
+    }
+  }
+  for (auto& g : p->bj_groups) {
+    int items = 0;
+    for (int b : g.members) items += p->args[p->blocked[b].layer].F_h;
+    g.ctas = std::min(p->blocked[g.members[0]].ctas, std::max(1, items));
+    for (int b : g.members) p->blocked[b].ctas = g.ctas;
+    bj_bytes = std::max(bj_bytes, (size_t)g.ctas * bj_slot_floats(g.Mp, g.Np, p->vec) * sizeof(float));
   }
   const size_t off_sym = bytes; bytes += align256(sym_bytes);
   const size_t off_g = bytes; bytes += align256(g_bytes);

@@ -147,9 +147,11 @@ cudaError_t prepare_replay(int NP);   // kernel attributes, once per plan
 bool replay_supported(int NP);        // a replay configuration exists for NP pairs
 
 // Blocked one-sided Jacobi on the tensor cores (blocked.cu): one CTA per symbol, X and W in a
-// per-CTA workspace slot (column-major real / imaginary planes).
+// per-CTA workspace slot (column-major real / imaginary planes). One launch serves the layers whose
+// symbols pad to the same Mp x Np; layer k's symbols are items [L[k].item_begin, + L[k].F_h).
 struct BJLaunch {
-  LayerArgs L;
+  LayerArgs L[kMaxLayers];
+  int32_t nlayers;
   int32_t Mp, Np;           // padded rows of X (multiple of 128) and columns (multiple of 128)
   int32_t ldx, ldw;         // leading dimensions of the X and W planes
   float* ws;                // slots of slot_floats floats, one per CTA of the grid
@@ -161,6 +163,7 @@ struct BJLaunch {
   Counters* counters;
 };
 bool bj_supported(int M, int N);
+int bj_min_symbols(int N);   // half-grid symbols from which the built-in choice takes the route
 void bj_dims(int M, int N, int* Mp, int* Np);
 size_t bj_slot_floats(int M, int N, bool vec);
 cudaError_t bj_max_ctas(bool vec, int sms, int* ctas);   // co-resident CTAs (kernel attributes set)

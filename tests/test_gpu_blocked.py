@@ -59,13 +59,41 @@ def test_blocked_route_matches_oracle(spec):
 
 def test_blocked_route_is_the_default_for_wide_channel_layers():
     """Tall or square symbols of 256 to 512 columns take the blocked route by default (and with the
-    committed autotuner cache); 128 columns and wide symbols keep the element-wise kernels."""
+    committed autotuner cache) when the layer has enough symbols to fill the GPU (74 half-grid
+    symbols at 12 x 12, 100 at 14 x 14, 34 at 8 x 8 for 384 columns); a 512-channel layer on 4 x 4 (10 symbols), 128 columns and
+    wide symbols keep the element-wise kernels."""
     import os
     cache = os.path.join(os.path.dirname(os.path.dirname(__file__)), "paper_2506_05617_gb300", "tune_gb300.txt")
-    for spec, vec, blocked in [((512, 512, 3, 3, 4, 4), True, True), ((512, 512, 3, 3, 4, 4), False, True),
-                               ((256, 256, 3, 3, 4, 4), True, True), ((300, 256, 3, 3, 4, 4), True, True),
-                               ((128, 128, 3, 3, 4, 4), True, False), ((256, 512, 3, 3, 4, 4), True, False)]:
+    for spec, vec, blocked in [((512, 512, 3, 3, 12, 12), True, True), ((512, 512, 3, 3, 12, 12), False, True),
+                               ((256, 256, 3, 3, 14, 14), True, True), ((300, 256, 3, 3, 14, 14), True, True),
+                               ((384, 384, 3, 3, 8, 8), False, True),
+                               ((512, 512, 3, 3, 4, 4), False, False), ((512, 512, 3, 3, 7, 7), False, False),
+                               ((128, 128, 3, 3, 4, 4), True, False), ((256, 512, 3, 3, 14, 14), True, False)]:
         for tc in (None, cache):
             plan = LfaPlan([spec], vectors=vec, tune_cache=tc)
             assert (plan.meta[0]["variant"] == C.LFA_VARIANT_BLOCKED) == blocked, (spec, vec, tc)
             plan.close()
+
+
+def test_blocked_layers_share_a_launch():
+    """Layers whose symbols pad to the same size go through one blocked launch (items of several
+    layers in one queue): two 256 x 256 layers and a 300 x 256 one (a launch of its own) on 14 x 14,
+    values and vectors, checked against the oracle on sampled half-grid frequencies of each layer."""
+    specs = [(256, 256, 3, 3, 14, 14), (256, 256, 3, 3, 14, 14), (300, 256, 3, 3, 14, 14)]
+    ws = [rand_w(co, ci, kh, kw, seed=90 + i) for i, (co, ci, kh, kw, n, m) in enumerate(specs)]
+    plan = LfaPlan(specs, vectors=True)
+    assert all(mt["variant"] == C.LFA_VARIANT_BLOCKED for mt in plan.meta)
+    sig, U, V = plan.svd([torch.from_numpy(w).cuda() for w in ws])
+    torch.cuda.synchronize()
+    st, info = plan.info()
+    assert st == C.LFA_OK, info
+    for i, ((co, ci, kh, kw, n, m), w) in enumerate(zip(specs, ws)):
+        half = O.half_grid(n, m)
+        pick = np.sort(np.random.default_rng(i).choice(len(half), 12, replace=False))
+        f = half[pick]
+        s = sig[i].cpu().numpy()
+        s_ref = O.lfa_svd(w, n, m, compute_uv=False, freqs=f)
+        smax = float(s_ref.max())
+        assert np.max(np.abs(s[f].astype(np.float64) - s_ref)) <= 1e-5 * smax
+        check_factors(O.symbols(w, n, m)[f], s[f], U[i].cpu().numpy()[pick], V[i].cpu().numpy()[pick])
+    plan.close()
