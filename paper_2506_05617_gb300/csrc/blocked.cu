@@ -112,13 +112,15 @@ __device__ __forceinline__ void wait_buf(unsigned char* sm, Counters* ctr, int b
 // A chunk of KC = 32 rows is staged as TF32 hi | lo (16 KB each), core matrix (kc, pg) = (rows
 // 4kc..4kc+3, Z columns 8pg..8pg+7) at byte ((kc * 16 + pg) * 8) * 16: LBO (along K) = 2048 B, SBO
 // (along M/N) = 128 B.
-// Two chunk buffers alternate; each thread loads its next chunk into registers while the tensor
-// core works on the current one.
+// Two chunk buffers alternate; the next two chunks are in flight (asynchronous copies into raw
+// buffers) while the tensor core works on the current one.
 __device__ void gram_pair(unsigned char* sm, const float* Xr, const float* Xi, int ld, int Mp, const int* cols,
                           Counters* ctr, uint32_t& ph) {
   Misc* ms = misc(sm);
   constexpr uint32_t LBO = 2048, SBO = 128, LO = KC * 2 * P * 4;
   constexpr uint32_t ID = tc::idesc_tf32(128, 128);
+  constexpr int RAW = KC * 2 * P * 4;               // bytes of one raw chunk (fp32, staged layout)
+  static_assert(OFF_UPD + 2 * RAW <= REGION_BYTES, "two raw chunks fit the update buffers' place");
   const uint32_t base0 = tc::smem_u32(sm + OFF_STAGE), base1 = tc::smem_u32(sm + OFF_R1);
   constexpr int NIT = KC * 2 * P / 4 / THREADS;   // float4 per thread and chunk
   const float* src[NIT];
@@ -131,32 +133,41 @@ __device__ void gram_pair(unsigned char* sm, const float* Xr, const float* Xi, i
     src[it] = (p < P ? Xr + (size_t)cols[p] * ld : Xi + (size_t)cols[p - P] * ld) + 4 * kc;
     off[it] = ((kc * 16 + pg) * 8 + plo) * 4;
   }
-  // X is rewritten by the update epilogues: read at L2, never through the non-coherent read-only
-  // path or a possibly stale L1 line
-  float4 pre[NIT];
-#pragma unroll
-  for (int it = 0; it < NIT; ++it) pre[it] = __ldcg(reinterpret_cast<const float4*>(src[it]));
+  // Raw chunks arrive by asynchronous copies (at L2: X is rewritten by the update epilogues) into two
+  // raw buffers in the update buffers' place, two chunks ahead; each thread converts the float4s it
+  // copied itself, so its own wait_group is the only synchronisation the raw data needs.
+  float* raw = reinterpret_cast<float*>(sm + OFF_UPD);
   const int n = Mp / KC;
+  auto fetch = [&](int c) {
+    float* r = raw + (c & 1) * (RAW / 4);
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) tc::cp_async16(r + off[it], src[it] + c * KC);
+  };
+  fetch(0);
+  tc::cp_async_commit();
+  if (n > 1) fetch(1);
+  tc::cp_async_commit();
   for (int c = 0; c < n; ++c) {
     const int b = c & 1;
     float* st = reinterpret_cast<float*>(sm + (b ? OFF_R1 : OFF_STAGE));
+    tc::cp_async_wait<1>();                         // chunk c has arrived (c + 1 may be in flight)
+    const float* r = raw + b * (RAW / 4);
 #pragma unroll
     for (int it = 0; it < NIT; ++it) {
+      const float4 v = *reinterpret_cast<const float4*>(r + off[it]);
       float4 h, l;
-      tc::split_tf32(pre[it].x, h.x, l.x);
-      tc::split_tf32(pre[it].y, h.y, l.y);
-      tc::split_tf32(pre[it].z, h.z, l.z);
-      tc::split_tf32(pre[it].w, h.w, l.w);
+      tc::split_tf32(v.x, h.x, l.x);
+      tc::split_tf32(v.y, h.y, l.y);
+      tc::split_tf32(v.z, h.z, l.z);
+      tc::split_tf32(v.w, h.w, l.w);
       *reinterpret_cast<float4*>(st + off[it]) = h;
       *reinterpret_cast<float4*>(st + LO / 4 + off[it]) = l;
     }
+    if (c + 2 < n) fetch(c + 2);                    // into the raw buffer this thread just read
+    tc::cp_async_commit();
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
-    if (c + 1 < n) {
-#pragma unroll
-      for (int it = 0; it < NIT; ++it) pre[it] = __ldcg(reinterpret_cast<const float4*>(src[it] + (c + 1) * KC));
-    }
     if (threadIdx.x == 0 && !ms->failed) {
       tc::fence_after_sync();
 #pragma unroll
@@ -174,6 +185,7 @@ __device__ void gram_pair(unsigned char* sm, const float* Xr, const float* Xi, i
     }
     if (c >= 1) wait_buf(sm, ctr, (c - 1) & 1, ph);   // chunk c - 1 done: its buffer is free for c + 1
   }
+  tc::cp_async_wait<0>();
   wait_buf(sm, ctr, (n - 1) & 1, ph);
 }
 
@@ -244,20 +256,35 @@ __device__ __forceinline__ void inner_pair(int t, int i, bool full, int& a, int&
   else { a = (t + i) % (P - 1); b = (t - i + (P - 1)) % (P - 1); }
 }
 
+// x (1 + cm) + y (ar + i ai) for complex x, y: the one-column form of every 2 x 2 rotation below,
+// as three fused multiply-adds per component.
+__device__ __forceinline__ float2 combo(float2 x, float2 y, float cm, float ar, float ai) {
+  return make_float2(fmaf(-ai, y.y, fmaf(ar, y.x, fmaf(cm, x.x, x.x))),
+                     fmaf(ai, y.x, fmaf(ar, y.y, fmaf(cm, x.y, x.y))));
+}
+
 // One cyclic two-sided Jacobi sweep on H (OFF_R1) accumulating Q (OFF_STAGE, fp32, starts as I):
 // per round, 32 threads choose the rotations of the round's 32 disjoint pairs; then
 // H <- J^* H J by 2 x 2 blocks (P <= P') and Q <- Q J, J = [[1 + cm1, es], [-conj(es), 1 + cm1]]
-// per pair. Returns this thread's count of rotations.
+// per pair. A thread's blocks (P, P') are fixed for the sweep; their columns in round t follow from
+// the schedule (inner_pair). Returns this thread's count of rotations.
 __device__ int inner_sweep(unsigned char* sm, float tol2, bool full) {
+  constexpr int NBLK = (528 + THREADS - 1) / THREADS;       // 2 x 2-block pairs (P, P') per thread
   float2* H = reinterpret_cast<float2*>(sm + OFF_R1);
   float2* Q = reinterpret_cast<float2*>(sm + OFF_STAGE);
   float4* prm = reinterpret_cast<float4*>(sm + OFF_PRM);
-  int* pa = reinterpret_cast<int*>(sm + OFF_PAB);
-  int* pb = pa + 32;
   const uint16_t* tri = reinterpret_cast<const uint16_t*>(sm + OFF_TRI);
   Misc* ms = misc(sm);
   for (int e = threadIdx.x; e < P * P; e += THREADS)
     Q[e] = make_float2((e / P) == (e % P) ? 1.f : 0.f, 0.f);
+  int mp[NBLK], mq[NBLK];
+#pragma unroll
+  for (int k = 0; k < NBLK; ++k) {
+    const int e = threadIdx.x + THREADS * k;
+    const int v = e < 528 ? tri[e] : 0;
+    mp[k] = e < 528 ? v >> 8 : -1;
+    mq[k] = v & 0xff;
+  }
   int nrot = 0;
   constexpr int QW = THREADS / 32;                          // rows of Q per pass
   const int qi = threadIdx.x & 31, qx = threadIdx.x >> 5;   // Q: pair qi, rows qx + QW k
@@ -273,50 +300,41 @@ __device__ int inner_sweep(unsigned char* sm, float tol2, bool full) {
       const bool rot = pair_test(al, be, gr, gi, tol2);
       const float4 q = pair_params(al, be, gr, gi, rot);
       prm[threadIdx.x] = rot ? make_float4(q.x, q.y, q.z, 1.f) : make_float4(0.f, 0.f, 0.f, 0.f);
-      pa[threadIdx.x] = a;
-      pb[threadIdx.x] = b;
       if (rot) { ++nrot; ms->rotated = 1; }
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < 528; e += THREADS) {
-      const int pp = tri[e] >> 8, qq = tri[e] & 0xff;    // pp <= qq
+#pragma unroll
+    for (int k = 0; k < NBLK; ++k) {
+      const int pp = mp[k], qq = mq[k];                     // pp <= qq
+      if (pp < 0) continue;
       const float4 jp = prm[pp], jq = prm[qq];
       if (jp.w == 0.f && jq.w == 0.f) continue;
-      const int a = pa[pp], b = pb[pp], c = pa[qq], d = pb[qq];
-      float2 B00 = H[a * HS + c], B01 = H[a * HS + d], B10 = H[b * HS + c], B11 = H[b * HS + d];
-      float2 T00, T01, T10, T11;
-      {
-        // T = B J_q: t0 = b0 (1 + cm) - b1 conj(es); t1 = b0 es + b1 (1 + cm)
-        const float cm = jq.x, er = jq.y, ei = jq.z;
-        T00 = make_float2(fmaf(cm, B00.x, B00.x) - (B01.x * er + B01.y * ei), fmaf(cm, B00.y, B00.y) - (B01.y * er - B01.x * ei));
-        T01 = make_float2(fmaf(cm, B01.x, B01.x) + (B00.x * er - B00.y * ei), fmaf(cm, B01.y, B01.y) + (B00.x * ei + B00.y * er));
-        T10 = make_float2(fmaf(cm, B10.x, B10.x) - (B11.x * er + B11.y * ei), fmaf(cm, B10.y, B10.y) - (B11.y * er - B11.x * ei));
-        T11 = make_float2(fmaf(cm, B11.x, B11.x) + (B10.x * er - B10.y * ei), fmaf(cm, B11.y, B11.y) + (B10.x * ei + B10.y * er));
-      }
-      {
-        // B' = J_p^* T: row a' = (1 + cm) row_a - es row_b; row b' = conj(es) row_a + (1 + cm) row_b
-        const float cm = jp.x, er = jp.y, ei = jp.z;
-        B00 = make_float2(fmaf(cm, T00.x, T00.x) - (T10.x * er - T10.y * ei), fmaf(cm, T00.y, T00.y) - (T10.x * ei + T10.y * er));
-        B01 = make_float2(fmaf(cm, T01.x, T01.x) - (T11.x * er - T11.y * ei), fmaf(cm, T01.y, T01.y) - (T11.x * ei + T11.y * er));
-        B10 = make_float2(fmaf(cm, T10.x, T10.x) + (T00.x * er + T00.y * ei), fmaf(cm, T10.y, T10.y) + (T00.y * er - T00.x * ei));
-        B11 = make_float2(fmaf(cm, T11.x, T11.x) + (T01.x * er + T01.y * ei), fmaf(cm, T11.y, T11.y) + (T01.y * er - T01.x * ei));
-      }
-      H[a * HS + c] = B00;
-      H[a * HS + d] = B01;
-      H[b * HS + c] = B10;
-      H[b * HS + d] = B11;
+      int a, b, c, d;
+      inner_pair(t, pp, full, a, b);
+      inner_pair(t, qq, full, c, d);
+      const float2 B00 = H[a * HS + c], B01 = H[a * HS + d], B10 = H[b * HS + c], B11 = H[b * HS + d];
+      // T = B J_q: t0 = b0 (1 + cm) - b1 conj(es); t1 = b1 (1 + cm) + b0 es
+      const float2 T00 = combo(B00, B01, jq.x, -jq.y, jq.z), T01 = combo(B01, B00, jq.x, jq.y, jq.z);
+      const float2 T10 = combo(B10, B11, jq.x, -jq.y, jq.z), T11 = combo(B11, B10, jq.x, jq.y, jq.z);
+      // B' = J_p^* T: row a' = (1 + cm) row_a - es row_b; row b' = (1 + cm) row_b + conj(es) row_a
+      const float2 C00 = combo(T00, T10, jp.x, -jp.y, -jp.z), C01 = combo(T01, T11, jp.x, -jp.y, -jp.z);
+      const float2 C10 = combo(T10, T00, jp.x, jp.y, -jp.z), C11 = combo(T11, T01, jp.x, jp.y, -jp.z);
+      H[a * HS + c] = C00;
+      H[a * HS + d] = C01;
+      H[b * HS + c] = C10;
+      H[b * HS + d] = C11;
       if (pp != qq) {
-        H[c * HS + a] = make_float2(B00.x, -B00.y);
-        H[d * HS + a] = make_float2(B01.x, -B01.y);
-        H[c * HS + b] = make_float2(B10.x, -B10.y);
-        H[d * HS + b] = make_float2(B11.x, -B11.y);
+        H[c * HS + a] = make_float2(C00.x, -C00.y);
+        H[d * HS + a] = make_float2(C01.x, -C01.y);
+        H[c * HS + b] = make_float2(C10.x, -C10.y);
+        H[d * HS + b] = make_float2(C11.x, -C11.y);
       }
     }
     {
       const float4 j = prm[qi];
       if (j.w != 0.f) {
-        const int a = pa[qi], b = pb[qi];
-        const float cm = j.x, er = j.y, ei = j.z;
+        int a, b;
+        inner_pair(t, qi, full, a, b);
         // every row's pair of entries first, then the rotated values (loads not held up by stores)
         float2 qa[P / QW], qb[P / QW];
 #pragma unroll
@@ -327,10 +345,8 @@ __device__ int inner_sweep(unsigned char* sm, float tol2, bool full) {
 #pragma unroll
         for (int k = 0; k < P / QW; ++k) {
           const int x = qx + QW * k;
-          Q[x * P + a] = make_float2(fmaf(cm, qa[k].x, qa[k].x) - (qb[k].x * er + qb[k].y * ei),
-                                     fmaf(cm, qa[k].y, qa[k].y) - (qb[k].y * er - qb[k].x * ei));
-          Q[x * P + b] = make_float2(fmaf(cm, qb[k].x, qb[k].x) + (qa[k].x * er - qa[k].y * ei),
-                                     fmaf(cm, qb[k].y, qb[k].y) + (qa[k].x * ei + qa[k].y * er));
+          Q[x * P + a] = combo(qa[k], qb[k], j.x, -j.y, j.z);   // qa (1 + cm) - qb conj(es)
+          Q[x * P + b] = combo(qb[k], qa[k], j.x, j.y, j.z);    // qb (1 + cm) + qa es
         }
       }
     }
@@ -581,7 +597,11 @@ __global__ void __maxnreg__(bj::MAX_REGS) bj_kernel(const __grid_constant__ BJLa
   unsigned int* queue = &ctr->queue[A.queue_slot];
 
   // phase clocks of thread 0: Gram, inner sweep, update, assembly, output, whole symbols
-  unsigned long long cyc[6] = {0, 0, 0, 0, 0, 0};
+  // kept in shared memory by thread 0 (no registers held across the phases)
+  __shared__ unsigned long long cyc[6];
+  __shared__ long long c_sym, c_ph;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 6; ++k) cyc[k] = 0;
   for (;;) {
     if (threadIdx.x == 0) ms->item = (int)atomicAdd(queue, 1u);
     __syncthreads();
@@ -592,7 +612,7 @@ __global__ void __maxnreg__(bj::MAX_REGS) bj_kernel(const __grid_constant__ BJLa
     const LayerArgs& La = A.L[lk];
     const int h = item - La.item_begin;                 // half-grid symbol of that layer
     const int M = La.M, N = La.N;
-    const long long c_sym = clock64();
+    if (threadIdx.x == 0) c_sym = clock64();
     const int f = La.half[h];
     const int jj = f / La.m, ll = f - jj * La.m;
     const int kk = La.kh * La.kw;
@@ -614,8 +634,10 @@ __global__ void __maxnreg__(bj::MAX_REGS) bj_kernel(const __grid_constant__ BJLa
     }
     __threadfence_block();
     __syncthreads();
-    long long c_ph = clock64();
-    cyc[3] += (unsigned long long)(c_ph - c_sym);
+    if (threadIdx.x == 0) {
+      c_ph = clock64();
+      cyc[3] += (unsigned long long)(c_ph - c_sym);
+    }
     // ---- sweeps
     int sweeps = 0, nrot = 0, ngram = 0, nupd = 0;
     bool converged = false;
@@ -632,14 +654,18 @@ __global__ void __maxnreg__(bj::MAX_REGS) bj_kernel(const __grid_constant__ BJLa
           const bool full = (t == 0);         // the first round of the sweep: intra-block pairs too
           gram_to_h(sm, La.tol2, full);
           ++ngram;
-          long long c1 = clock64();
-          cyc[0] += (unsigned long long)(c1 - c_ph);
-          c_ph = c1;
+          if (threadIdx.x == 0) {
+            const long long c1 = clock64();
+            cyc[0] += (unsigned long long)(c1 - c_ph);
+            c_ph = c1;
+          }
           if (ms->any) {                      // else no pair of the block pair rotates: skip the rest
             nrot += inner_sweep(sm, La.tol2, full);
-            c1 = clock64();
-            cyc[1] += (unsigned long long)(c1 - c_ph);
-            c_ph = c1;
+            if (threadIdx.x == 0) {
+              const long long c1 = clock64();
+              cyc[1] += (unsigned long long)(c1 - c_ph);
+              c_ph = c1;
+            }
             if (ms->rotated) {
               rotated_sweep = 1;
               ++nupd;
@@ -648,9 +674,11 @@ __global__ void __maxnreg__(bj::MAX_REGS) bj_kernel(const __grid_constant__ BJLa
             }
           }
           __syncthreads();
-          c1 = clock64();
-          cyc[2] += (unsigned long long)(c1 - c_ph);
-          c_ph = c1;
+          if (threadIdx.x == 0) {
+            const long long c1 = clock64();
+            cyc[2] += (unsigned long long)(c1 - c_ph);
+            c_ph = c1;
+          }
         }
       }
       ++sweeps;
@@ -756,9 +784,11 @@ __global__ void __maxnreg__(bj::MAX_REGS) bj_kernel(const __grid_constant__ BJLa
       __syncthreads();
     }
     __syncthreads();   // the slot is reused by the CTA's next symbol
-    const long long c_end = clock64();
-    cyc[4] += (unsigned long long)(c_end - c_ph);
-    cyc[5] += (unsigned long long)(c_end - c_sym);
+    if (threadIdx.x == 0) {
+      const long long c_end = clock64();
+      cyc[4] += (unsigned long long)(c_end - c_ph);
+      cyc[5] += (unsigned long long)(c_end - c_sym);
+    }
   }
   if (threadIdx.x == 0)
     for (int k = 0; k < 6; ++k) atomicAdd(&ctr->bj_cycles[k], cyc[k]);

@@ -139,6 +139,17 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// ---------------------------------------------------------------------------------- async copies
+// 16 bytes global -> shared, cached at L2 only (not L1); completes asynchronously. Both addresses
+// 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// Waits until at most n of this thread's committed groups are still in flight.
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // ---------------------------------------------------------------------------------- TF32 split
 // x = hi + lo with hi = x rounded to TF32 (nearest, ties away) and lo = (x - hi) rounded to TF32:
 // the operands of the 3xTF32 product hi*hi + hi*lo + lo*hi, whose error is a few fp32 units.
