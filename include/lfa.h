@@ -118,7 +118,9 @@ typedef struct lfa_options {
                            LFA_VARIANT_LOGGED | v (plans with LFA_VECTORS) runs values-mode
                            variant v with the rotation log, the W replay and the finalize
                            kernel instead of carrying W in registers */
-  int32_t use_graph;    /* 1 (default if <0): lfa_svd replays a captured CUDA graph */
+  int32_t use_graph;    /* 1 (default if <0): lfa_svd and lfa_svd_backward replay a CUDA graph
+                           captured on their first call with a given set of buffers (the
+                           forward's independent kernel groups as parallel branches) */
   const char* tune_cache; /* nullable path of the autotuner's cache (text); read at plan time */
   /* Frequency sharding (the frequencies are independent problems, Algorithm 1; the paper calls
    * LFA embarrassingly parallel, Sec. V). With shard_count = R > 1 every layer's half grid
@@ -225,8 +227,11 @@ lfa_status_t lfa_expand(lfa_plan_t plan, int32_t layer, const float* U, const fl
  *  dsigma[l] device float32 in sigma's layout (input)
  *  U[l], V[l] the lfa_svd outputs of the same w (input)
  *  dw[l]     device float32 [c_out][c_in][kh][kw], overwritten (output)
+ * Stride-1 layers with c_out, c_in >= 128 and at most 25 taps form G_k on the tensor cores
+ * (TF32 split in three, FP32 accuracy); other layers on the CUDA cores.
  * Deterministic (fixed reduction order; no float atomics). Requires a plan with
- * LFA_VECTORS (else LFA_ERR_INVALID_ARG). Asynchronous. */
+ * LFA_VECTORS (else LFA_ERR_INVALID_ARG). Allocates nothing; asynchronous (all layers in one
+ * replayed CUDA graph unless the plan was created with use_graph = 0). */
 lfa_status_t lfa_svd_backward(lfa_plan_t plan, const float* const* dsigma, const float* const* U,
                               const float* const* V, float* const* dw, void* stream);
 

@@ -258,11 +258,22 @@ struct lfa_plan_s {
   std::vector<void*> fft_plans;
   std::vector<int> fft_pairs;
   void* fft_ws = nullptr;
+  // independent parts of a forward (each element-wise group; all blocked groups; all logged
+  // batches) run on their own streams, forked from and joined back into the caller's stream (under
+  // capture: parallel branches of the graph)
+  std::vector<cudaStream_t> branch;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
   // graph cache
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<const void*> graph_key;
+  // the backward of all layers, captured once per set of buffers like the forward
+  cudaGraph_t bw_graph = nullptr;
+  cudaGraphExec_t bw_exec = nullptr;
+  std::vector<const void*> bw_key;
+  int64_t bw_kernels = 0;                 // kernels in the captured backward
   cudaStream_t last_stream = nullptr;
 };
 
@@ -296,50 +307,24 @@ void free_plan(lfa_plan_s* p) {
     if (h) fft_destroy_plan(h);
   if (p->exec) cudaGraphExecDestroy(p->exec);
   if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->bw_exec) cudaGraphExecDestroy(p->bw_exec);
+  if (p->bw_graph) cudaGraphDestroy(p->bw_graph);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  for (cudaStream_t b : p->branch)
+    if (b) cudaStreamDestroy(b);
+  for (cudaEvent_t e : p->join)
+    if (e) cudaEventDestroy(e);
+  if (p->fork) cudaEventDestroy(p->fork);
   if (p->dmem) cudaFree(p->dmem);
   delete p;
 }
 
-// Enqueue the forward work of one call on stream s (used directly or under capture).
-lfa_status_t enqueue_forward(lfa_plan_s* p, const float* const* w, float* const* sigma,
-                             float* const* U, float* const* V, cudaStream_t s) {
-  LFA_CUDA_TRY(cudaMemsetAsync(p->counters, 0, sizeof(Counters), s));
-  if (fault("launch")) return from_cuda(cudaErrorLaunchFailure);
-  if (p->plain) {
-    // plain per-layer path: materialise the symbols, then one Jacobi launch per layer
-    for (int l = 0; l < p->nlayers; ++l) {
-      LayerArgs La = p->args[l];
-      La.w = w[l];
-      La.sigma = sigma[l];
-      La.symbols = p->sym_ws;
-      La.item_begin = 0;
-      if (p->fft) {
-        int nk = 0;
-        LFA_CUDA_TRY(launch_fft_symbols(La, p->fft_plans[l], p->fft_pairs[l], p->fft_ws, p->sym_ws, s, &nk));
-        g_launches += nk;
-      } else {
-        LFA_CUDA_TRY(launch_symbols(La, p->sym_ws, s));
-        g_launches += 1;
-      }
-      JacobiLaunch P{};
-      P.L[0] = La;
-      P.nlayers = 1;
-      const int spu = variant_spu(p->variant[l]);
-      P.total_items = (La.F_h + spu - 1) / spu;
-      P.max_sweeps = p->max_sweeps;
-      P.half_output = p->half_output;
-      P.queue_slot = l % 16;
-      P.counters = p->counters;
-      const int grid = p->plain_grid[l];
-      if (l >= 16) LFA_CUDA_TRY(cudaMemsetAsync(&p->counters->queue[l % 16], 0, sizeof(unsigned), s));
-      LFA_CUDA_TRY(vlaunch(p->variant[l], false, false, P, grid, s));
-      g_launches += 1;
-    }
-    return LFA_OK;
-  }
-  int slot = 0;
-  for (const auto& g : p->groups) {
+// One element-wise variant group of a forward: one persistent launch over all its layers (queue slot
+// gi), then the completion of zero columns for cluster variants with vectors.
+lfa_status_t enqueue_group(lfa_plan_s* p, int gi, const float* const* w, float* const* sigma, float* const* U,
+                           float* const* V, cudaStream_t s) {
+  const auto& g = p->groups[gi];
+  {
     JacobiLaunch P{};
     int items = 0;
     for (size_t k = 0; k < g.layers.size(); ++k) {
@@ -357,7 +342,7 @@ lfa_status_t enqueue_forward(lfa_plan_s* p, const float* const* w, float* const*
     P.total_items = items;
     P.max_sweeps = p->max_sweeps;
     P.half_output = p->half_output;
-    P.queue_slot = slot++;
+    P.queue_slot = gi;
     P.counters = p->counters;
     LFA_CUDA_TRY(vlaunch(g.variant, p->vec, true, P, g.grid, s));
     // cluster variants write zero vectors for negligible singular values: complete them
@@ -365,6 +350,11 @@ lfa_status_t enqueue_forward(lfa_plan_s* p, const float* const* w, float* const*
       for (int k = 0; k < P.nlayers; ++k)
         LFA_CUDA_TRY(launch_complete(P.L[k], P.L[k].wide ? P.L[k].V : P.L[k].U, P.L[k].F_h, s));
   }
+  return LFA_OK;
+}
+
+lfa_status_t enqueue_blocked(lfa_plan_s* p, const float* const* w, float* const* sigma, float* const* U,
+                             float* const* V, cudaStream_t s) {
   // blocked layers: one persistent launch per group of same-size layers (queue slot 14), then the
   // completion of zero columns per layer
   for (const auto& bg : p->bj_groups) {
@@ -401,6 +391,11 @@ lfa_status_t enqueue_forward(lfa_plan_s* p, const float* const* w, float* const*
       for (int k = 0; k < A->nlayers; ++k)
         LFA_CUDA_TRY(launch_complete(A->L[k], A->L[k].wide ? A->L[k].V : A->L[k].U, A->L[k].F_h, s));
   }
+  return LFA_OK;
+}
+
+lfa_status_t enqueue_logged(lfa_plan_s* p, const float* const* w, float* const* sigma, float* const* U,
+                            float* const* V, cudaStream_t s) {
   // logged layers: per batch of symbols, the values-mode forward that logs its rotations and
   // writes sigma and the X-side vectors, then the replay that builds W
   for (const auto& lg : p->logged) {
@@ -445,6 +440,69 @@ lfa_status_t enqueue_forward(lfa_plan_s* p, const float* const* w, float* const*
       LFA_CUDA_TRY(launch_replay(NP, R, cnt, s, &nk));
       LFA_CUDA_TRY(launch_complete(La, La.wide ? La.V : La.U, cnt, s));
     }
+  }
+  return LFA_OK;
+}
+
+// Enqueue the forward work of one call on stream s (used directly or under capture).
+lfa_status_t enqueue_forward(lfa_plan_s* p, const float* const* w, float* const* sigma,
+                             float* const* U, float* const* V, cudaStream_t s) {
+  LFA_CUDA_TRY(cudaMemsetAsync(p->counters, 0, sizeof(Counters), s));
+  if (fault("launch")) return from_cuda(cudaErrorLaunchFailure);
+  if (p->plain) {
+    // plain per-layer path: materialise the symbols, then one Jacobi launch per layer
+    for (int l = 0; l < p->nlayers; ++l) {
+      LayerArgs La = p->args[l];
+      La.w = w[l];
+      La.sigma = sigma[l];
+      La.symbols = p->sym_ws;
+      La.item_begin = 0;
+      if (p->fft) {
+        int nk = 0;
+        LFA_CUDA_TRY(launch_fft_symbols(La, p->fft_plans[l], p->fft_pairs[l], p->fft_ws, p->sym_ws, s, &nk));
+        g_launches += nk;
+      } else {
+        LFA_CUDA_TRY(launch_symbols(La, p->sym_ws, s));
+        g_launches += 1;
+      }
+      JacobiLaunch P{};
+      P.L[0] = La;
+      P.nlayers = 1;
+      const int spu = variant_spu(p->variant[l]);
+      P.total_items = (La.F_h + spu - 1) / spu;
+      P.max_sweeps = p->max_sweeps;
+      P.half_output = p->half_output;
+      P.queue_slot = l % 16;
+      P.counters = p->counters;
+      const int grid = p->plain_grid[l];
+      if (l >= 16) LFA_CUDA_TRY(cudaMemsetAsync(&p->counters->queue[l % 16], 0, sizeof(unsigned), s));
+      LFA_CUDA_TRY(vlaunch(p->variant[l], false, false, P, grid, s));
+      g_launches += 1;
+    }
+    return LFA_OK;
+  }
+  // the parts of the forward, each a function of the stream it is enqueued on
+  std::vector<std::function<lfa_status_t(cudaStream_t)>> parts;
+  for (size_t gi = 0; gi < p->groups.size(); ++gi)
+    parts.push_back([=](cudaStream_t st) { return enqueue_group(p, (int)gi, w, sigma, U, V, st); });
+  if (!p->bj_groups.empty())
+    parts.push_back([=](cudaStream_t st) { return enqueue_blocked(p, w, sigma, U, V, st); });
+  if (!p->logged.empty())
+    parts.push_back([=](cudaStream_t st) { return enqueue_logged(p, w, sigma, U, V, st); });
+  if (parts.size() <= 1 || p->branch.size() < parts.size()) {
+    for (auto& f : parts) {
+      const lfa_status_t st = f(s);
+      if (st != LFA_OK) return st;
+    }
+    return LFA_OK;
+  }
+  LFA_CUDA_TRY(cudaEventRecord(p->fork, s));
+  for (size_t k = 0; k < parts.size(); ++k) {
+    LFA_CUDA_TRY(cudaStreamWaitEvent(p->branch[k], p->fork, 0));
+    const lfa_status_t st = parts[k](p->branch[k]);
+    if (st != LFA_OK) return st;
+    LFA_CUDA_TRY(cudaEventRecord(p->join[k], p->branch[k]));
+    LFA_CUDA_TRY(cudaStreamWaitEvent(s, p->join[k], 0));
   }
   return LFA_OK;
 }
@@ -769,6 +827,19 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
   }
   if (e == cudaSuccess && p->groups.size() > 14) e = cudaErrorInvalidValue;   // 14: blocked, 15: logged layers
   if (e == cudaSuccess && p->use_graph) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+  // streams and events of the forward's parallel parts
+  const size_t nparts = p->groups.size() + (p->bj_groups.empty() ? 0 : 1) + (p->logged.empty() ? 0 : 1);
+  if (e == cudaSuccess && !p->plain && nparts > 1) {
+    e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
+    for (size_t k = 0; k < nparts && e == cudaSuccess; ++k) {
+      cudaStream_t b = nullptr;
+      cudaEvent_t j = nullptr;
+      e = cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking);
+      if (e == cudaSuccess) p->branch.push_back(b);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
+      if (e == cudaSuccess) p->join.push_back(j);
+    }
+  }
   if (e != cudaSuccess) { free_plan(p); return from_cuda(e); }
   *plan = p;
   return LFA_OK;
@@ -864,17 +935,54 @@ lfa_status_t lfa_svd_backward(lfa_plan_t p, const float* const* dsigma, const fl
   for (int l = 0; l < p->nlayers; ++l)
     if (!dsigma[l] || !U[l] || !V[l] || !dw[l]) return LFA_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  for (int l = 0; l < p->nlayers; ++l) {
-    const LayerArgs& La = p->args[l];
-    const int64_t CC = (int64_t)La.c_out * La.c_in;
-    const int64_t g_cap = p->g_cap_bytes / (CC * 8);
-    int nk = 0;
-    LFA_CUDA_TRY(launch_backward(La, dsigma[l], p->half_output, reinterpret_cast<const float2*>(U[l]),
-                                 reinterpret_cast<const float2*>(V[l]), p->g_ws, g_cap, p->partial_ws,
-                                 p->bw_chunks[l], dw[l], s, &nk, p->counters->bw_queue, p->counters, p->sms));
+  // every layer's backward in turn (they share the G and partial-sum workspaces)
+  auto enqueue = [&](cudaStream_t st, int64_t* kernels) -> lfa_status_t {
+    for (int l = 0; l < p->nlayers; ++l) {
+      const LayerArgs& La = p->args[l];
+      const int64_t CC = (int64_t)La.c_out * La.c_in;
+      const int64_t g_cap = p->g_cap_bytes / (CC * 8);
+      int nk = 0;
+      LFA_CUDA_TRY(launch_backward(La, dsigma[l], p->half_output, reinterpret_cast<const float2*>(U[l]),
+                                   reinterpret_cast<const float2*>(V[l]), p->g_ws, g_cap, p->partial_ws,
+                                   p->bw_chunks[l], dw[l], st, &nk, p->counters->bw_queue, p->counters, p->sms));
+      *kernels += nk;
+    }
+    return LFA_OK;
+  };
+  if (!p->use_graph) {
+    int64_t nk = 0;
+    const lfa_status_t st = enqueue(s, &nk);
     g_launches += nk;
+    return st;
   }
-  return LFA_OK;
+  // graph path: capture once per distinct set of buffers, then replay
+  std::vector<const void*> key;
+  key.reserve(4 * p->nlayers);
+  for (int l = 0; l < p->nlayers; ++l) {
+    key.push_back(dsigma[l]);
+    key.push_back(U[l]);
+    key.push_back(V[l]);
+    key.push_back(dw[l]);
+  }
+  if (p->bw_exec == nullptr || key != p->bw_key) {
+    if (p->bw_exec) { cudaGraphExecDestroy(p->bw_exec); p->bw_exec = nullptr; }
+    if (p->bw_graph) { cudaGraphDestroy(p->bw_graph); p->bw_graph = nullptr; }
+    LFA_CUDA_TRY(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int64_t nk = 0;
+    const lfa_status_t st = enqueue(p->cap_stream, &nk);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(p->cap_stream, &g);
+    if (st != LFA_OK) { if (g) cudaGraphDestroy(g); return st; }
+    if (e != cudaSuccess) return from_cuda(e);
+    p->bw_graph = g;
+    e = cudaGraphInstantiate(&p->bw_exec, g, 0);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); p->bw_graph = nullptr; p->bw_exec = nullptr; return from_cuda(e); }
+    p->bw_key = key;
+    p->bw_kernels = nk;
+  }
+  const lfa_status_t st = from_cuda(cudaGraphLaunch(p->bw_exec, s));
+  if (st == LFA_OK) g_launches += p->bw_kernels;
+  return st;
 }
 
 lfa_status_t lfa_spectral_edit(lfa_plan_t p, const float* const* sigma, const float* const* U,
