@@ -162,6 +162,8 @@ typedef struct lfa_info {
   float tol;
   int64_t tc_grams;         /* blocked tensor-core route: block-pair Gram matrices formed */
   int64_t tc_updates;       /* blocked tensor-core route: block-pair rotations applied to X (and W) */
+  int32_t debug_error;      /* library built with LFA_DEBUG: the site of the first failed index
+                               check (include/lfa_debug.h), 0 if none; always 0 otherwise */
 } lfa_info_t;
 
 /* Creates a plan for nlayers layers (Algorithm 1's "SVD with LFA(A, m, n)",

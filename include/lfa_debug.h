@@ -90,6 +90,19 @@ void lfa_debug_set_bj_ctas_per_sm(int32_t n);
  * Returns an lfa_status_t. */
 int32_t lfa_debug_bj_occupancy(int32_t vectors, int32_t* out);
 
+/* Site ids of the index checks of the debug build (liblfa_debug.so, built with -DLFA_DEBUG; the
+ * release library has none): lfa_info_t.debug_error holds the first failed one, and lfa_get_info
+ * then returns LFA_ERR_CUDA. The guarded access is skipped, never trapped.
+ *   1  element-wise Jacobi, cluster variants: output rank of a column, or symbol index
+ *   2  element-wise Jacobi, single-CTA variants: output rank of a column (staging mailbox)
+ *   4  rotation-log finalize: output rank or symbol index
+ *   5  blocked route: work item -> (layer, symbol)
+ *   6  blocked route: output rank of a column
+ *   7  lifting: half-grid position of a frequency
+ *   8  CUDA-core backward G: symbol index
+ *   9  tensor-core backward G: work item -> symbol
+ *   10 tensor-core backward tap projection: part or frequency range */
+
 #ifdef __cplusplus
 }
 #endif

@@ -5,7 +5,12 @@ Every translation unit under ``csrc/`` is compiled by nvcc in parallel (one
 ``paper_2506_05617_gb300/lib/liblfa.so`` against the shared CUDA runtime, so the
 library shares the runtime (and streams) of the PyTorch process that loads it.
 
-    python -m paper_2506_05617_gb300.build [--force]
+    python -m paper_2506_05617_gb300.build [--force] [--debug]
+
+With ``--debug`` (``build(debug=True)``) the same sources are compiled with ``-DLFA_DEBUG`` into
+``lib/liblfa_debug.so``: kernel index checks that record a site id in the plan's debug word
+(reported by ``lfa_get_info``) instead of making the access. The binding loads that library when
+the environment has ``LFA_DEBUG=1``.
 """
 from __future__ import annotations
 
@@ -21,6 +26,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "liblfa.so")
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(LIBDIR, "liblfa_debug.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -52,20 +59,22 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    bdir, lib_path = (BUILD_DEBUG, LIB_DEBUG) if debug else (BUILD, LIB)
+    flags = FLAGS + (["-DLFA_DEBUG"] if debug else [])
+    os.makedirs(bdir, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     nv = nvcc()
     hs = headers()
     jobs = []
     for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
         if force or _stale(obj, [src] + hs):
             jobs.append((src, obj))
 
     def compile_one(job):
         src, obj = job
-        cmd = [nv] + ARCH + FLAGS + ["-c", src, "-o", obj]
+        cmd = [nv] + ARCH + flags + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {os.path.basename(src)}:\n{r.stderr}")
@@ -76,20 +85,21 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             list(ex.map(compile_one, jobs))
-    objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in sources()]
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + ".tmp"
+    objs = [os.path.join(bdir, os.path.basename(s)[:-3] + ".o") for s in sources()]
+    if force or jobs or _stale(lib_path, objs):
+        tmp = lib_path + ".tmp"
         cmd = [nv] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + ["-lcufft"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("--force", action="store_true")
     ap.add_argument("-v", "--verbose", action="store_true")
+    ap.add_argument("--debug", action="store_true", help="the index-checked library liblfa_debug.so")
     a = ap.parse_args()
-    print(build(force=a.force, verbose=a.verbose))
+    print(build(force=a.force, verbose=a.verbose, debug=a.debug))

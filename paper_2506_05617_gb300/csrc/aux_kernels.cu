@@ -103,7 +103,8 @@ __global__ void __launch_bounds__(256) expand_kernel(LayerArgs La, const float2*
     const int fc = ((n - (int)j) % n) * m + (m - (int)my_l) % m;
     my_conj = fc < f;
     my_pa = La.tw_n[(j * (unsigned)x1) % (unsigned)n];
-    my_src = ((int64_t)half_position(n, m, f) * C + src_row) * r + sv;
+    const int64_t hp = half_position(n, m, f);
+    my_src = LFA_DOK(La.dbg, hp >= 0 && hp < La.F_h, 7) ? (hp * C + src_row) * r + sv : 0;   // lifting: position
     float2 u0 = __ldg(Src + my_src);                   // the entry for u_w = 0 (all when sw = 1)
     if (my_conj) u0.y = -u0.y;
     my_a = make_float2((u0.x * my_pa.x - u0.y * my_pa.y) * scale, (u0.x * my_pa.y + u0.y * my_pa.x) * scale);
@@ -326,6 +327,7 @@ __global__ void __launch_bounds__(256) backward_g_kernel(LayerArgs La, const flo
   __shared__ float2 Vs[32][33];
   __shared__ float gs[32];
   const int h = h_begin + blockIdx.z;
+  if (!LFA_DOK(La.dbg, h < La.F_h, 8)) return;           // backward G: symbol
   const int o0 = blockIdx.y * 32, i0 = blockIdx.x * 32;
   const int r = La.r, co = La.c_out, ci = La.c_in;
   const int f = La.half[h];

@@ -98,6 +98,7 @@ bw_g_tc_kernel(LayerArgs La, const float* dsigma, int half_output, const float2*
     const int it = ms->item;
     if (it >= total) break;
     const int h = h_begin + it / (to * ti);
+    if (!LFA_DOK(La.dbg, h < h_end && h < La.F_h, 9)) continue;   // tensor-core G: item -> symbol
     const int tile = it % (to * ti);
     const int o0 = (tile / ti) * TM, i0 = (tile % ti) * TN;
     const int f = La.half[h];
@@ -230,6 +231,7 @@ __global__ void __launch_bounds__(256) bw_dw_tc_kernel(LayerArgs La, const float
   const int kk = La.kh * La.kw;
   const int e0 = (blockIdx.x * blockDim.x + threadIdx.x) * E;
   const int p = blockIdx.y;
+  if (!LFA_DOK(La.dbg, p < nparts && h_end <= La.F_h, 10)) return;   // tap projection: part, range
   const int nh = h_end - h_begin;
   const int len = (nh + nparts - 1) / nparts;
   const int p0 = h_begin + p * len;

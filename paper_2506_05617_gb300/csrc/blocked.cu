@@ -611,6 +611,7 @@ __global__ void __maxnreg__(bj::MAX_REGS) bj_kernel(const __grid_constant__ BJLa
     while (lk + 1 < A.nlayers && item >= A.L[lk + 1].item_begin) ++lk;
     const LayerArgs& La = A.L[lk];
     const int h = item - La.item_begin;                 // half-grid symbol of that layer
+    if (!LFA_DOK(La.dbg, h >= 0 && h < La.F_h, 5)) continue;   // blocked route: item -> layer, symbol
     const int M = La.M, N = La.N;
     if (threadIdx.x == 0) c_sym = clock64();
     const int f = La.half[h];
@@ -740,7 +741,7 @@ __global__ void __maxnreg__(bj::MAX_REGS) bj_kernel(const __grid_constant__ BJLa
             rank += (v > sc) || (v == sc && q2 < c);
           }
           float* srow = La.sigma + (size_t)(A.half_output ? h : f) * La.r;
-          srow[rank] = sc;
+          if (LFA_DOK(La.dbg, rank >= 0 && rank < N, 6)) srow[rank] = sc;   // blocked route: rank
           if (!A.half_output) {
             const int fc = ((La.n - jj) % La.n) * La.m + (La.m - ll) % La.m;
             if (fc != f) La.sigma[(size_t)fc * La.r + rank] = sc;

@@ -701,6 +701,7 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
 #pragma unroll
           for (int kc = 0; kc < NCOL; ++kc) {
             if (cid[kc] >= N) continue;
+            if (!LFA_DOK(La.dbg, rk[kc] >= 0 && rk[kc] < N && h < La.F_h, 1)) continue;   // cluster output: rank
             const Planes<C>& X = col(kc);
 #pragma unroll
             for (int i = 0; i < MR; ++i) {
@@ -726,6 +727,7 @@ jacobi_kernel(const __grid_constant__ JacobiLaunch P) {
 #pragma unroll
         for (int kc = 0; kc < NCOL; ++kc) {
           if (cid[kc] >= N) continue;
+          if (!LFA_DOK(La.dbg, rk[kc] >= 0 && rk[kc] < N, 2)) continue;   // staged output: rank
           const Planes<C>& X = col(kc);
           float2* d = mbox + (size_t)rk[kc] * CSx;
 #pragma unroll

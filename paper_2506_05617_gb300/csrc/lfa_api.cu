@@ -778,6 +778,7 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
     La.half = reinterpret_cast<const int32_t*>(base + off_half[l]);
     La.tw_n = reinterpret_cast<const float2*>(base + off_twn[l]);
     La.tw_m = reinterpret_cast<const float2*>(base + off_twm[l]);
+    La.dbg = &p->counters->debug_error;
     e = cudaMemcpy(base + off_half[l], p->half_host[l].data(), (size_t)La.F_h * 4, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) break;
     twiddles(La.n);
@@ -1068,6 +1069,8 @@ lfa_status_t lfa_get_info(lfa_plan_t p, lfa_info_t* info) {
   info->tol = p->tol_opt > 0.f ? p->tol_opt : default_tol(p->args[0].M, p->args[0].wide != 0);
   info->tc_grams = (int64_t)c.tc_grams;
   info->tc_updates = (int64_t)c.tc_updates;
+  info->debug_error = (int32_t)c.debug_error;
+  if (c.debug_error) return LFA_ERR_CUDA;   // debug build: a kernel index left its range
   if (c.timeouts) return LFA_ERR_TIMEOUT;
   if (c.nonfinite) return LFA_ERR_NONFINITE;
   if (c.unconverged) return LFA_ERR_NOT_CONVERGED;

@@ -24,6 +24,7 @@ struct Counters {
   unsigned long long bj_cycles[6];
   unsigned int queue[16];        // work-queue tickets, one per launch of a call
   unsigned int bw_queue[2];      // work-queue tickets of the tensor-core backward's launches
+  unsigned int debug_error;      // debug build: the site id of the first failed index check
 };
 
 // One layer as a kernel sees it. The Jacobi problem of a symbol is X (M x N), with
@@ -45,7 +46,22 @@ struct LayerArgs {
   // columns (i, u_h, u_w) -> i sh sw + u_h sw + u_w: the polyphase components of the fine input.
   int32_t c_w, sh, sw;
   float tol2;               // squared Jacobi threshold
+  unsigned int* dbg;        // debug build: the word a failed index check writes its site id to
 };
+
+// Index checks of the debug build (compiled with -DLFA_DEBUG, library liblfa_debug.so): a failed
+// check records its site id in the plan's debug word (the first failure wins) and the guarded
+// access is skipped; the release build compiles them out. Nothing traps. Site ids are listed in
+// include/lfa_debug.h.
+#ifdef LFA_DEBUG
+__device__ __forceinline__ bool debug_check(unsigned int* word, bool ok, unsigned int id) {
+  if (!ok && word) atomicCAS(word, 0u, id);
+  return ok;
+}
+#define LFA_DOK(word, cond, id) ::lfa::debug_check((word), (cond), (id))
+#else
+#define LFA_DOK(word, cond, id) true
+#endif
 
 // floor(a / s) for s >= 1: the coarse offset q of a tap y = s q + u, 0 <= u < s.
 __host__ __device__ __forceinline__ int floor_div(int a, int s) { return a >= 0 ? a / s : -((s - 1 - a) / s); }

@@ -144,6 +144,7 @@ extern "C" lfa_status_t lfa_svd_backward_noalloc(const lfa_layer_desc_t* layer, 
   La.U = nullptr;
   La.V = nullptr;
   La.symbols = nullptr;
+  La.dbg = nullptr;
   const int s_self = (1 + (d.n % 2 == 0)) * (1 + (d.m % 2 == 0));
   La.F_h = (int)(((int64_t)d.n * d.m + s_self) / 2);
   La.item_begin = 0;

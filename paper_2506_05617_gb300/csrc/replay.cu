@@ -145,6 +145,7 @@ __global__ void __launch_bounds__(512) finalize_kernel(const __grid_constant__ R
   const int jj = f / La.m, ll = f - jj * La.m;
   const int r = La.r;
   float* row = La.sigma + (size_t)(R.half_output ? h : f) * r;
+  if (!LFA_DOK(La.dbg, rank >= 0 && rank < N && h < La.F_h, 4)) return;   // finalize: rank, symbol
   row[rank] = sc;
   if (!R.half_output) {
     const int fc = ((La.n - jj) % La.n) * La.m + (La.m - ll) % La.m;

@@ -17,7 +17,8 @@ from ctypes import POINTER, c_char_p, c_float, c_int32, c_int64, c_uint16, c_uin
 from typing import Iterable, List, Optional, Sequence
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "lib", "liblfa.so")
+# LFA_DEBUG=1 loads the index-checked build (build.py --debug)
+LIB_PATH = os.path.join(HERE, "lib", "liblfa_debug.so" if os.environ.get("LFA_DEBUG") == "1" else "liblfa.so")
 
 # flags (include/lfa.h)
 LFA_VALUES = 0x1
@@ -85,7 +86,7 @@ class Info(ctypes.Structure):
     _fields_ = [("symbols", c_int64), ("singular_values", c_int64), ("unconverged", c_int64),
                 ("nonfinite", c_int64), ("sweeps", c_int64), ("rotations", c_int64),
                 ("plan_device_bytes", c_int64), ("nlayers", c_int32), ("max_sweeps", c_int32),
-                ("tol", c_float), ("tc_grams", c_int64), ("tc_updates", c_int64)]
+                ("tol", c_float), ("tc_grams", c_int64), ("tc_updates", c_int64), ("debug_error", c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
