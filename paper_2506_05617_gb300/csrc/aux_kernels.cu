@@ -42,8 +42,57 @@ __global__ void __launch_bounds__(256) symbols_kernel(LayerArgs La, float2* out)
   }
 }
 
+// Stride-1 layers with at most KK taps: one thread per symbol entry (o, i) keeps the entry's taps in
+// registers and writes the entry for a block of SB frequencies, whose k_h x k_w phase grids are
+// staged in shared memory; the weights are then read once per SB symbols instead of once per
+// symbol, and each frequency's row of entries is written coalesced (consecutive i per warp).
+constexpr int kSymbolsBlock = 16;
+template <int KK>
+__global__ void __launch_bounds__(256) symbols_tiled_kernel(LayerArgs La, float2* out) {
+  __shared__ float2 phs[kSymbolsBlock][KK];
+  const int kk = La.kh * La.kw;
+  const int h0 = blockIdx.y * kSymbolsBlock;
+  const int nh = min(kSymbolsBlock, La.F_h - h0);
+  for (int x = threadIdx.x; x < nh * kk; x += blockDim.x) {
+    const int hh = x / kk, t = x - hh * kk;
+    const int f = La.half[h0 + hh];
+    const int j = f / La.m, l = f - j * La.m;
+    phs[hh][t] = tap_phase(La, j, l, t / La.kw, t % La.kw);
+  }
+  __syncthreads();
+  const int CC = La.c_out * La.c_in;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= CC) return;
+  float wt[KK];
+  const float* wp = La.w + (size_t)e * kk;   // stride 1: entry (o, i) is weight row o * c_in + i
+#pragma unroll
+  for (int t = 0; t < KK; ++t) wt[t] = t < kk ? __ldg(wp + t) : 0.f;
+  for (int hh = 0; hh < nh; ++hh) {
+    float re = 0.f, im = 0.f;
+#pragma unroll
+    for (int t = 0; t < KK; ++t) {
+      if (t < kk) {
+        const float2 p = phs[hh][t];
+        re = fmaf(wt[t], p.x, re);
+        im = fmaf(wt[t], p.y, im);
+      }
+    }
+    out[(size_t)(h0 + hh) * CC + e] = make_float2(re, im);
+  }
+}
+
 cudaError_t launch_symbols(const LayerArgs& La, float2* out, cudaStream_t s) {
   if (La.F_h <= 0) return cudaSuccess;
+  const int kk = La.kh * La.kw;
+  if (La.sh == 1 && La.sw == 1 && kk <= 25) {
+    const int CC = La.c_out * La.c_in;
+    dim3 grid((unsigned)((CC + 255) / 256), (unsigned)((La.F_h + kSymbolsBlock - 1) / kSymbolsBlock));
+    if (grid.y > 65535) return cudaErrorInvalidValue;
+    if (kk <= 1) symbols_tiled_kernel<1><<<grid, 256, 0, s>>>(La, out);
+    else if (kk <= 9) symbols_tiled_kernel<9><<<grid, 256, 0, s>>>(La, out);
+    else symbols_tiled_kernel<25><<<grid, 256, 0, s>>>(La, out);
+    return cudaGetLastError();
+  }
   symbols_kernel<<<La.F_h, 256, 0, s>>>(La, out);
   return cudaGetLastError();
 }
@@ -111,6 +160,41 @@ __global__ void __launch_bounds__(256) expand_kernel(LayerArgs La, const float2*
   }
   float2* out = dst + (size_t)(q0 - first) * C * n * m + row_off;
   const size_t vec_stride = (size_t)C * n * m;
+  if (sw == 1 && (m & 1) == 0 && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+    // 16-byte stores: a row is P = m/2 float4s; lane gl of a group of G lanes (the power of two
+    // >= P, at most 32) writes float4s gl, gl + G, ... of one vector's row, and the warp's 32 / G
+    // groups write the rows of as many consecutive vectors with one store instruction (two 32-entry
+    // rows per instruction at m = 32). The column phase start and step are recomputed only when
+    // the group's frequency changes.
+    const int P = m >> 1;
+    int G = 1;
+    while (G < P && G < 32) G <<= 1;
+    const int V = 32 / G, sub = lane / G, gl = lane - sub * G;
+    unsigned lprev = 0xffffffffu, idx0 = 0, step = 0;
+    for (int i0 = 0; i0 < nv; i0 += V) {
+      const int iv = i0 + sub;
+      const bool act = iv < nv;
+      const int src_lane = iv & 31;
+      const float2 a0 = make_float2(__shfl_sync(0xffffffffu, my_a.x, src_lane), __shfl_sync(0xffffffffu, my_a.y, src_lane));
+      const unsigned l = __shfl_sync(0xffffffffu, my_l, src_lane);
+      if (l != lprev) {
+        lprev = l;
+        idx0 = (l * (unsigned)(2 * gl)) % (unsigned)m;   // (l x2) mod m for x2 = 2 gl
+        step = (l * (unsigned)(2 * G)) % (unsigned)m;
+      }
+      float4* o4 = reinterpret_cast<float4*>(out + (size_t)iv * vec_stride);
+      unsigned idx = idx0;
+      for (int q = gl; q < P; q += G) {
+        unsigned i1 = idx + l;
+        if (i1 >= (unsigned)m) i1 -= (unsigned)m;
+        const float2 v0 = cmul(a0, La.tw_m[idx]), v1 = cmul(a0, La.tw_m[i1]);
+        if (act) o4[q] = make_float4(v0.x, v0.y, v1.x, v1.y);
+        idx += step;
+        if (idx >= (unsigned)m) idx -= (unsigned)m;
+      }
+    }
+    return;
+  }
   // consecutive vectors mostly share the frequency: the column phase start and step are
   // recomputed only when l changes (l is warp-uniform, so is the branch)
   unsigned lprev = 0xffffffffu, idx0 = 0, step = 0;
