@@ -318,13 +318,18 @@ def run_lfa(args, rank: int, world: int, local_rank: int):
     from paper_2506_05617_gb300 import lfa as C
     from paper_2506_05617_gb300.torch_api import LfaPlan
 
-    B.build()
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
+    # one process per node compiles (the others would race on the same build folder), then all load
+    if local_rank == 0:
+        B.build()
+    if dist is not None:
+        dist.barrier()
+    B.build()
 
     layers = W.layers(args.workload)
     vectors = not (args.values_only or args.workload in VALUES_ONLY)

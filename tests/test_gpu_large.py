@@ -158,26 +158,83 @@ def test_conv512_values_sampled():
 
 
 def test_conv512_n64_values_and_vectors_sampled():
-    """512->512 3x3 on 64x64 (2050 half-grid symbols): values and vectors, checked on samples."""
+    """512->512 3x3 on 64x64 (2050 half-grid symbols, the benchmark layer): values on 24 random
+    frequencies plus the four self-conjugate ones and the GPU's argmax frequency (whose oracle
+    value pins the layer's sigma_max), Parseval over all 2.1M values; vectors (residual
+    A v - sigma u, orthonormality) on 8 half-grid frequencies including f = 0 and the argmax's
+    representative."""
     lay = W.layers("conv512_k3_n64")[0]
     w = W.weights(lay)
-    plan = LfaPlan([(lay.c_out, lay.c_in, lay.kh, lay.kw, lay.n, lay.m)], vectors=True)
+    n, m = lay.n, lay.m
+    plan = LfaPlan([(lay.c_out, lay.c_in, lay.kh, lay.kw, n, m)], vectors=True)
     sig, U, V = plan.svd([torch.from_numpy(w).cuda()])
     torch.cuda.synchronize()
     st, info = plan.info()
     assert st == C.LFA_OK, info
     s = sig[0].cpu().numpy()
-    sampled_sigma_check(w, lay, s, 4, seed=8)
-    half = O.half_grid(lay.n, lay.m)
-    pick = np.random.default_rng(1).choice(len(half), 3, replace=False)
-    S = O.symbols(w, lay.n, lay.m, freqs=half[pick])
+    fmax = int(np.argmax(s) // lay.r)
+    selfc = [0, (n // 2) * m, m // 2, (n // 2) * m + m // 2]
+    rnd = np.random.default_rng(8).choice(lay.F, 24, replace=False)
+    fr = np.unique(np.concatenate([rnd, selfc, [fmax]]))
+    s_ref = O.lfa_svd(w, n, m, compute_uv=False, freqs=fr)
+    smax = float(s.max())
+    k = int(np.searchsorted(fr, fmax))
+    assert abs(float(s_ref[k].max()) - smax) <= SIG_TOL * smax          # the layer's sigma_max
+    assert float(s_ref.max()) <= smax * (1 + SIG_TOL)
+    assert np.max(np.abs(s[fr].astype(np.float64) - s_ref)) <= SIG_TOL * smax
+    np.testing.assert_allclose(np.sum(s.astype(np.float64) ** 2), n * m * np.sum(w.astype(np.float64) ** 2),
+                               rtol=2e-5)
+    half = O.half_grid(n, m)
+    fcm = ((-(fmax // m)) % n) * m + (-(fmax % m)) % m
+    hmax = int(np.searchsorted(half, min(fmax, fcm)))
+    pick = np.unique(np.concatenate([[0, hmax], np.random.default_rng(1).choice(len(half), 6, replace=False)]))
+    S = O.symbols(w, n, m, freqs=half[pick])
     Uu = U[0][torch.from_numpy(pick).cuda()].cpu().numpy().astype(np.complex128)
     Vv = V[0][torch.from_numpy(pick).cuda()].cpu().numpy().astype(np.complex128)
     ss = s[half[pick]].astype(np.float64)
     res = np.einsum("hoi,his->hos", S, Vv) - Uu * ss[:, None, :]
-    assert np.max(np.linalg.norm(res, axis=1)) <= VEC_TOL * s.max()
+    assert np.max(np.linalg.norm(res, axis=1)) <= VEC_TOL * smax
     for X in (Uu, Vv):
         assert np.max(np.abs(np.einsum("hos,hot->hst", np.conj(X), X) - np.eye(lay.r))) <= VEC_TOL
+    plan.close()
+
+
+def test_conv512_n64_backward_on_sampled_frequencies():
+    """The benchmark layer's backward (tensor-core G over 17 blocks of the 2050 symbols) with the
+    upstream gradient kept on 6 sampled frequencies and their conjugates: equal to the oracle's
+    backward over those frequencies with the GPU's own U, V (1e-5 relative)."""
+    lay = W.layers("conv512_k3_n64")[0]
+    w = W.weights(lay)
+    n, m, r = lay.n, lay.m, lay.r
+    plan = LfaPlan([(lay.c_out, lay.c_in, lay.kh, lay.kw, n, m)], vectors=True)
+    sig, U, V = plan.svd([torch.from_numpy(w).cuda()])
+    half = O.half_grid(n, m)
+    pick = np.array([0, 1, 700, 1500, 2048, 2049])           # first, middle and last G blocks
+    f = half[pick]
+    fc = ((-(f // m)) % n) * m + (-(f % m)) % m
+    keep = np.zeros(n * m, bool)
+    keep[f] = True
+    keep[fc] = True
+    g = W.upstream_gradient((n * m, r), seed=17) * keep[:, None]
+    dw = plan.backward([torch.from_numpy(g.astype(np.float32)).cuda()], U, V)[0].cpu().numpy().astype(np.float64)
+    torch.cuda.synchronize()
+    st, info = plan.info()
+    assert st == C.LFA_OK, info
+    full_f = np.flatnonzero(keep)
+    hpos = {int(h): q for q, h in enumerate(half)}
+    Ug = U[0][torch.from_numpy(pick).cuda()].cpu().numpy().astype(np.complex128)
+    Vg = V[0][torch.from_numpy(pick).cuda()].cpu().numpy().astype(np.complex128)
+    loc = {int(h): q for q, h in enumerate(f)}
+    Uf = np.empty((len(full_f), lay.c_out, r), np.complex128)
+    Vf = np.empty((len(full_f), lay.c_in, r), np.complex128)
+    for q, ff in enumerate(full_f):
+        fcc = ((-(ff // m)) % n) * m + (-(ff % m)) % m
+        if ff in loc:
+            Uf[q], Vf[q] = Ug[loc[ff]], Vg[loc[ff]]
+        else:
+            Uf[q], Vf[q] = np.conj(Ug[loc[fcc]]), np.conj(Vg[loc[fcc]])
+    ref = O.lfa_backward(w, n, m, g[full_f], Uf, Vf, freqs=full_f)
+    assert np.linalg.norm(dw - ref) / np.linalg.norm(ref) <= 1e-5
     plan.close()
 
 
