@@ -77,9 +77,10 @@ def test_blocked_route_is_the_default_for_wide_channel_layers():
 
 def test_blocked_layers_share_a_launch():
     """Layers whose symbols pad to the same size go through one blocked launch (items of several
-    layers in one queue): two 256 x 256 layers and a 300 x 256 one (a launch of its own) on 14 x 14,
-    values and vectors, checked against the oracle on sampled half-grid frequencies of each layer."""
-    specs = [(256, 256, 3, 3, 14, 14), (256, 256, 3, 3, 14, 14), (300, 256, 3, 3, 14, 14)]
+    layers in one queue): two 256 x 256 layers, and a 300 x 256 and a 384 x 256 one (both padded to
+    384 rows: a second launch shared by layers of different row counts) on 14 x 14, values and
+    vectors, checked against the oracle on sampled half-grid frequencies of each layer."""
+    specs = [(256, 256, 3, 3, 14, 14), (256, 256, 3, 3, 14, 14), (300, 256, 3, 3, 14, 14), (384, 256, 3, 3, 14, 14)]
     ws = [rand_w(co, ci, kh, kw, seed=90 + i) for i, (co, ci, kh, kw, n, m) in enumerate(specs)]
     plan = LfaPlan(specs, vectors=True)
     assert all(mt["variant"] == C.LFA_VARIANT_BLOCKED for mt in plan.meta)

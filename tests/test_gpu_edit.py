@@ -110,3 +110,33 @@ def test_pseudo_inverse_of_a_scaled_identity_is_exact_and_strided_layers_are_ref
         plan.spectral_edit(sig, U, V, "pinv", 0.0)
     assert ei.value.status == C.LFA_ERR_UNSUPPORTED
     plan.close()
+
+
+@pytest.mark.parametrize("mode", ["clip", "pinv"])
+def test_spectral_edit_on_the_tensor_core_route(mode):
+    """A 128 -> 160 layer (both sides >= 128 channels): the edit's projection runs through the
+    tensor-core G product (for the pseudo-inverse on the transposed layer, U and V exchanged)."""
+    from paper_2506_05617_gb300 import lfa as C
+    c_out, c_in, kh, kw, n, m = 160, 128, 3, 3, 2, 3
+    assert C.lfa_debug_backward_route(c_out, c_in, kh, kw) == 2
+    assert C.lfa_debug_backward_route(c_in, c_out, kh, kw) == 2
+    w = rand_w(c_out, c_in, kh, kw, seed=53)
+    s_ref = O.lfa_svd(w, n, m, compute_uv=False)
+    plan = LfaPlan([(c_out, c_in, kh, kw, n, m)], vectors=True)
+    sig, U, V = plan.svd([torch.from_numpy(w).cuda()])
+    if mode == "clip":
+        a = 0.7 * float(s_ref.max())
+        got = plan.spectral_edit(sig, U, V, "clip", a)[0].cpu().numpy()
+        ref = O.spectral_edit(w, n, m, "clip", a)
+        assert np.linalg.norm(got - ref) <= 1e-4 * np.linalg.norm(ref)
+    else:
+        # threshold in the widest gap of the spectrum's lower part (fp32 and fp64 agree on each side);
+        # 1/sigma amplifies the fp32 error of small values: tolerance 1e-4 * sigma_max / a
+        v = np.sort(s_ref.ravel())
+        lo, hi = len(v) // 5, 3 * len(v) // 5
+        k = lo + int(np.argmax(np.diff(v[lo:hi])))
+        a = 0.5 * (v[k] + v[k + 1])
+        got = plan.spectral_edit(sig, U, V, "pinv", a)[0].cpu().numpy()
+        ref = O.pinv_projection(w, n, m, a)
+        assert np.linalg.norm(got - ref) <= 1e-4 * (float(v[-1]) / a) * np.linalg.norm(ref)
+    plan.close()
