@@ -817,7 +817,7 @@ static cudaError_t bj_prepare_t(int sms, int* max_ctas) {
 // to 512 rows.
 bool bj_supported(int M, int N) { return N >= 128 && M <= 512 && N <= 512; }
 
-// The built-in choice takes the blocked route for tall or square symbols of 256-512 columns when a
+// The built-in choice takes the blocked route for tall or square symbols of 129-512 columns when a
 // layer has enough symbols to fill the GPU. One symbol per CTA takes ~20 ms at 256 columns, ~55 ms
 // at 384 and ~125 ms at 512 (alone on an SM, values), while the element-wise cluster kernels spread
 // a symbol over up to 16 SMs at ~0.24, ~1.9 and ~1.9 ms of throughput per symbol (GB300): the

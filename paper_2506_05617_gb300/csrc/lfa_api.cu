@@ -624,10 +624,11 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
         v = rq;
       }
     }
-    // built-in choice: the blocked tensor-core route for tall or square symbols of 256 columns and
-    // more, in layers with enough symbols to fill the GPU (bj_min_symbols); measured faster than the
-    // element-wise kernels there, with and without vectors
-    if (v < 0 && !blocked && !p->plain && !La.wide && La.N >= 256 && bj_supported(La.M, La.N) &&
+    // built-in choice: the blocked tensor-core route for tall or square symbols of more than 128
+    // columns, in layers with enough symbols to fill the GPU (bj_min_symbols); measured faster than
+    // the element-wise kernels there, with and without vectors (at 192 columns, 514 symbols: 46 ms
+    // against 167 ms with vectors). 128 columns: the autotuner cache decides
+    if (v < 0 && !blocked && !p->plain && !La.wide && La.N > 128 && bj_supported(La.M, La.N) &&
         La.F_h >= bj_min_symbols(La.N))
       blocked = true;
     if (blocked) {

@@ -66,7 +66,7 @@ def test_blocked_route_is_the_default_for_wide_channel_layers():
     cache = os.path.join(os.path.dirname(os.path.dirname(__file__)), "paper_2506_05617_gb300", "tune_gb300.txt")
     for spec, vec, blocked in [((512, 512, 3, 3, 12, 12), True, True), ((512, 512, 3, 3, 12, 12), False, True),
                                ((256, 256, 3, 3, 14, 14), True, True), ((300, 256, 3, 3, 14, 14), True, True),
-                               ((384, 384, 3, 3, 8, 8), False, True),
+                               ((384, 384, 3, 3, 8, 8), False, True), ((192, 192, 3, 3, 14, 14), True, True),
                                ((512, 512, 3, 3, 4, 4), False, False), ((512, 512, 3, 3, 7, 7), False, False),
                                ((128, 128, 3, 3, 4, 4), True, False), ((256, 512, 3, 3, 14, 14), True, False)]:
         for tc in (None, cache):
