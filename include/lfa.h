@@ -142,7 +142,9 @@ typedef struct lfa_options {
  * (128 <= N <= 512 columns, M <= 512 rows; not with LFA_PLAIN): one-sided Jacobi over blocks of
  * 32 columns whose Gram matrices and block rotations run on the tcgen05 tensor cores with TF32
  * operands split in three (hi*hi + hi*lo + lo*hi, FP32 accumulation), one CTA per symbol. It is
- * also the built-in choice for tall or square symbols (c_out >= c_in) of 256 columns or more.
+ * also the built-in choice for tall or square symbols (c_out >= c_in) of more than 128 columns in
+ * layers with enough half-grid symbols to fill the GPU (84 up to 256 columns, 30 up to 384, 68 up
+ * to 512; fewer go to the element-wise cluster kernels).
  * lfa_layer_query reports it as this value. */
 #define LFA_VARIANT_BLOCKED 0x20000
 

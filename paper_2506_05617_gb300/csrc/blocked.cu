@@ -5,11 +5,12 @@
 // Method (Hestenes' one-sided Jacobi, applied to blocks of columns): X = A_k (or A_k^* for wide
 // symbols) has its N columns split into nb blocks of 32. A sweep visits every pair of blocks
 // (I, J) once, in the circle-method order over blocks (nb / 2 disjoint pairs per round). For a
-// pair, Y = [X_I, X_J] (M x 64) gives the Hermitian Gram matrix H = Y^* Y (64 x 64); one cyclic
-// two-sided Jacobi sweep over H (63 rounds of 32 disjoint 2x2 rotations, each rotation chosen
-// only when |h_pq| > tol sqrt(h_pp h_qq), the one-sided test) accumulates the unitary Q, and Y
-// and the matching columns of W (the accumulated right factor, W = I initially) are replaced
-// by Y Q and W Q. Because X = A W holds for any right factor, x_c = A w_c stays exact to
+// pair, Y = [X_I, X_J] (M x 64) gives the Hermitian Gram matrix H = Y^* Y (64 x 64); one
+// two-sided Jacobi sweep over H (rounds of 32 disjoint 2x2 rotations, each rotation chosen only
+// when |h_pq| > tol sqrt(h_pp h_qq), the one-sided test: all 63 rounds of the circle method in
+// the first round of an outer sweep, the 32 rounds of the pairs across the two blocks otherwise)
+// accumulates the unitary Q, and Y and the matching columns of W (the accumulated right factor,
+// W = I initially) are replaced by Y Q and W Q. Because X = A W holds for any right factor, x_c = A w_c stays exact to
 // rounding; sweeps repeat until no pair of a sweep rotates. Then sigma_c = |x_c| / |w_c|, the X
 // columns normalised give U (V for wide symbols) and the W columns V (U).
 //
@@ -17,11 +18,11 @@
 //  * The two dense contractions of a block pair run on the tensor cores with TF32 operands
 //    split 3 ways (hi*hi + hi*lo + lo*hi, FP32 accumulation in tensor memory), which keeps
 //    FP32 accuracy: the Gram in real form, Z^T Z with Z = [Re Y, Im Y] (M x 128, one
-//    128 x 128 MMA tile, K = M), and the update Y Q in real form, [Re Y, Im Y] against Re Q
-//    and Im Q (M = 128-row tiles, N = 64, K = 64, the negation of Im Q taken by the
-//    instruction descriptor). Operands are staged by the CTA's threads (which split fp32 into
-//    TF32 pairs) in K-major core-matrix layout; one thread issues the MMAs and an mbarrier
-//    reports their completion.
+//    128 x 128 MMA tile, K = M), and the update Y (Q - I) as Re Y B and Im Y B with
+//    B = [Re(Q - I) | Im Q] (M = 128-row tiles, N = 128, K = 64), combined and added to Y on the
+//    CUDA cores. Operands are staged by the CTA's threads (which split fp32 into TF32 pairs) in
+//    K-major core-matrix layout; one thread issues the MMAs and an mbarrier reports their
+//    completion.
 //  * The inner 64 x 64 problem runs on the CUDA cores from shared memory.
 //  * One CTA of 256 threads works on one symbol (X and W, 4 MB at 512 x 512, in its workspace
 //    slot), taking the block pairs of each round in turn; CTAs pull symbols from an atomic work
