@@ -111,10 +111,41 @@ bw_g_tc_kernel(LayerArgs La, const float* dsigma, int half_output, const float2*
     const float2* Vr = V + ((size_t)h * ci + (irow ? i0 + row : 0)) * r;
     // a chunk's four singular indices of this thread: g~ U and V entries of its rows
     float2 pu[PD][4], pv[PD][4];
+    // With r a multiple of 4 (and 16-byte aligned arrays), a thread's four singular indices are all in
+    // range or all out, and its rows of U, V and dsigma start on 16-byte boundaries: 16-byte loads.
+    const bool vec4 = (r & 3) == 0 && ((reinterpret_cast<uintptr_t>(dsigma) | reinterpret_cast<uintptr_t>(U) |
+                                         reinterpret_cast<uintptr_t>(V)) & 15) == 0;
     auto prefetch = [&](int c, float2* u, float2* v) {
+      const int s0 = c * KS + 4 * kc;
+      if (vec4) {
+        if (s0 < r) {
+          float4 g4 = *reinterpret_cast<const float4*>(g_f + s0);
+          if (g_c) {
+            const float4 c4 = *reinterpret_cast<const float4*>(g_c + s0);
+            g4 = make_float4(g4.x + c4.x, g4.y + c4.y, g4.z + c4.z, g4.w + c4.w);
+          }
+          const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+          const float4 u01 = orow ? *reinterpret_cast<const float4*>(Ur + s0) : z;
+          const float4 u23 = orow ? *reinterpret_cast<const float4*>(Ur + s0 + 2) : z;
+          const float4 v01 = irow ? *reinterpret_cast<const float4*>(Vr + s0) : z;
+          const float4 v23 = irow ? *reinterpret_cast<const float4*>(Vr + s0 + 2) : z;
+          u[0] = make_float2(u01.x * g4.x, u01.y * g4.x);
+          u[1] = make_float2(u01.z * g4.y, u01.w * g4.y);
+          u[2] = make_float2(u23.x * g4.z, u23.y * g4.z);
+          u[3] = make_float2(u23.z * g4.w, u23.w * g4.w);
+          v[0] = make_float2(v01.x, v01.y);
+          v[1] = make_float2(v01.z, v01.w);
+          v[2] = make_float2(v23.x, v23.y);
+          v[3] = make_float2(v23.z, v23.w);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) u[q] = v[q] = make_float2(0.f, 0.f);
+        }
+        return;
+      }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int s = c * KS + 4 * kc + q;
+        const int s = s0 + q;
         const bool ok = s < r;
         const float g = ok ? g_f[s] + (g_c ? g_c[s] : 0.f) : 0.f;
         float2 x = (ok && orow) ? Ur[s] : make_float2(0.f, 0.f);
