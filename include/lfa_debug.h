@@ -77,13 +77,20 @@ int32_t lfa_debug_backward_route(int32_t c_out, int32_t c_in, int32_t kh, int32_
 
 /* Phase profile of the blocked tensor-core route in the last lfa_svd call of a plan (waits for the
  * plan's last stream): out[0..5] = clock cycles summed over the route's CTAs (thread 0 of each) in
- * block-pair Grams, inner sweeps, updates, symbol assembly, output, and whole symbols; *ctas = the
- * CTAs of the route's launch for the plan's first blocked layer (0 when no layer takes the route).
- * plan is an lfa_plan_t. Returns an lfa_status_t (0 on success, 1 on a NULL argument). */
+ * block-pair Grams, inner sweeps, updates, symbol assembly (with a warm start's product), output,
+ * and whole symbols; out[6] = symbols that started warm (from the V of the previous symbol of their
+ * run); *ctas = the CTAs of the route's launch for the plan's first blocked layer (0 when no layer
+ * takes the route). out holds 7 entries. plan is an lfa_plan_t. Returns an lfa_status_t (0 on
+ * success, 1 on a NULL argument). */
 int32_t lfa_debug_bj_profile(void* plan, uint64_t* out, int32_t* ctas);
 /* Co-resident CTAs per SM of the blocked route in plans created afterwards: 0 restores the
  * kernel's own choice (two), 1 launches one per SM. For launch-shape measurements. */
 void lfa_debug_set_bj_ctas_per_sm(int32_t n);
+/* Launch shape of the blocked route in plans created afterwards: at most max_ctas CTAs (<= 0: the
+ * kernel's own count), and `runs` runs of neighbouring symbols per layer for the warm starts with
+ * vectors (0: two per CTA, the default; < 0: no warm starts, every symbol starts from W = I). For
+ * tests of the warm starts on small layers and for measurements. */
+void lfa_debug_set_bj_grid(int32_t max_ctas, int32_t runs);
 /* Resources of the blocked route's kernel (values-only or with vectors): out[0] = CTAs per SM the
  * occupancy calculator admits, out[1] = registers per thread, out[2] = static and out[3] = dynamic
  * shared memory per CTA in bytes, out[4] = CTAs per SM with 32 KB of dynamic shared memory instead.

@@ -86,7 +86,8 @@ struct Misc {
   int32_t failed;       // a bounded wait ran out: no further tensor work in this CTA
   int32_t item;         // work item
   int32_t any;          // some pair of the block pair passes the rotation test
-  int32_t pad[5];
+  int32_t warm;         // the symbol starts from its predecessor's V
+  int32_t pad[4];
 };
 static_assert(sizeof(Misc) <= 64, "misc block");
 
@@ -561,6 +562,72 @@ __device__ void cta_teardown(unsigned char* sm) {
   }
 }
 
+// ---------------------------------------------------------------------------------- warm start
+// X = T W for a warm start (T, X: Mp x Np; W: Np x Np; complex, column-major planes, T and X with
+// leading dimension ldx, W with ldw), on the CUDA cores in FP32. Only the first K columns of T and
+// rows of W are nonzero (K a multiple of 32). 64 x 64 output tiles, K in chunks of 32 staged in
+// shared memory (the block-pair region, free at the start of a symbol); thread (ty, tx) of 16 x 16
+// forms the 4 x 4 complex block at rows 4 ty.., columns 4 tx...
+__device__ void warm_gemm(unsigned char* sm, const float* Tr, const float* Ti, const float* Wr, const float* Wi,
+                          float* Xr, float* Xi, int ldx, int ldw, int Mp, int Np, int K) {
+  constexpr int TR = 64, TC = 64, TK = 32, SA = TR + 4, SB = TC + 4;
+  static_assert(THREADS == 256 && 2 * TK * (SA + SB) * 4 <= REGION_BYTES, "tiles fit the region");
+  float* sAr = reinterpret_cast<float*>(sm + OFF_STAGE);   // [TK][SA]: column k of the T tile
+  float* sAi = sAr + TK * SA;
+  float* sBr = sAi + TK * SA;                               // [TK][SB]: row k of the W tile
+  float* sBi = sBr + TK * SB;
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  for (int r0 = 0; r0 < Mp; r0 += TR) {
+    for (int c0 = 0; c0 < Np; c0 += TC) {
+      float accr[4][4], acci[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) accr[i][j] = acci[i][j] = 0.f;
+      for (int k0 = 0; k0 < K; k0 += TK) {
+#pragma unroll
+        for (int it = 0; it < TK * TR / THREADS; ++it) {   // T: 64 consecutive rows of column k
+          const int e = threadIdx.x + THREADS * it, k = e / TR, r = e % TR;
+          const size_t g = (size_t)(k0 + k) * ldx + r0 + r;
+          sAr[k * SA + r] = __ldcg(Tr + g);
+          sAi[k * SA + r] = __ldcg(Ti + g);
+        }
+#pragma unroll
+        for (int it = 0; it < TK * TC / THREADS; ++it) {   // W: 32 consecutive rows of column c
+          const int e = threadIdx.x + THREADS * it, c = e / TK, k = e % TK;
+          const size_t g = (size_t)(c0 + c) * ldw + k0 + k;
+          sBr[k * SB + c] = __ldcg(Wr + g);
+          sBi[k * SB + c] = __ldcg(Wi + g);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < TK; ++k) {
+          const float4 ar = *reinterpret_cast<const float4*>(sAr + k * SA + 4 * ty);
+          const float4 ai = *reinterpret_cast<const float4*>(sAi + k * SA + 4 * ty);
+          const float4 br = *reinterpret_cast<const float4*>(sBr + k * SB + 4 * tx);
+          const float4 bi = *reinterpret_cast<const float4*>(sBi + k * SB + 4 * tx);
+          const float xr[4] = {ar.x, ar.y, ar.z, ar.w}, xi[4] = {ai.x, ai.y, ai.z, ai.w};
+          const float yr[4] = {br.x, br.y, br.z, br.w}, yi[4] = {bi.x, bi.y, bi.z, bi.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              accr[i][j] = fmaf(xr[i], yr[j], fmaf(-xi[i], yi[j], accr[i][j]));
+              acci[i][j] = fmaf(xr[i], yi[j], fmaf(xi[i], yr[j], acci[i][j]));
+            }
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const size_t g = (size_t)(c0 + 4 * tx + j) * ldx + r0 + 4 * ty;
+        *reinterpret_cast<float4*>(Xr + g) = make_float4(accr[0][j], accr[1][j], accr[2][j], accr[3][j]);
+        *reinterpret_cast<float4*>(Xi + g) = make_float4(acci[0][j], acci[1][j], acci[2][j], acci[3][j]);
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------------- symbol kernel
 // Block pair of position `pos` at round t of the circle method over nb blocks: (t, nb - 1) for
 // position 0, else (c(t + pos), c(t - pos)), c(x) = x mod (nb - 1).
@@ -573,7 +640,9 @@ __device__ __forceinline__ void outer_pair(int t, int pos, int nb, int& I, int& 
 }  // namespace bj
 
 // One symbol per CTA (a persistent grid pulling symbols from an atomic work queue). Per symbol:
-// assembly of X = A_k (or A_k^*) into the CTA's workspace slot and W = I; sweeps over the block
+// assembly of X = A_k (or A_k^*) into the CTA's workspace slot and W = I, or with a warm start
+// W = the previous symbol's V and X = A_k W (neighbouring frequencies have nearby singular
+// vectors, so X starts nearly orthogonal and needs fewer sweeps); sweeps over the block
 // pairs in circle-method order (nb - 1 rounds of nb / 2 pairs); then sigma, ranks and the
 // normalised factors written to the layer's outputs. CTAs of 256 threads, two per SM.
 template <bool VEC>
@@ -611,27 +680,63 @@ __global__ void __maxnreg__(bj::MAX_REGS) bj_kernel(const __grid_constant__ BJLa
     int lk = 0;                                         // the item's layer
     while (lk + 1 < A.nlayers && item >= A.L[lk + 1].item_begin) ++lk;
     const LayerArgs& La = A.L[lk];
-    const int h = item - La.item_begin;                 // half-grid symbol of that layer
+    // the layer's item t: run t % runs, position t / runs in it, symbol run * len + position
+    int h = item - La.item_begin, pos = 0;
+    if (A.runs > 0) {
+      const int len = (La.F_h + A.runs - 1) / A.runs, t = h;
+      pos = t / A.runs;
+      h = (t - pos * A.runs) * len + pos;
+      if (h >= La.F_h) {                                // past the layer's last symbol
+        __syncthreads();                                // every thread has read ms->item
+        continue;
+      }
+    }
     if (!LFA_DOK(La.dbg, h >= 0 && h < La.F_h, 5)) continue;   // blocked route: item -> layer, symbol
     const int M = La.M, N = La.N;
-    if (threadIdx.x == 0) c_sym = clock64();
+    if (threadIdx.x == 0) {
+      c_sym = clock64();
+      // a warm start when the run's previous symbol is done (its factors are in the outputs)
+      ms->warm = (VEC && pos > 0 && tc::ld_acquire_gpu(A.done + A.sym_begin[lk] + h - 1) != 0) ? 1 : 0;
+    }
     const int f = La.half[h];
     const int jj = f / La.m, ll = f - jj * La.m;
     const int kk = La.kh * La.kw;
     for (int t = threadIdx.x; t < kk; t += THREADS) phs[t] = tap_phase(La, jj, ll, t / La.kw, t % La.kw);
     __syncthreads();
-    // ---- X = the symbol (assembled from the taps), W = I; padding rows and columns are zero
+    const bool warm = VEC && ms->warm;
+    // ---- X = the symbol (assembled from the taps), W = I; padding rows and columns are zero.
+    // Warm start: the symbol goes to the T planes, W = V of the run's previous symbol, X = T W (the
+    // sweeps keep X = A W for any starting W; a nearly orthogonal T W needs fewer of them)
+    float* Tr = warm ? sg + Np : Xr;
+    float* Ti = warm ? Tr + (size_t)Np * ldx : Xi;
     for (int c = 0; c < Np; ++c) {
       for (int row = threadIdx.x; row < Mp; row += THREADS) {
         const float2 v = x_entry<true>(La, h, row, c, phs);
-        Xr[(size_t)c * ldx + row] = v.x;
-        Xi[(size_t)c * ldx + row] = v.y;
+        Tr[(size_t)c * ldx + row] = v.x;
+        Ti[(size_t)c * ldx + row] = v.y;
       }
       if constexpr (VEC) {
-        for (int row = threadIdx.x; row < Np; row += THREADS) {
-          Wr[(size_t)c * ldw + row] = (row == c && c < N) ? 1.f : 0.f;
-          Wi[(size_t)c * ldw + row] = 0.f;
+        if (!warm) {
+          for (int row = threadIdx.x; row < Np; row += THREADS) {
+            Wr[(size_t)c * ldw + row] = (row == c && c < N) ? 1.f : 0.f;
+            Wi[(size_t)c * ldw + row] = 0.f;
+          }
         }
+      }
+    }
+    if constexpr (VEC) {
+      if (warm) {
+        // W(row, c) = Wo(row, c) of the previous symbol (row-major N x N, read along rows)
+        const float2* Wp = (La.wide ? La.U : La.V) + (size_t)(h - 1) * N * N;
+        for (int e = threadIdx.x; e < Np * Np; e += THREADS) {
+          const int row = e / Np, c = e - row * Np;
+          const float2 v = (row < N && c < N) ? __ldcg(Wp + (size_t)row * N + c) : make_float2(0.f, 0.f);
+          Wr[(size_t)c * ldw + row] = v.x;
+          Wi[(size_t)c * ldw + row] = v.y;
+        }
+        __syncthreads();
+        warm_gemm(sm, Tr, Ti, Wr, Wi, Xr, Xi, ldx, ldw, Mp, Np, (N + 31) / 32 * 32);
+        if (threadIdx.x == 0) atomicAdd(&ctr->warm_starts, 1ull);
       }
     }
     __threadfence_block();
@@ -785,8 +890,11 @@ __global__ void __maxnreg__(bj::MAX_REGS) bj_kernel(const __grid_constant__ BJLa
       }
       __syncthreads();
     }
+    if (VEC && A.runs > 0) __threadfence();   // this thread's outputs, before the done flag
     __syncthreads();   // the slot is reused by the CTA's next symbol
     if (threadIdx.x == 0) {
+      // every thread's outputs precede the barrier; the release publishes them with the flag
+      if (VEC && A.runs > 0) tc::st_release_gpu(A.done + A.sym_begin[lk] + h, 1);
       const long long c_end = clock64();
       cyc[4] += (unsigned long long)(c_end - c_ph);
       cyc[5] += (unsigned long long)(c_end - c_sym);
@@ -798,6 +906,8 @@ __global__ void __maxnreg__(bj::MAX_REGS) bj_kernel(const __grid_constant__ BJLa
 }
 
 int g_bj_ctas_per_sm = 0;
+int g_bj_max_ctas = 0;
+int g_bj_runs = 0;
 
 template <bool VEC>
 static cudaError_t bj_prepare_t(int sms, int* max_ctas) {
@@ -857,7 +967,8 @@ cudaError_t bj_max_ctas(bool vec, int sms, int* ctas) {
 size_t bj_slot_floats(int M, int N, bool vec) {
   int Mp, Np;
   bj_dims(M, N, &Mp, &Np);
-  return (size_t)2 * Np * Mp + (vec ? (size_t)2 * Np * Np : 0) + (size_t)Np;
+  // X planes, W planes (vectors), sigma per column, and with vectors a warm start's T planes
+  return (size_t)2 * Np * Mp + (vec ? (size_t)2 * Np * Np : 0) + (size_t)Np + (vec ? (size_t)2 * Np * Mp : 0);
 }
 
 cudaError_t launch_bj(const BJLaunch& A, int ctas, bool vec, cudaStream_t s) {

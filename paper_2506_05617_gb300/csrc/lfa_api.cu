@@ -234,11 +234,13 @@ struct lfa_plan_s {
   std::vector<Logged> logged;
   // layers on the blocked tensor-core route, and their launches: one persistent launch per group of
   // layers whose symbols pad to the same Mp x Np (indices into `blocked`), with its CTA count
-  struct Blocked { int layer; int ctas; };
+  struct Blocked { int layer; int ctas; int sym_begin; };   // sym_begin: the layer's first done flag
   std::vector<Blocked> blocked;
-  struct BlockedGroup { std::vector<int> members; int ctas; int Mp, Np; };
+  struct BlockedGroup { std::vector<int> members; int ctas; int Mp, Np; int runs; };
   std::vector<BlockedGroup> bj_groups;
   float* bj_ws = nullptr;
+  int32_t* bj_done = nullptr;   // done flags of the blocked layers' symbols (warm starts)
+  int bj_symbols = 0;
   float4* log_ws = nullptr;
   int32_t* rounds_ws = nullptr;
   float2* xraw_ws = nullptr;
@@ -357,6 +359,8 @@ lfa_status_t enqueue_blocked(lfa_plan_s* p, const float* const* w, float* const*
                              float* const* V, cudaStream_t s) {
   // blocked layers: one persistent launch per group of same-size layers (queue slot 14), then the
   // completion of zero columns per layer
+  if (p->bj_done)
+    LFA_CUDA_TRY(cudaMemsetAsync(p->bj_done, 0, (size_t)p->bj_symbols * sizeof(int32_t), s));
   for (const auto& bg : p->bj_groups) {
     // BJLaunch holds kMaxLayers layers (~10 KB): built on the heap, passed by value at launch
     std::unique_ptr<BJLaunch> A(new (std::nothrow) BJLaunch());
@@ -371,9 +375,13 @@ lfa_status_t enqueue_blocked(lfa_plan_s* p, const float* const* w, float* const*
       La.U = p->vec ? reinterpret_cast<float2*>(U[l]) : nullptr;
       La.V = p->vec ? reinterpret_cast<float2*>(V[l]) : nullptr;
       La.item_begin = items;
-      items += La.F_h;
+      // with warm starts, runs * ceil(F_h / runs) items (see BJLaunch)
+      items += bg.runs > 0 ? bg.runs * ((La.F_h + bg.runs - 1) / bg.runs) : La.F_h;
+      A->sym_begin[k] = p->blocked[bg.members[k]].sym_begin;
     }
     A->nlayers = (int)bg.members.size();
+    A->runs = bg.runs;
+    A->done = p->bj_done;
     A->Mp = bg.Mp;
     A->Np = bg.Np;
     A->ldx = bg.Mp;
@@ -635,7 +643,7 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
       int ctas = 0;
       cudaError_t be = bj_max_ctas(p->vec, prop.multiProcessorCount, &ctas);
       if (be != cudaSuccess || ctas < 1) { free_plan(p); return be != cudaSuccess ? from_cuda(be) : LFA_ERR_UNSUPPORTED; }
-      p->blocked.push_back({l, ctas});   // the CTA count is the launch's, set per group below
+      p->blocked.push_back({l, ctas, 0});   // the CTA count is the launch's, set per group below
       p->variant[l] = -1;
     }
     if (!blocked && v < 0) v = choose_variant(La.M, La.N, p->vec);
@@ -702,7 +710,7 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
     auto it = std::find_if(p->bj_groups.begin(), p->bj_groups.end(),
                            [&](const lfa_plan_s::BlockedGroup& g) { return g.Mp == Mp && g.Np == Np; });
     if (it == p->bj_groups.end()) {
-      p->bj_groups.push_back({{b}, 0, Mp, Np});
+      p->bj_groups.push_back({{b}, 0, Mp, Np, 0});
       it = p->bj_groups.end() - 1;
     } else {
       it->members.push_back(b);
@@ -712,7 +720,15 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
     int items = 0;
     for (int b : g.members) items += p->args[p->blocked[b].layer].F_h;
     g.ctas = std::min(p->blocked[g.members[0]].ctas, std::max(1, items));
-    for (int b : g.members) p->blocked[b].ctas = g.ctas;
+    if (g_bj_max_ctas > 0) g.ctas = std::min(g.ctas, g_bj_max_ctas);
+    // warm starts (vectors): two runs of neighbouring symbols per CTA, so that the CTA taking a
+    // run's next symbol finds the previous one done (about two symbol times apart in the queue)
+    g.runs = (!p->vec || g_bj_runs < 0) ? 0 : g_bj_runs > 0 ? g_bj_runs : 2 * g.ctas;
+    for (int b : g.members) {
+      p->blocked[b].ctas = g.ctas;
+      p->blocked[b].sym_begin = p->bj_symbols;
+      p->bj_symbols += p->args[p->blocked[b].layer].F_h;
+    }
     bj_bytes = std::max(bj_bytes, (size_t)g.ctas * bj_slot_floats(g.Mp, g.Np, p->vec) * sizeof(float));
   }
   const size_t off_sym = bytes; bytes += align256(sym_bytes);
@@ -730,6 +746,7 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
   const size_t off_rounds = bytes; bytes += align256(rounds_bytes);
   const size_t off_wraw = bytes; bytes += align256(wraw_bytes);
   const size_t off_bj = bytes; bytes += align256(bj_bytes);
+  const size_t off_done = bytes; bytes += align256((size_t)p->bj_symbols * sizeof(int32_t));
   // FFT route: transform batches of channel pairs within 512 MB of real grids and spectra
   size_t fft_bytes = 0;
   if (p->fft) {
@@ -760,6 +777,7 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
   p->rounds_ws = rounds_bytes ? reinterpret_cast<int32_t*>(base + off_rounds) : nullptr;
   p->wraw_ws = wraw_bytes ? reinterpret_cast<float2*>(base + off_wraw) : nullptr;
   p->bj_ws = bj_bytes ? reinterpret_cast<float*>(base + off_bj) : nullptr;
+  p->bj_done = p->bj_symbols ? reinterpret_cast<int32_t*>(base + off_done) : nullptr;
   p->fft_ws = fft_bytes ? static_cast<void*>(base + off_fft) : nullptr;
   for (int l = 0; l < nlayers && p->fft && e == cudaSuccess; ++l)
     e = fft_make_plan(p->args[l], p->fft_pairs[l], &p->fft_plans[l]);
@@ -1197,11 +1215,17 @@ int32_t lfa_debug_bj_profile(void* plan, uint64_t* out, int32_t* ctas) {
   Counters c;
   LFA_CUDA_TRY(cudaMemcpy(&c, p->counters, sizeof c, cudaMemcpyDeviceToHost));
   for (int k = 0; k < 6; ++k) out[k] = (uint64_t)c.bj_cycles[k];
+  out[6] = (uint64_t)c.warm_starts;
   *ctas = p->blocked.empty() ? 0 : p->blocked[0].ctas;
   return LFA_OK;
 }
 
 void lfa_debug_set_bj_ctas_per_sm(int32_t n) { g_bj_ctas_per_sm = n < 0 ? 0 : n; }
+
+void lfa_debug_set_bj_grid(int32_t max_ctas, int32_t runs) {
+  g_bj_max_ctas = max_ctas < 0 ? 0 : max_ctas;
+  g_bj_runs = runs;
+}
 
 int32_t lfa_debug_bj_occupancy(int32_t vectors, int32_t* out) {
   if (out == nullptr) return LFA_ERR_INVALID_ARG;

@@ -25,6 +25,7 @@ struct Counters {
   unsigned int queue[16];        // work-queue tickets, one per launch of a call
   unsigned int bw_queue[2];      // work-queue tickets of the tensor-core backward's launches
   unsigned int debug_error;      // debug build: the site id of the first failed index check
+  unsigned long long warm_starts; // blocked route: symbols started from their predecessor's V
 };
 
 // One layer as a kernel sees it. The Jacobi problem of a symbol is X (M x N), with
@@ -164,15 +165,24 @@ bool replay_supported(int NP);        // a replay configuration exists for NP pa
 
 // Blocked one-sided Jacobi on the tensor cores (blocked.cu): one CTA per symbol, X and W in a
 // per-CTA workspace slot (column-major real / imaginary planes). One launch serves the layers whose
-// symbols pad to the same Mp x Np; layer k's symbols are items [L[k].item_begin, + L[k].F_h).
+// symbols pad to the same Mp x Np; layer k's items start at L[k].item_begin (F_h of them, or
+// runs * ceil(F_h / runs) with warm starts).
 struct BJLaunch {
   LayerArgs L[kMaxLayers];
   int32_t nlayers;
+  // Warm starts (vectors; runs > 0): layer k's symbols are items in `runs` runs of neighbouring
+  // half-grid symbols (item t of the layer -> run t % runs, position p = t / runs, symbol
+  // run * len + p with len = ceil(F_h / runs); a layer has runs * len items, those past F_h are
+  // skipped). done[sym_begin[k] + h] != 0 once symbol h's outputs are written; the run's next
+  // symbol then starts from its V, else from W = I. runs = 0: item t is symbol t, cold starts.
+  int32_t runs;
+  int32_t* done;
+  int32_t sym_begin[kMaxLayers];
   int32_t Mp, Np;           // padded rows of X (multiple of 128) and columns (multiple of 128)
   int32_t ldx, ldw;         // leading dimensions of the X and W planes
   float* ws;                // slots of slot_floats floats, one per CTA of the grid
   size_t slot_floats;
-  int32_t total_items;      // symbols of the launch
+  int32_t total_items;      // items of the launch
   int32_t max_sweeps;
   int32_t half_output;
   int32_t queue_slot;
@@ -184,6 +194,8 @@ void bj_dims(int M, int N, int* Mp, int* Np);
 size_t bj_slot_floats(int M, int N, bool vec);
 cudaError_t bj_max_ctas(bool vec, int sms, int* ctas);   // co-resident CTAs (kernel attributes set)
 extern int g_bj_ctas_per_sm;                             // 0: the kernel's own choice (debug hook)
+extern int g_bj_max_ctas;                                // > 0: at most this many CTAs (debug hook)
+extern int g_bj_runs;                                    // 0: two runs per CTA, < 0: no warm starts
 cudaError_t bj_occupancy(bool vec, int* blocks, int* regs, int* smem_static, int* smem_dyn);
 cudaError_t launch_bj(const BJLaunch& A, int ctas, bool vec, cudaStream_t s);
 cudaError_t launch_bj_gram_test(const float* Xr, const float* Xi, int ld, int Mp, const int* cols, float* D,

@@ -150,6 +150,16 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// Flags between CTAs of one grid: a load with acquire and a store with release semantics at GPU scope.
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // ---------------------------------------------------------------------------------- TF32 split
 // x = hi + lo with hi = x rounded to TF32 (nearest, ties away) and lo = (x - hi) rounded to TF32:
 // the operands of the 3xTF32 product hi*hi + hi*lo + lo*hi, whose error is a few fp32 units.

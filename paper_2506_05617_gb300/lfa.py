@@ -55,7 +55,7 @@ EXPORTS = [
     "lfa_debug_schedule", "lfa_debug_half_grid", "lfa_debug_choose_variant", "lfa_debug_variant_count",
     "lfa_debug_tuned_variant", "lfa_debug_variant_fits", "lfa_debug_logged_ok", "lfa_debug_half_position",
     "lfa_debug_shard_range", "lfa_debug_tc_gram", "lfa_debug_tc_update", "lfa_debug_bj_profile",
-    "lfa_debug_set_bj_ctas_per_sm", "lfa_debug_bj_occupancy", "lfa_debug_backward_route",
+    "lfa_debug_set_bj_ctas_per_sm", "lfa_debug_set_bj_grid", "lfa_debug_bj_occupancy", "lfa_debug_backward_route",
 ]
 
 
@@ -148,6 +148,7 @@ def lib():
                                           c_void_p, c_void_p]),
         "lfa_debug_bj_profile": (c_int32, [P, POINTER(ctypes.c_uint64), POINTER(c_int32)]),
         "lfa_debug_set_bj_ctas_per_sm": (None, [c_int32]),
+        "lfa_debug_set_bj_grid": (None, [c_int32, c_int32]),
         "lfa_debug_bj_occupancy": (c_int32, [c_int32, POINTER(c_int32)]),
         "lfa_debug_backward_route": (c_int32, [c_int32] * 6),
     }
@@ -360,19 +361,26 @@ BJ_PHASES = ("gram", "inner", "update", "assembly", "output", "symbol")
 
 
 def lfa_debug_bj_profile(plan: int):
-    """Phase clock cycles of the blocked route in the plan's last forward (summed over its CTAs) and
-    the CTA count of its launch: (dict phase -> cycles, ctas)."""
-    out = (ctypes.c_uint64 * 6)()
+    """Phase clock cycles of the blocked route in the plan's last forward (summed over its CTAs),
+    plus "warm_starts" (symbols started from their predecessor's V), and the CTA count of its
+    launch: (dict, ctas)."""
+    out = (ctypes.c_uint64 * 7)()
     ctas = c_int32(0)
     st = lib().lfa_debug_bj_profile(c_void_p(plan), out, ctypes.byref(ctas))
     if st != LFA_OK:
         raise LfaError(st, "lfa_debug_bj_profile")
-    return {k: int(v) for k, v in zip(BJ_PHASES, out)}, int(ctas.value)
+    return {k: int(v) for k, v in zip(BJ_PHASES + ("warm_starts",), out)}, int(ctas.value)
 
 
 def lfa_debug_set_bj_ctas_per_sm(n: int) -> None:
     """CTAs per SM of the blocked route in plans created afterwards (0: the kernel's choice)."""
     lib().lfa_debug_set_bj_ctas_per_sm(int(n))
+
+
+def lfa_debug_set_bj_grid(max_ctas: int, runs: int) -> None:
+    """Blocked route in plans created afterwards: at most max_ctas CTAs (<= 0: the kernel's count)
+    and `runs` warm-start runs per layer (0: two per CTA, < 0: no warm starts)."""
+    lib().lfa_debug_set_bj_grid(int(max_ctas), int(runs))
 
 
 def lfa_debug_bj_occupancy(vectors: bool):

@@ -98,3 +98,47 @@ def test_blocked_layers_share_a_launch():
         assert np.max(np.abs(s[f].astype(np.float64) - s_ref)) <= 1e-5 * smax
         check_factors(O.symbols(w, n, m)[f], s[f], U[i].cpu().numpy()[pick], V[i].cpu().numpy()[pick])
     plan.close()
+
+
+WARM = [
+    # c_out, c_in, k, n, m
+    (256, 256, 3, 8, 8),     # square
+    (300, 200, 3, 8, 7),     # ragged: 200 columns padded to 256, K of the warm product 224
+    (200, 300, 3, 7, 8),     # wide: X = A^*, the warm start takes U of the previous symbol
+]
+
+
+@pytest.mark.parametrize("spec", WARM, ids=lambda s: "x".join(str(v) for v in s))
+def test_blocked_warm_starts_match_oracle(spec):
+    """Warm starts: each symbol after the first of a run of neighbouring frequencies starts its
+    sweeps from X = A W with W the previous symbol's V (the invariant X = A W holds for any
+    starting W). Four CTAs and eight runs, so that most symbols find their predecessor done; the
+    factors against the oracle as for cold starts, and fewer sweeps than the same layer with every
+    symbol started from W = I."""
+    c_out, c_in, k, n, m = spec
+    w = rand_w(c_out, c_in, k, k, seed=7 * c_out + c_in)
+    half = O.half_grid(n, m)
+    sweeps = {}
+    try:
+        for runs in (8, -1):
+            C.lfa_debug_set_bj_grid(4, runs)
+            plan = LfaPlan([(c_out, c_in, k, k, n, m)], vectors=True, variant=C.LFA_VARIANT_BLOCKED)
+            sig, U, V = plan.svd([torch.from_numpy(w).cuda()])
+            torch.cuda.synchronize()
+            st, info = plan.info()
+            assert st == C.LFA_OK, info
+            prof, ctas = C.lfa_debug_bj_profile(plan.handle)
+            assert ctas == 4
+            if runs > 0:
+                # runs of ceil(F_h / 8) symbols; the first symbol of each of the 8 runs starts cold
+                assert prof["warm_starts"] >= len(half) // 2, (prof["warm_starts"], len(half))
+            else:
+                assert prof["warm_starts"] == 0
+            s = sig[0].cpu().numpy()
+            check_sigma(w, n, m, s)
+            check_factors(O.symbols(w, n, m)[half], s[half], U[0].cpu().numpy(), V[0].cpu().numpy())
+            sweeps[runs] = info["sweeps"]
+            plan.close()
+    finally:
+        C.lfa_debug_set_bj_grid(0, 0)
+    assert sweeps[8] < sweeps[-1], sweeps
