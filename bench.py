@@ -83,9 +83,11 @@ def kernel_sha16() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic(workload: str):
+def measured_traffic(workload: str, info=None):
     """DRAM bytes per launch of the Jacobi kernel from the committed ncu capture, or None when
-    there is none for this workload or the kernel source changed since it was taken."""
+    there is none for this workload or the kernel source changed since it was taken. A capture of
+    the blocked route on a smaller case gives bytes per block-pair Gram (each Gram reads the pair's
+    columns of X, each update rewrites them and W's): scaled by the launch's own Gram count."""
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(prof)).get(workload)
@@ -93,6 +95,8 @@ def measured_traffic(workload: str):
         return None
     if not rec or rec.get("kernel_sha16") != kernel_sha16():
         return None
+    if "bytes_per_gram" in rec:
+        return rec["bytes_per_gram"] * info["tc_grams"] if info else None
     return rec.get("bytes_per_launch")
 
 
@@ -577,7 +581,7 @@ def run_lfa(args, rank: int, world: int, local_rank: int):
     flops = sum(layer_flops(l, vectors) for l in layers)
     peak = fp32_peak_tflops()
     achieved = flops / (fwd_mean / 1e3) / 1e12
-    traffic = measured_traffic(args.workload)
+    traffic = measured_traffic(args.workload, info)
     routes = [m["variant"] for m in plan.meta]
     if routes[0] == C.LFA_VARIANT_BLOCKED:
         # the dominant kernel is the blocked Jacobi on the tensor cores (all layers of the workload

@@ -677,26 +677,27 @@ __global__ void __maxnreg__(bj::MAX_REGS) bj_kernel(const __grid_constant__ BJLa
     __syncthreads();
     const int item = ms->item;
     if (item >= A.total_items) break;
-    int lk = 0;                                         // the item's layer
-    while (lk + 1 < A.nlayers && item >= A.L[lk + 1].item_begin) ++lk;
-    const LayerArgs& La = A.L[lk];
-    // the layer's item t: run t % runs, position t / runs in it, symbol run * len + position
-    int h = item - La.item_begin, pos = 0;
+    // item t: run t % runs, position t / runs in it, symbol g = run * run_len + position of the launch
+    int g = item, pos = 0;
     if (A.runs > 0) {
-      const int len = (La.F_h + A.runs - 1) / A.runs, t = h;
-      pos = t / A.runs;
-      h = (t - pos * A.runs) * len + pos;
-      if (h >= La.F_h) {                                // past the layer's last symbol
+      pos = item / A.runs;
+      g = (item - pos * A.runs) * A.run_len + pos;
+      if (g >= A.total_symbols) {                       // past the launch's last symbol
         __syncthreads();                                // every thread has read ms->item
         continue;
       }
     }
+    int lk = 0;                                         // the symbol's layer
+    while (lk + 1 < A.nlayers && g >= A.L[lk + 1].item_begin) ++lk;
+    const LayerArgs& La = A.L[lk];
+    const int h = g - La.item_begin;                    // half-grid symbol of that layer
     if (!LFA_DOK(La.dbg, h >= 0 && h < La.F_h, 5)) continue;   // blocked route: item -> layer, symbol
     const int M = La.M, N = La.N;
     if (threadIdx.x == 0) {
       c_sym = clock64();
       // a warm start when the run's previous symbol is done (its factors are in the outputs)
-      ms->warm = (VEC && pos > 0 && tc::ld_acquire_gpu(A.done + A.sym_begin[lk] + h - 1) != 0) ? 1 : 0;
+      // (the previous symbol of the run in the same layer)
+      ms->warm = (VEC && pos > 0 && h > 0 && tc::ld_acquire_gpu(A.done + g - 1) != 0) ? 1 : 0;
     }
     const int f = La.half[h];
     const int jj = f / La.m, ll = f - jj * La.m;
@@ -894,7 +895,7 @@ __global__ void __maxnreg__(bj::MAX_REGS) bj_kernel(const __grid_constant__ BJLa
     __syncthreads();   // the slot is reused by the CTA's next symbol
     if (threadIdx.x == 0) {
       // every thread's outputs precede the barrier; the release publishes them with the flag
-      if (VEC && A.runs > 0) tc::st_release_gpu(A.done + A.sym_begin[lk] + h, 1);
+      if (VEC && A.runs > 0) tc::st_release_gpu(A.done + g, 1);
       const long long c_end = clock64();
       cyc[4] += (unsigned long long)(c_end - c_ph);
       cyc[5] += (unsigned long long)(c_end - c_sym);

@@ -374,14 +374,16 @@ lfa_status_t enqueue_blocked(lfa_plan_s* p, const float* const* w, float* const*
       La.sigma = sigma[l];
       La.U = p->vec ? reinterpret_cast<float2*>(U[l]) : nullptr;
       La.V = p->vec ? reinterpret_cast<float2*>(V[l]) : nullptr;
-      La.item_begin = items;
-      // with warm starts, runs * ceil(F_h / runs) items (see BJLaunch)
-      items += bg.runs > 0 ? bg.runs * ((La.F_h + bg.runs - 1) / bg.runs) : La.F_h;
-      A->sym_begin[k] = p->blocked[bg.members[k]].sym_begin;
+      La.item_begin = items;   // the layer's first symbol in the launch
+      items += La.F_h;
     }
     A->nlayers = (int)bg.members.size();
+    A->total_symbols = items;
     A->runs = bg.runs;
-    A->done = p->bj_done;
+    A->run_len = bg.runs > 0 ? (items + bg.runs - 1) / bg.runs : 1;
+    // the group's layers have consecutive done flags
+    A->done = p->bj_done ? p->bj_done + p->blocked[bg.members[0]].sym_begin : nullptr;
+    if (bg.runs > 0) items = bg.runs * A->run_len;
     A->Mp = bg.Mp;
     A->Np = bg.Np;
     A->ldx = bg.Mp;

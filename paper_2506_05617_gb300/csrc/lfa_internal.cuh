@@ -42,7 +42,7 @@ struct LayerArgs {
   const float2* symbols;    // materialised symbols [F_h][c_out][c_in] (plain path) or null
   int32_t c_out, c_in, kh, kw, n, m, ph, pw;
   int32_t F_h, r, M, N, wide;
-  int32_t item_begin;       // first work item of this layer in its launch
+  int32_t item_begin;       // first work item of this layer in its launch (blocked route: first symbol)
   // Stride (sh, sw) >= 1 and the weights' input channels c_w. The symbol has c_in = c_w sh sw
   // columns (i, u_h, u_w) -> i sh sw + u_h sw + u_w: the polyphase components of the fine input.
   int32_t c_w, sh, sw;
@@ -165,24 +165,25 @@ bool replay_supported(int NP);        // a replay configuration exists for NP pa
 
 // Blocked one-sided Jacobi on the tensor cores (blocked.cu): one CTA per symbol, X and W in a
 // per-CTA workspace slot (column-major real / imaginary planes). One launch serves the layers whose
-// symbols pad to the same Mp x Np; layer k's items start at L[k].item_begin (F_h of them, or
-// runs * ceil(F_h / runs) with warm starts).
+// symbols pad to the same Mp x Np; layer k's symbols are [L[k].item_begin, + L[k].F_h) of the
+// launch's total_symbols.
 struct BJLaunch {
   LayerArgs L[kMaxLayers];
   int32_t nlayers;
-  // Warm starts (vectors; runs > 0): layer k's symbols are items in `runs` runs of neighbouring
-  // half-grid symbols (item t of the layer -> run t % runs, position p = t / runs, symbol
-  // run * len + p with len = ceil(F_h / runs); a layer has runs * len items, those past F_h are
-  // skipped). done[sym_begin[k] + h] != 0 once symbol h's outputs are written; the run's next
-  // symbol then starts from its V, else from W = I. runs = 0: item t is symbol t, cold starts.
-  int32_t runs;
-  int32_t* done;
-  int32_t sym_begin[kMaxLayers];
+  // Warm starts (vectors; runs > 0): the launch's symbols (layer after layer, half-grid order) are
+  // cut into `runs` runs of run_len consecutive symbols; item t is position p = t / runs of run
+  // t % runs, symbol g = (t % runs) * run_len + p (total_items = runs * run_len, items past the
+  // last symbol are skipped). done[g] != 0 once symbol g's outputs are written; the next symbol of
+  // its run, in the same layer, then starts from its V, else from W = I. runs = 0: item t is
+  // symbol t, every symbol starts cold.
+  int32_t runs, run_len;
+  int32_t total_symbols;
+  int32_t* done;            // the launch's done flags (total_symbols)
   int32_t Mp, Np;           // padded rows of X (multiple of 128) and columns (multiple of 128)
   int32_t ldx, ldw;         // leading dimensions of the X and W planes
   float* ws;                // slots of slot_floats floats, one per CTA of the grid
   size_t slot_floats;
-  int32_t total_items;      // items of the launch
+  int32_t total_items;      // work items of the launch (total_symbols without warm starts)
   int32_t max_sweeps;
   int32_t half_output;
   int32_t queue_slot;

@@ -142,3 +142,38 @@ def test_blocked_warm_starts_match_oracle(spec):
     finally:
         C.lfa_debug_set_bj_grid(0, 0)
     assert sweeps[8] < sweeps[-1], sweeps
+
+
+def test_blocked_warm_start_runs_cross_layers_of_one_launch():
+    """Runs of warm starts span the symbols of all layers of one blocked launch: a 256 -> 200 and a
+    256 -> 256 layer (both padded to 256 x 256, one launch); a run that passes into the next layer
+    starts that layer's first symbol cold (its predecessor has other columns). Four CTAs, eight
+    runs; both layers against the oracle, and fewer sweeps than with cold starts only."""
+    specs = [(256, 200, 3, 3, 8, 7), (256, 256, 3, 3, 7, 8)]
+    ws = [rand_w(co, ci, kh, kw, seed=61 + i) for i, (co, ci, kh, kw, n, m) in enumerate(specs)]
+    total = sum(len(O.half_grid(n, m)) for (_, _, _, _, n, m) in specs)
+    sweeps = {}
+    try:
+        for runs in (8, -1):
+            C.lfa_debug_set_bj_grid(4, runs)
+            plan = LfaPlan(specs, vectors=True, variant=C.LFA_VARIANT_BLOCKED)
+            assert all(mt["variant"] == C.LFA_VARIANT_BLOCKED for mt in plan.meta)
+            sig, U, V = plan.svd([torch.from_numpy(w).cuda() for w in ws])
+            torch.cuda.synchronize()
+            st, info = plan.info()
+            assert st == C.LFA_OK, info
+            prof, _ = C.lfa_debug_bj_profile(plan.handle)
+            if runs > 0:
+                assert prof["warm_starts"] >= total // 2, (prof["warm_starts"], total)
+            else:
+                assert prof["warm_starts"] == 0
+            for i, ((co, ci, kh, kw, n, m), w) in enumerate(zip(specs, ws)):
+                s = sig[i].cpu().numpy()
+                check_sigma(w, n, m, s)
+                half = O.half_grid(n, m)
+                check_factors(O.symbols(w, n, m)[half], s[half], U[i].cpu().numpy(), V[i].cpu().numpy())
+            sweeps[runs] = info["sweeps"]
+            plan.close()
+    finally:
+        C.lfa_debug_set_bj_grid(0, 0)
+    assert sweeps[8] < sweeps[-1], sweeps
