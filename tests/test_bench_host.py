@@ -81,3 +81,18 @@ def test_traffic_is_reported_only_under_the_kernel_source_it_was_measured_on(tmp
     assert bench.measured_traffic("resnet18_body") is None
     monkeypatch.setattr(bench, "kernel_sha16", lambda: "bbbb")
     assert bench.measured_traffic("conv64_k3_n32") is None
+
+
+def test_blocked_route_traffic_scales_with_the_launch_gram_count(tmp_path, monkeypatch):
+    """A capture on a smaller case of the blocked route gives bytes per block-pair Gram; the bench
+    line's traffic is that times its own launch's Gram count, and null without the count."""
+    os.makedirs(tmp_path / "profiles")
+    with open(tmp_path / "profiles" / "traffic.json", "w") as fh:
+        json.dump({"conv512_k3_n64": {"bytes_per_gram": 1000.0, "kernel_sha16": "aaaa"}}, fh)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_sha16", lambda: "aaaa")
+    assert bench.measured_traffic("conv512_k3_n64", {"tc_grams": 2500}) == 2.5e6
+    assert bench.measured_traffic("conv512_k3_n64") is None
+    monkeypatch.setattr(bench, "kernel_sha16", lambda: "bbbb")
+    assert bench.measured_traffic("conv512_k3_n64", {"tc_grams": 2500}) is None
+
