@@ -104,6 +104,14 @@ typedef struct lfa_layer_desc {
                                   comparison system (Sec. II, Sec. IV Table II): a batched cuFFT
                                   transform of the zero-padded kernel per channel pair instead of
                                   the tap sums (stride-1 layers, values only; implies LFA_PLAIN) */
+#define LFA_REPRODUCIBLE 0x20u /* bitwise identical results from call to call. With vectors the
+                                  blocked route (LFA_VARIANT_BLOCKED) normally starts a symbol from
+                                  the singular vectors of its neighbouring frequency when that one
+                                  is already done, which takes fewer sweeps but depends on timing:
+                                  results then differ between calls in rounding (all within the
+                                  same tolerance). This flag starts every symbol from W = I
+                                  (512 channels: ~12.6 instead of ~8.5 sweeps per symbol). The
+                                  other routes are reproducible without it. */
 
 /* Options (nullable pointer: defaults). */
 typedef struct lfa_options {

@@ -215,7 +215,7 @@ int tuned_variant(const char* path, int M, int N, bool vec) {
 struct lfa_plan_s {
   int nlayers = 0;
   uint32_t flags = 0;
-  bool vec = false, half_output = false, plain = false, use_graph = true, fft = false;
+  bool vec = false, half_output = false, plain = false, use_graph = true, fft = false, reproducible = false;
   int max_sweeps = 30;
   float tol_opt = 0.f;
   int device = 0, sms = 0;
@@ -545,7 +545,7 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
   if (plan == nullptr) return LFA_ERR_INVALID_ARG;
   *plan = nullptr;
   if (layers == nullptr || nlayers < 1 || nlayers > kMaxLayers) return LFA_ERR_INVALID_ARG;
-  if (flags & ~(uint32_t)(LFA_VALUES | LFA_VECTORS | LFA_HALF_OUTPUT | LFA_PLAIN | LFA_FFT_ROUTE))
+  if (flags & ~(uint32_t)(LFA_VALUES | LFA_VECTORS | LFA_HALF_OUTPUT | LFA_PLAIN | LFA_FFT_ROUTE | LFA_REPRODUCIBLE))
     return LFA_ERR_INVALID_ARG;
   if (flags & LFA_FFT_ROUTE) {
     flags |= LFA_PLAIN;
@@ -577,6 +577,7 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
   p->half_output = (flags & LFA_HALF_OUTPUT) != 0;
   p->plain = (flags & LFA_PLAIN) != 0;
   p->fft = (flags & LFA_FFT_ROUTE) != 0;
+  p->reproducible = (flags & LFA_REPRODUCIBLE) != 0;
   p->max_sweeps = (opt && opt->max_sweeps > 0) ? opt->max_sweeps : 30;
   if (fault("nonconverge")) p->max_sweeps = 1;
   p->tol_opt = opt ? opt->tol : 0.f;
@@ -725,7 +726,8 @@ lfa_status_t lfa_plan(lfa_plan_t* plan, const lfa_layer_desc_t* layers, int32_t 
     if (g_bj_max_ctas > 0) g.ctas = std::min(g.ctas, g_bj_max_ctas);
     // warm starts (vectors): two runs of neighbouring symbols per CTA, so that the CTA taking a
     // run's next symbol finds the previous one done (about two symbol times apart in the queue)
-    g.runs = (!p->vec || g_bj_runs < 0) ? 0 : g_bj_runs > 0 ? g_bj_runs : 2 * g.ctas;
+    // (none with LFA_REPRODUCIBLE: whether a predecessor is done depends on timing)
+    g.runs = (!p->vec || p->reproducible || g_bj_runs < 0) ? 0 : g_bj_runs > 0 ? g_bj_runs : 2 * g.ctas;
     for (int b : g.members) {
       p->blocked[b].ctas = g.ctas;
       p->blocked[b].sym_begin = p->bj_symbols;

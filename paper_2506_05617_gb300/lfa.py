@@ -26,6 +26,7 @@ LFA_VECTORS = 0x2
 LFA_HALF_OUTPUT = 0x4
 LFA_PLAIN = 0x8
 LFA_FFT_ROUTE = 0x10
+LFA_REPRODUCIBLE = 0x20
 LFA_VARIANT_LOGGED = 0x10000   # options.variant flag: values variant + rotation log + W replay
 LFA_VARIANT_BLOCKED = 0x20000  # options.variant value: blocked Jacobi on the tensor cores
 

@@ -30,12 +30,13 @@ class LfaPlan:
     def __init__(self, layers: Sequence, vectors: bool = False, half_output: bool = False,
                  plain: bool = False, tol: float = 0.0, max_sweeps: int = 0, variant: int = -1,
                  use_graph: int = -1, tune_cache: Optional[str] = None, shard: tuple = (0, 1),
-                 fft_route: bool = False):
+                 fft_route: bool = False, reproducible: bool = False):
         self.layers = [_layer_tuple(d) for d in layers]
         self.vectors = bool(vectors)
         self.half_output = bool(half_output)
         flags = C.LFA_VALUES | (C.LFA_VECTORS if vectors else 0) | (C.LFA_HALF_OUTPUT if half_output else 0) \
-            | (C.LFA_PLAIN if plain else 0) | (C.LFA_FFT_ROUTE if fft_route else 0)
+            | (C.LFA_PLAIN if plain else 0) | (C.LFA_FFT_ROUTE if fft_route else 0) \
+            | (C.LFA_REPRODUCIBLE if reproducible else 0)
         self.shard = (int(shard[0]), int(shard[1]))
         self.handle = C.lfa_plan(self.layers, flags, tol, max_sweeps, variant, use_graph, tune_cache,
                                  self.shard[0], self.shard[1])
