@@ -152,7 +152,9 @@ typedef struct lfa_options {
  * operands split in three (hi*hi + hi*lo + lo*hi, FP32 accumulation), one CTA per symbol. It is
  * also the built-in choice for tall or square symbols (c_out >= c_in) of more than 128 columns in
  * layers with enough half-grid symbols to fill the GPU (84 up to 256 columns, 30 up to 384, 68 up
- * to 512; fewer go to the element-wise cluster kernels).
+ * to 512; fewer go to the element-wise cluster kernels). With vectors a symbol starts from the
+ * singular vectors of its neighbouring frequency when that symbol is already done (fewer sweeps;
+ * LFA_REPRODUCIBLE turns this off).
  * lfa_layer_query reports it as this value. */
 #define LFA_VARIANT_BLOCKED 0x20000
 
