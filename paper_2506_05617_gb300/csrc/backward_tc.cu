@@ -98,7 +98,10 @@ bw_g_tc_kernel(LayerArgs La, const float* dsigma, int half_output, const float2*
     const int it = ms->item;
     if (it >= total) break;
     const int h = h_begin + it / (to * ti);
-    if (!LFA_DOK(La.dbg, h < h_end && h < La.F_h, 9)) continue;   // tensor-core G: item -> symbol
+    if (!LFA_DOK(La.dbg, h < h_end && h < La.F_h, 9)) {   // tensor-core G: item -> symbol
+      __syncthreads();                                     // every thread has read ms->item
+      continue;
+    }
     const int tile = it % (to * ti);
     const int o0 = (tile / ti) * TM, i0 = (tile % ti) * TN;
     const int f = La.half[h];

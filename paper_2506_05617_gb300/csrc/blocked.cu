@@ -691,7 +691,10 @@ __global__ void __maxnreg__(bj::MAX_REGS) bj_kernel(const __grid_constant__ BJLa
     while (lk + 1 < A.nlayers && g >= A.L[lk + 1].item_begin) ++lk;
     const LayerArgs& La = A.L[lk];
     const int h = g - La.item_begin;                    // half-grid symbol of that layer
-    if (!LFA_DOK(La.dbg, h >= 0 && h < La.F_h, 5)) continue;   // blocked route: item -> layer, symbol
+    if (!LFA_DOK(La.dbg, h >= 0 && h < La.F_h, 5)) {   // blocked route: item -> layer, symbol
+      __syncthreads();                                 // every thread has read ms->item
+      continue;
+    }
     const int M = La.M, N = La.N;
     if (threadIdx.x == 0) {
       c_sym = clock64();
