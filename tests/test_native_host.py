@@ -119,6 +119,36 @@ def test_plan_rejects_bad_flags_and_counts():
     assert ei.value.status == C.LFA_ERR_INVALID_ARG
 
 
+def test_header_constants_match_the_binding():
+    """Every numeric LFA_* constant of lfa.h (flags, variants, edit modes, status codes, sizes) has
+    the same value in the ctypes binding."""
+    txt = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "lfa.h")).read(), flags=re.S)
+    defs = {}
+    for name, val in re.findall(r"#define\s+(LFA_[A-Z0-9_]+)\s+\(?((?:0x[0-9a-fA-F]+|\d+)u?(?:\s*<<\s*\d+)?)\)?", txt):
+        defs[name] = eval(val.replace("u", ""), {})
+    for name, val in re.findall(r"\b(LFA_[A-Z0-9_]+)\s*=\s*(\d+)", txt):   # enumerators
+        defs[name] = int(val)
+    assert {"LFA_VECTORS", "LFA_REPRODUCIBLE", "LFA_VARIANT_BLOCKED", "LFA_ERR_TIMEOUT"} <= set(defs)
+    for name, v in defs.items():
+        if hasattr(C, name):
+            assert getattr(C, name) == v, name
+    missing = [n for n in defs if not hasattr(C, n) and not n.endswith("_H_")]
+    assert all(n.startswith("LFA_NOALLOC") or n.startswith("LFA_VERSION") or n == "LFA_API" for n in missing), missing
+
+
+def test_plan_flags_validation_accepts_reproducible():
+    """LFA_REPRODUCIBLE is a valid plan flag: without a GPU the plan then fails only at the device."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(C.LfaError) as ei:
+        C.lfa_plan([(4, 4, 3, 3, 8, 8)], C.LFA_VALUES | C.LFA_VECTORS | C.LFA_REPRODUCIBLE)
+    assert ei.value.status in (C.LFA_ERR_CUDA, C.LFA_ERR_UNSUPPORTED)
+    with pytest.raises(C.LfaError) as ei:
+        C.lfa_plan([(4, 4, 3, 3, 8, 8)], C.LFA_VALUES | 0x40)
+    assert ei.value.status == C.LFA_ERR_INVALID_ARG
+
+
 def test_null_plan_calls_are_rejected():
     L = C.lib()
     assert L.lfa_svd(None, None, None, None, None, None) == C.LFA_ERR_INVALID_ARG
